@@ -1,0 +1,198 @@
+/*
+ * msclbm.h - C ABI of the B300 (sm_103a) MSC-LBM library (libmsclbm.so).
+ *
+ * MSC-LBM is the macroscopic-shadow-corrected lattice Boltzmann method of
+ * arxiv 2609.39474: a BDF dual-time inner iteration on periodic D2Q9 / D3Q19
+ * lattices whose fixed point is the fully discrete population equation
+ * T(f) - f = 0 (Eq. fixed-point-problem).  Each inner iteration runs one fused
+ * TRT collide-stream sweep at the operating point Lambda = 1/4,
+ * omega+ = omega- = 1 (Eqs. collision-operating, sweep), tests the raw
+ * population RMS residual (Eq. residual), and otherwise corrects the conserved
+ * residual moments by a masked Fourier-space solve of the shadow system and an
+ * equilibrium lift (Eqs. schur, lift, shadow-update; Algorithm 1).
+ *
+ * Conventions shared by every entry point
+ *  - Lattices are periodic and cubic: n sites per direction, n a power of two,
+ *    8 <= n <= 8192 for D2Q9 (dim 2) and 8 <= n <= 512 for D3Q19 (dim 3).
+ *  - Layout is structure of arrays with x fastest: populations f[k][z][y][x]
+ *    (k in the paper's ordering, Appendix A), fields m[c][z][y][x] with
+ *    c = 0 the pressure-like variable p_hat and c = 1..d the velocity
+ *    components.  2D arrays drop the z index.  "sites" = n^dim.
+ *  - Storage precision (MSC_FP64 / MSC_FP32) fixes the element type of
+ *    population and working-field arrays (double / float).  Host-facing
+ *    fields (p_hat, u, residual norms, BDF moment history) are always double.
+ *  - Device pointers must come from cudaMalloc-class allocations of the
+ *    current device; the library never frees caller memory and never
+ *    allocates device memory itself (the context lives in a caller-provided
+ *    workspace).  Stream arguments are cudaStream_t values passed as void*;
+ *    NULL means the legacy default stream.  Work is enqueued on that stream
+ *    only.
+ *  - Unless stated otherwise calls are asynchronous with respect to the host;
+ *    msc_get_stats, msc_read_*, msc_get_* and msc_save_state synchronise
+ *    the stream.
+ *  - Every function returns MSC_OK (0) or one of the status codes below and
+ *    performs no work when it returns MSC_ERR_ARG.
+ */
+#ifndef MSCLBM_H
+#define MSCLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define MSC_OK 0
+#define MSC_ERR_ARG 1          /* invalid argument: size, pointer, precision, parameter */
+#define MSC_ERR_NONCONVERGED 2 /* a physical step reached K_max without passing the residual test
+                                  (Section 4.1: recorded nonconvergent); the state stays at the
+                                  last accepted step */
+#define MSC_ERR_NONFINITE 3    /* a non-finite raw residual (never accepted, Section 4.1); the
+                                  march stops with the state at the last accepted step */
+#define MSC_ERR_TIMEOUT 4      /* reserved: a bounded device wait gave up */
+#define MSC_ERR_CUDA 5         /* a CUDA runtime call failed */
+#define MSC_ERR_STATE 6        /* call out of order (e.g. march before init or set_params) */
+
+/* Storage precisions. */
+#define MSC_FP64 0
+#define MSC_FP32 1
+
+typedef struct msc_ctx msc_ctx; /* opaque; lives inside the caller's workspace */
+
+typedef struct {
+    int dim;        /* 2: D2Q9, 3: D3Q19 (Appendix A orderings) */
+    int n;          /* sites per direction (power of two, see limits above) */
+    int precision;  /* MSC_FP64 or MSC_FP32 population storage */
+    int max_steps;  /* capacity of the per-step statistics and replay tables (>= 1) */
+    int hist_cap;   /* capacity of the inner-residual history ring (>= 1) */
+} msc_lattice_desc;
+
+typedef struct {
+    double nu;      /* viscosity of the shadow solve, Eq. shadow-mom; the sweep itself runs at the
+                       operating point omega+ = omega- = 1, i.e. nu = 1/6 (Eq. trt) */
+    double dt;      /* physical BDF step Delta t in lattice time units (> 0), Eq. bdf2 */
+    double eps;     /* acceptance tolerance on the raw RMS residual (>= 0), Algorithm 1 */
+    int kmax;       /* maximum inner iterations per physical step (>= 1) */
+    int nmin;       /* minimum accepted inner count (>= 1): 2 in 2D, 1 in 3D in the paper */
+    int corrector;  /* 1: MSC-LBM shadow correction (Algorithm 1); 0: plain Picard */
+    int replay;     /* 1: accept step i at the inner count set by msc_set_replay_counts,
+                       regardless of the residual (parity testing); 0: normal acceptance */
+} msc_params;
+
+typedef struct {
+    int64_t steps_done;   /* accepted physical steps since msc_init_fields */
+    int64_t inner_total;  /* inner sweeps run by the last march call */
+    int32_t steps_in_call;/* physical steps accepted by the last march call */
+    int32_t last_iters;   /* inner count of the last accepted step */
+    int32_t last_q;       /* BDF order of the last accepted step (1 or 2) */
+    int32_t status;       /* MSC_OK or the code that stopped the last march */
+    double last_R;        /* last raw RMS residual computed */
+} msc_stats;
+
+/* ---- Context: state of one periodic lattice (Sections 2.3, 3.1) -------------------------- */
+
+/* Bytes of device workspace a context with this description needs (0 if the description is
+   invalid).  The workspace holds the population ring (f^n, f^{n-1}, f^{n-2} and two working
+   buffers), the FP64 moment histories m^n, m^{n-1}, the history term h, residual moments,
+   the shadow correction, the half spectrum, twiddles, reduction partials and statistics. */
+size_t msc_workspace_bytes(const msc_lattice_desc* desc);
+
+/* Create a context in dev_workspace (device memory of >= msc_workspace_bytes bytes, 256-byte
+   aligned; owned by the caller and used exclusively by this context until msc_destroy).  The
+   context's host part is allocated with malloc; its CUDA graphs are built lazily on first use.
+   The stream is where every later call of this context enqueues work. */
+int msc_create(msc_ctx** out, const msc_lattice_desc* desc, void* dev_workspace, size_t bytes,
+               void* stream);
+
+/* Destroy the host part and graphs of a context (the workspace is not touched). */
+void msc_destroy(msc_ctx* ctx);
+
+/* Set the march parameters (validated here; returns MSC_ERR_ARG on nonsense). */
+int msc_set_params(msc_ctx* ctx, const msc_params* params);
+
+/* f^0 = f_eq(p_hat, u) (Eq. feq), m^0 = P f^0 (Eq. moments); no pre-march relaxation
+   (Section 4.1).  p_hat has sites doubles, u has dim*sites doubles, both in the field layout
+   above, on the host (on_device = 0) or the device (on_device = 1).  Resets the histories so
+   that the next physical step is BDF1. */
+int msc_init_fields(msc_ctx* ctx, const double* p_hat, const double* u, int on_device);
+
+/* Run n_steps physical steps of Algorithm 1 (corrector = 1) or plain Picard dual-time
+   stepping (corrector = 0) entirely on the device: per step the BDF coefficients and the
+   population warm start (Section 3.1), then inner iterations sweep -> residual test ->
+   shadow correction until acceptance, then reconstruction of m^{n+1} and history rotation.
+   BDF1 is used on the first step after msc_init_fields, BDF2 after.  Asynchronous; read the
+   outcome with msc_get_stats.  A nonconvergent or non-finite step stops the march with the
+   state at the last accepted step. */
+int msc_march(msc_ctx* ctx, int n_steps);
+
+/* Run n_steps explicit LBM steps f <- S f_eq(P f) (same collision and streaming with no BDF
+   source; Section 4.1) from the current accepted populations.  Afterwards m^n = P f and the
+   dual-time history restarts (the next physical step is BDF1). */
+int msc_explicit_march(msc_ctx* ctx, int n_steps);
+
+/* Statistics of the last march call (synchronises the stream). */
+int msc_get_stats(msc_ctx* ctx, msc_stats* out);
+
+/* Copy the accepted macroscopic field m^n = (p_hat, u) (double, layout above) to host or
+   device memory (synchronises). */
+int msc_read_fields(msc_ctx* ctx, double* p_hat, double* u, int on_device);
+
+/* Copy the accepted populations f^n (converted to double, Q*sites values) out (synchronises). */
+int msc_read_populations(msc_ctx* ctx, double* f, int on_device);
+
+/* Copy up to cap raw residuals R_l of the last march call (oldest first) to the host; *n gets
+   the number copied.  The ring keeps the last hist_cap values. */
+int msc_get_residual_history(msc_ctx* ctx, double* R, int cap, int* n);
+
+/* Copy the accepted inner count of each step of the last march call (host ints; *n copied). */
+int msc_get_step_iters(msc_ctx* ctx, int* iters, int cap, int* n);
+
+/* Set the inner counts that replay mode forces on the next march call's steps (host ints,
+   1 <= counts[i] <= kmax, n <= max_steps). */
+int msc_set_replay_counts(msc_ctx* ctx, const int* counts, int n);
+
+/* Serialise the accepted state (f^n, f^{n-1}, f^{n-2}, m^n, m^{n-1}, step counters) into a
+   host blob.  With blob == NULL only *bytes is set to the size needed. */
+int msc_save_state(msc_ctx* ctx, void* host_blob, size_t* bytes);
+int msc_load_state(msc_ctx* ctx, const void* host_blob, size_t bytes);
+
+/* Human-readable text for a status code (static storage). */
+const char* msc_strerror(int status);
+
+/* ---- Stage entry points: one step of the hot path on caller-owned device arrays ----------- */
+
+/* Scratch bytes the stage calls below need for this lattice (reduction partials and the half
+   spectrum).  The scratch is device memory owned by the caller, 256-byte aligned. */
+size_t msc_stage_scratch_bytes(int dim, int n, int precision);
+
+/* One fused sweep (Eqs. macro-reconstruct .. sweep, residual):
+     trial  f = f_in + E dm            (Eq. lift; skipped when dm == NULL)
+     m = (P f + h/2)/(1 + a/2),  s = h - a m,  C = f_eq(m) + Phi(m, s)/2,
+     f_out = S C (periodic push streaming),  r = f_out - f,
+     pr_out = P r  ((dim+1)*sites values),  *sumsq_out = sum_x sum_k r_k(x)^2 (one double).
+   f_in / f_out: Q*sites elements of the storage type, distinct arrays; dm, h, pr_out:
+   (dim+1)*sites elements of the storage type; sumsq_out: device double.  With a = 0 and h all
+   zero this is one explicit LBM step plus its change.  Scratch as above. */
+int msc_sweep(int dim, int n, int precision, double a, const void* f_in, const void* dm,
+              const void* h, void* f_out, void* pr_out, double* sumsq_out, void* scratch,
+              size_t scratch_bytes, void* stream);
+
+/* Shadow correction of the residual moments (Eq. shadow-update, first two lines):
+     dm = F^{-1}[ chi(k) H(k)^{-1} F[pr] ]
+   with the paper's transform convention (Eq. fft-convention), wavenumbers k_j = 2 pi j / n
+   (Eq. wavenumbers), the rectangular mask |j_alpha| <= n/4 (Eq. shadow-mask) and the closed-form
+   Schur elimination of H(k) (Eq. schur) evaluated in FP64.  pr, dm: (dim+1)*sites elements of
+   the storage type (may not alias). */
+int msc_shadow_solve(int dim, int n, int precision, double a, double nu, const void* pr, void* dm,
+                     void* scratch, size_t scratch_bytes, void* stream);
+
+/* f_out = f_eq(p_hat, u) (Eq. feq) from double device fields; f_out in the storage type. */
+int msc_equilibrium(int dim, int n, int precision, const double* p_hat, const double* u,
+                    void* f_out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MSCLBM_H */

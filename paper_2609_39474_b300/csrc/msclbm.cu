@@ -1,0 +1,861 @@
+// C ABI of the MSC-LBM library: contexts, the device-resident march (CUDA graph with nested
+// conditional WHILE/IF nodes, so that the acceptance test of Algorithm 1 never leaves the
+// device), the explicit LBM baseline and the stage entry points.  See include/msclbm.h.
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+#include "fft.cuh"
+#include "march.cuh"
+#include "spectral2d.cuh"
+#include "spectral3d.cuh"
+#include "sweep2d.cuh"
+#include "sweep3d.cuh"
+
+using namespace msc;
+
+#define CK(call)                                   \
+    do {                                           \
+        cudaError_t e_ = (call);                   \
+        if (e_ != cudaSuccess) return MSC_ERR_CUDA; \
+    } while (0)
+
+struct msc_ctx {
+    msc_lattice_desc desc;
+    int Q, logn;
+    size_t sites;
+    size_t elem;  // bytes per stored population / field element
+    Layout lay;
+    unsigned char* ws;
+    cudaStream_t stream;
+    bool params_set, fields_set;
+    msc_params params;
+    // graphs
+    cudaGraph_t g_march;
+    cudaGraphExec_t x_march;
+    cudaGraph_t g_ex;
+    cudaGraphExec_t x_ex;
+    int sweep_blocks;
+};
+
+namespace {
+
+template <typename P>
+P* at(msc_ctx* c, size_t off) {
+    return reinterpret_cast<P*>(c->ws + off);
+}
+
+int sweep_blocks_for(int dim, int n, int precision) {
+    if (dim == 2) return sweep2_geometry(n).blocks;
+    return sweep3_geometry(n, precision == MSC_FP64 ? 8 : 4).blocks;
+}
+
+size_t spec_bytes(int dim, int n, int precision) {
+    const size_t celem = precision == MSC_FP64 ? 16 : 8;
+    if (dim == 2) return (size_t)3 * n * (n / 4 + 1) * celem;
+    return spec3_bytes(n, celem);
+}
+
+bool compute_layout(const msc_lattice_desc* d, Layout* L) {
+    if (!d || !valid_lattice(d->dim, d->n, d->precision)) return false;
+    if (d->max_steps < 1 || d->hist_cap < 1) return false;
+    const size_t n = d->n;
+    const size_t sites = d->dim == 2 ? n * n : n * n * n;
+    const size_t Q = lattice_q(d->dim);
+    const size_t F = d->dim + 1;
+    const size_t e = d->precision == MSC_FP64 ? 8 : 4;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        const size_t r = o;
+        o = align_up(o + bytes, 256);
+        return r;
+    };
+    L->state = take(sizeof(DevState));
+    L->fstride = Q * sites * e;
+    L->fbuf = take(kNumFBuf * L->fstride);
+    L->mbuf = take(2 * F * sites * 8);
+    L->h = take(F * sites * e);
+    L->pr = take(F * sites * e);
+    L->dm = take(F * sites * e);
+    L->spec = take(spec_bytes(d->dim, d->n, d->precision));
+    L->tw = take((n / 2) * 2 * e);
+    L->partial = take((size_t)sweep_blocks_for(d->dim, d->n, d->precision) * 8);
+    L->counter = take(256);
+    L->iters = take((size_t)d->max_steps * 4);
+    L->hist = take((size_t)d->hist_cap * 8);
+    L->replay = take((size_t)d->max_steps * 4);
+    L->total = o;
+    return true;
+}
+
+int grid_for(size_t sites) {
+    size_t b = (sites + kFieldThreads - 1) / kFieldThreads;
+    if (b > 148 * 16) b = 148 * 16;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+// ---- typed helpers ------------------------------------------------------------------------------
+
+template <typename T>
+Sweep2Args<T> sweep2_args_graph(msc_ctx* c) {
+    Sweep2Args<T> A;
+    memset(&A, 0, sizeof(A));
+    const Sweep2Geom g = sweep2_geometry(c->desc.n);
+    A.dm = at<T>(c, c->lay.dm);
+    A.h = at<T>(c, c->lay.h);
+    A.pr = at<T>(c, c->lay.pr);
+    A.partial = at<double>(c, c->lay.partial);
+    A.counter = at<unsigned int>(c, c->lay.counter);
+    A.n = c->desc.n;
+    A.nstrips = g.nstrips;
+    A.hb = g.hb;
+    A.nrowblk = g.nrowblk;
+    A.st = at<DevState>(c, c->lay.state);
+    A.fbase = at<T>(c, c->lay.fbuf);
+    A.fstride = c->lay.fstride / sizeof(T);
+    A.hist = at<double>(c, c->lay.hist);
+    A.hist_cap = c->desc.hist_cap;
+    A.replay_counts = at<int>(c, c->lay.replay);
+    A.max_steps = c->desc.max_steps;
+    return A;
+}
+
+template <typename T>
+Sweep3Args<T> sweep3_args_graph(msc_ctx* c) {
+    Sweep3Args<T> A;
+    memset(&A, 0, sizeof(A));
+    const Sweep3Geom g = sweep3_geometry(c->desc.n, sizeof(T));
+    A.dm = at<T>(c, c->lay.dm);
+    A.h = at<T>(c, c->lay.h);
+    A.pr = at<T>(c, c->lay.pr);
+    A.partial = at<double>(c, c->lay.partial);
+    A.counter = at<unsigned int>(c, c->lay.counter);
+    A.n = c->desc.n;
+    A.g = g;
+    A.st = at<DevState>(c, c->lay.state);
+    A.fbase = at<T>(c, c->lay.fbuf);
+    A.fstride = c->lay.fstride / sizeof(T);
+    A.hist = at<double>(c, c->lay.hist);
+    A.hist_cap = c->desc.hist_cap;
+    A.replay_counts = at<int>(c, c->lay.replay);
+    A.max_steps = c->desc.max_steps;
+    return A;
+}
+
+cudaGraphNode_t add_kernel(cudaGraph_t g, const std::vector<cudaGraphNode_t>& deps, const void* fn,
+                           dim3 grid, dim3 block, size_t smem, void** args, cudaError_t* err) {
+    cudaKernelNodeParams p;
+    memset(&p, 0, sizeof(p));
+    p.func = const_cast<void*>(fn);
+    p.gridDim = grid;
+    p.blockDim = block;
+    p.sharedMemBytes = (unsigned)smem;
+    p.kernelParams = args;
+    cudaGraphNode_t node = nullptr;
+    cudaError_t e = cudaGraphAddKernelNode(&node, g, deps.empty() ? nullptr : deps.data(), deps.size(), &p);
+    if (e != cudaSuccess && *err == cudaSuccess) *err = e;
+    return node;
+}
+
+cudaGraphNode_t add_cond(cudaGraph_t g, const std::vector<cudaGraphNode_t>& deps,
+                         cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type,
+                         cudaGraph_t* body, cudaError_t* err) {
+    // the parameter union has no default constructor: build it in zeroed raw storage
+    alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)];
+    memset(raw, 0, sizeof(raw));
+    cudaGraphNodeParams* p = reinterpret_cast<cudaGraphNodeParams*>(raw);
+    p->type = cudaGraphNodeTypeConditional;
+    p->conditional.handle = h;
+    p->conditional.type = type;
+    p->conditional.size = 1;
+    cudaGraphNode_t node = nullptr;
+    cudaError_t e = cudaGraphAddNode(&node, g, deps.empty() ? nullptr : deps.data(), nullptr, deps.size(), p);
+    if (e != cudaSuccess) {
+        if (*err == cudaSuccess) *err = e;
+        *body = nullptr;
+        return nullptr;
+    }
+    *body = p->conditional.phGraph_out[0];
+    return node;
+}
+
+// spectral correction nodes: 2D forward row FFT, column FFT + solve + inverse, inverse row FFT;
+// 3D the five passes of spectral3d.cuh.  All take the same argument block.
+template <typename T>
+void add_spectral_nodes(msc_ctx* c, cudaGraph_t g, cudaError_t* err) {
+    using C = typename Cplx<T>::type;
+    const int n = c->desc.n;
+    Spec2Args<T> S = spec3_args<T>(n, c->logn, 0.0, c->params.nu, at<T>(c, c->lay.pr), at<C>(c, c->lay.spec),
+                                   at<T>(c, c->lay.dm), at<C>(c, c->lay.tw), at<DevState>(c, c->lay.state));
+    void* args[] = {&S};
+    if (c->desc.dim == 2) {
+        S.nf = 3;
+        S.rows = n;
+        cudaGraphNode_t n1 = add_kernel(g, {}, (const void*)k_rowfft_fwd<T>, dim3(spec2_row_blocks(n)),
+                                        dim3(kFftThreads), spec2_row_smem<T>(n), args, err);
+        cudaGraphNode_t n2 = add_kernel(g, {n1}, (const void*)k_colsolve<T>, dim3(n / 4 + 1),
+                                        dim3(kFftThreads), spec2_col_smem<T>(n), args, err);
+        add_kernel(g, {n2}, (const void*)k_rowfft_inv<T>, dim3(spec2_row_blocks(n)), dim3(kFftThreads),
+                   spec2_row_smem<T>(n), args, err);
+    } else {
+        LaunchDesc L[5];
+        spectral3_launches<T>(n, L);
+        cudaGraphNode_t prev = nullptr;
+        for (int i = 0; i < 5; ++i) {
+            std::vector<cudaGraphNode_t> deps;
+            if (prev) deps.push_back(prev);
+            prev = add_kernel(g, deps, L[i].fn, L[i].grid, L[i].block, L[i].smem, args, err);
+        }
+    }
+}
+
+template <typename T>
+int set_smem_limits(int dim, int n) {
+    if (dim == 2) {
+        CK(cudaFuncSetAttribute(k_rowfft_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)spec2_row_smem<T>(n)));
+        CK(cudaFuncSetAttribute(k_rowfft_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)spec2_row_smem<T>(n)));
+        CK(cudaFuncSetAttribute(k_colsolve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)spec2_col_smem<T>(n)));
+    } else {
+        if (set_spec3_smem_limits<T>(n) != 0) return MSC_ERR_CUDA;
+        if (set_sweep3_smem_limits<T>(n) != 0) return MSC_ERR_CUDA;
+    }
+    return MSC_OK;
+}
+
+template <class L, typename T>
+int build_march_graph(msc_ctx* c) {
+    cudaError_t err = cudaSuccess;
+    int rc = set_smem_limits<T>(c->desc.dim, c->desc.n);
+    if (rc) return rc;
+    cudaGraph_t g;
+    CK(cudaGraphCreate(&g, 0));
+    DevState* st = at<DevState>(c, c->lay.state);
+    T* fbase = at<T>(c, c->lay.fbuf);
+    const size_t fstride = c->lay.fstride / sizeof(T);
+    double* mbuf = at<double>(c, c->lay.mbuf);
+    T* h = at<T>(c, c->lay.h);
+    int* iters = at<int>(c, c->lay.iters);
+    size_t sites = c->sites;
+    int max_steps = c->desc.max_steps;
+    const int fgrid = grid_for(sites);
+
+    cudaGraphConditionalHandle h_step, h_iter, h_corr;
+    CK(cudaGraphConditionalHandleCreate(&h_step, g, 0, 0));
+    void* a_arm[] = {&st, &h_step};
+    cudaGraphNode_t arm = add_kernel(g, {}, (const void*)k_arm, dim3(1), dim3(1), 0, a_arm, &err);
+    cudaGraph_t body_step;
+    add_cond(g, {arm}, h_step, cudaGraphCondTypeWhile, &body_step, &err);
+    if (err != cudaSuccess) { cudaGraphDestroy(g); return MSC_ERR_CUDA; }
+
+    CK(cudaGraphConditionalHandleCreate(&h_iter, body_step, 0, 0));
+    void* a_setup[] = {&st, &h_iter};
+    cudaGraphNode_t setup = add_kernel(body_step, {}, (const void*)k_step_setup, dim3(1), dim3(1), 0, a_setup, &err);
+    void* a_begin[] = {&st, &fbase, (void*)&fstride, &mbuf, &h, &sites};
+    cudaGraphNode_t begin = add_kernel(body_step, {setup}, (const void*)k_step_begin<L, T>, dim3(fgrid),
+                                       dim3(kFieldThreads), 0, a_begin, &err);
+    cudaGraph_t body_iter;
+    cudaGraphNode_t wit = add_cond(body_step, {begin}, h_iter, cudaGraphCondTypeWhile, &body_iter, &err);
+    if (err != cudaSuccess) { cudaGraphDestroy(g); return MSC_ERR_CUDA; }
+    void* a_end[] = {&st, &fbase, (void*)&fstride, &mbuf, &sites};
+    cudaGraphNode_t end = add_kernel(body_step, {wit}, (const void*)k_step_end<L, T>, dim3(fgrid),
+                                     dim3(kFieldThreads), 0, a_end, &err);
+    void* a_fin[] = {&st, &iters, &max_steps, &h_step};
+    add_kernel(body_step, {end}, (const void*)k_step_finish, dim3(1), dim3(1), 0, a_fin, &err);
+
+    CK(cudaGraphConditionalHandleCreate(&h_corr, body_iter, 0, 0));
+    cudaGraphNode_t sw;
+    if (L::D == 2) {
+        Sweep2Args<T> A = sweep2_args_graph<T>(c);
+        A.h_iter = h_iter;
+        A.h_corr = h_corr;
+        void* a_sw[] = {&A};
+        sw = add_kernel(body_iter, {}, (const void*)k_sweep2<T, false, true>, dim3(sweep2_geometry(c->desc.n).blocks),
+                        dim3(kSweepWarps * 32), 0, a_sw, &err);
+    } else {
+        Sweep3Args<T> A = sweep3_args_graph<T>(c);
+        A.h_iter = h_iter;
+        A.h_corr = h_corr;
+        void* a_sw[] = {&A};
+        sw = add_kernel(body_iter, {}, (const void*)k_sweep3<T, false, true>, dim3(A.g.blocks),
+                        dim3(A.g.threads), A.g.smem, a_sw, &err);
+    }
+    cudaGraph_t body_corr;
+    add_cond(body_iter, {sw}, h_corr, cudaGraphCondTypeIf, &body_corr, &err);
+    if (err != cudaSuccess) { cudaGraphDestroy(g); return MSC_ERR_CUDA; }
+    add_spectral_nodes<T>(c, body_corr, &err);
+    if (err != cudaSuccess) { cudaGraphDestroy(g); return MSC_ERR_CUDA; }
+
+    cudaGraphExec_t x;
+    if (cudaGraphInstantiate(&x, g, 0) != cudaSuccess) { cudaGraphDestroy(g); return MSC_ERR_CUDA; }
+    c->g_march = g;
+    c->x_march = x;
+    return MSC_OK;
+}
+
+template <class L, typename T>
+int build_explicit_graph(msc_ctx* c) {
+    cudaError_t err = cudaSuccess;
+    int rc = set_smem_limits<T>(c->desc.dim, c->desc.n);
+    if (rc) return rc;
+    cudaGraph_t g;
+    CK(cudaGraphCreate(&g, 0));
+    DevState* st = at<DevState>(c, c->lay.state);
+    cudaGraphConditionalHandle h_ex;
+    CK(cudaGraphConditionalHandleCreate(&h_ex, g, 0, 0));
+    void* a_arm[] = {&st, &h_ex};
+    cudaGraphNode_t arm = add_kernel(g, {}, (const void*)k_ex_arm, dim3(1), dim3(1), 0, a_arm, &err);
+    cudaGraph_t body;
+    add_cond(g, {arm}, h_ex, cudaGraphCondTypeWhile, &body, &err);
+    if (err != cudaSuccess) { cudaGraphDestroy(g); return MSC_ERR_CUDA; }
+    if (L::D == 2) {
+        Sweep2Args<T> A = sweep2_args_graph<T>(c);
+        Sweep2Args<T> B = A;
+        A.ex_dir = 0; A.ex_count = 0;
+        B.ex_dir = 1; B.ex_count = 1; B.h_ex = h_ex;
+        void* aa[] = {&A};
+        void* ab[] = {&B};
+        const int blocks = sweep2_geometry(c->desc.n).blocks;
+        cudaGraphNode_t n1 = add_kernel(body, {}, (const void*)k_sweep2<T, true, true>, dim3(blocks),
+                                        dim3(kSweepWarps * 32), 0, aa, &err);
+        add_kernel(body, {n1}, (const void*)k_sweep2<T, true, true>, dim3(blocks), dim3(kSweepWarps * 32), 0,
+                   ab, &err);
+    } else {
+        Sweep3Args<T> A = sweep3_args_graph<T>(c);
+        Sweep3Args<T> B = A;
+        A.ex_dir = 0; A.ex_count = 0;
+        B.ex_dir = 1; B.ex_count = 1; B.h_ex = h_ex;
+        void* aa[] = {&A};
+        void* ab[] = {&B};
+        cudaGraphNode_t n1 = add_kernel(body, {}, (const void*)k_sweep3<T, true, true>, dim3(A.g.blocks),
+                                        dim3(A.g.threads), A.g.smem, aa, &err);
+        add_kernel(body, {n1}, (const void*)k_sweep3<T, true, true>, dim3(A.g.blocks), dim3(A.g.threads),
+                   A.g.smem, ab, &err);
+    }
+    if (err != cudaSuccess) { cudaGraphDestroy(g); return MSC_ERR_CUDA; }
+    cudaGraphExec_t x;
+    if (cudaGraphInstantiate(&x, g, 0) != cudaSuccess) { cudaGraphDestroy(g); return MSC_ERR_CUDA; }
+    c->g_ex = g;
+    c->x_ex = x;
+    return MSC_OK;
+}
+
+template <class L, typename T>
+int run_explicit(msc_ctx* c, int n_steps) {
+    if (!c->x_ex) {
+        int rc = build_explicit_graph<L, T>(c);
+        if (rc) return rc;
+    }
+    DevState* st = at<DevState>(c, c->lay.state);
+    const int pairs = n_steps / 2;
+    const int odd = n_steps & 1;
+    k_ex_setup<<<1, 1, 0, c->stream>>>(st, pairs);
+    CK(cudaGetLastError());
+    if (pairs > 0) CK(cudaGraphLaunch(c->x_ex, c->stream));
+    if (odd) {
+        if (L::D == 2) {
+            Sweep2Args<T> A = sweep2_args_graph<T>(c);
+            A.ex_dir = 0;
+            k_sweep2<T, true, true><<<sweep2_geometry(c->desc.n).blocks, kSweepWarps * 32, 0, c->stream>>>(A);
+        } else {
+            Sweep3Args<T> A = sweep3_args_graph<T>(c);
+            A.ex_dir = 0;
+            k_sweep3<T, true, true><<<A.g.blocks, A.g.threads, A.g.smem, c->stream>>>(A);
+        }
+        CK(cudaGetLastError());
+    }
+    k_ex_finish<<<1, 1, 0, c->stream>>>(st, odd);
+    CK(cudaGetLastError());
+    // m^n = P f^n, m^{n-1} = m^n: read the new slot from the state on the device
+    k_moments_state<L, T><<<grid_for(c->sites), kFieldThreads, 0, c->stream>>>(
+        st, at<T>(c, c->lay.fbuf), c->lay.fstride / sizeof(T), at<double>(c, c->lay.mbuf), c->sites);
+    CK(cudaGetLastError());
+    return MSC_OK;
+}
+
+template <class L, typename T>
+int run_init(msc_ctx* c, const double* p, const double* u, int on_device) {
+    DevState* st = at<DevState>(c, c->lay.state);
+    double* m0 = at<double>(c, c->lay.mbuf);
+    double* m1 = m0 + (size_t)(L::D + 1) * c->sites;
+    const size_t fb = c->sites * sizeof(double);
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    // stage (p, u) in the m^{n-1} slot, build f^0 in ring slot 0, then m^0 = P f^0 in both slots
+    CK(cudaMemcpyAsync(m1, p, fb, kind, c->stream));
+    CK(cudaMemcpyAsync(m1 + c->sites, u, fb * L::D, kind, c->stream));
+    k_reset_history<<<1, 1, 0, c->stream>>>(st);
+    CK(cudaGetLastError());
+    T* f0 = at<T>(c, c->lay.fbuf);
+    k_equilibrium<L, T><<<grid_for(c->sites), kFieldThreads, 0, c->stream>>>(m1, m1 + c->sites, f0, c->sites);
+    CK(cudaGetLastError());
+    k_moments<L, T><<<grid_for(c->sites), kFieldThreads, 0, c->stream>>>(f0, m0, m1, c->sites);
+    CK(cudaGetLastError());
+    return MSC_OK;
+}
+
+int read_state(msc_ctx* c, DevState* hs) {
+    CK(cudaMemcpyAsync(hs, c->ws + c->lay.state, sizeof(DevState), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return MSC_OK;
+}
+
+}  // namespace
+
+// ================================================================================================
+extern "C" {
+
+const char* msc_strerror(int s) {
+    switch (s) {
+        case MSC_OK: return "ok";
+        case MSC_ERR_ARG: return "invalid argument";
+        case MSC_ERR_NONCONVERGED: return "physical step reached K_max without passing the residual test";
+        case MSC_ERR_NONFINITE: return "non-finite raw residual";
+        case MSC_ERR_TIMEOUT: return "device wait exceeded its budget";
+        case MSC_ERR_CUDA: return "CUDA runtime error";
+        case MSC_ERR_STATE: return "call out of order";
+        default: return "unknown status";
+    }
+}
+
+size_t msc_workspace_bytes(const msc_lattice_desc* desc) {
+    Layout L;
+    if (!compute_layout(desc, &L)) return 0;
+    return L.total;
+}
+
+int msc_create(msc_ctx** out, const msc_lattice_desc* desc, void* ws, size_t bytes, void* stream) {
+    if (!out) return MSC_ERR_ARG;
+    *out = nullptr;
+    Layout L;
+    if (!compute_layout(desc, &L) || !ws || bytes < L.total) return MSC_ERR_ARG;
+    if (reinterpret_cast<uintptr_t>(ws) % 256) return MSC_ERR_ARG;
+    msc_ctx* c = (msc_ctx*)calloc(1, sizeof(msc_ctx));
+    if (!c) return MSC_ERR_ARG;
+    c->desc = *desc;
+    c->Q = lattice_q(desc->dim);
+    c->logn = ilog2(desc->n);
+    c->sites = desc->dim == 2 ? (size_t)desc->n * desc->n : (size_t)desc->n * desc->n * desc->n;
+    c->elem = desc->precision == MSC_FP64 ? 8 : 4;
+    c->lay = L;
+    c->ws = (unsigned char*)ws;
+    c->stream = (cudaStream_t)stream;
+    // zero the state, the reduction counter and the correction (first lift reads it only if set)
+    if (cudaMemsetAsync(c->ws + L.state, 0, sizeof(DevState), c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->ws + L.counter, 0, 256, c->stream) != cudaSuccess) {
+        free(c);
+        return MSC_ERR_CUDA;
+    }
+    const int n = desc->n;
+    if (desc->precision == MSC_FP64)
+        k_twiddles<double2><<<(n / 2 + 255) / 256, 256, 0, c->stream>>>((double2*)(c->ws + L.tw), n);
+    else
+        k_twiddles<float2><<<(n / 2 + 255) / 256, 256, 0, c->stream>>>((float2*)(c->ws + L.tw), n);
+    if (cudaGetLastError() != cudaSuccess) {
+        free(c);
+        return MSC_ERR_CUDA;
+    }
+    *out = c;
+    return MSC_OK;
+}
+
+void msc_destroy(msc_ctx* c) {
+    if (!c) return;
+    if (c->x_march) cudaGraphExecDestroy(c->x_march);
+    if (c->g_march) cudaGraphDestroy(c->g_march);
+    if (c->x_ex) cudaGraphExecDestroy(c->x_ex);
+    if (c->g_ex) cudaGraphDestroy(c->g_ex);
+    free(c);
+}
+
+int msc_set_params(msc_ctx* c, const msc_params* p) {
+    if (!c || !p) return MSC_ERR_ARG;
+    if (!(p->dt > 0.0) || !(p->eps >= 0.0) || !(p->nu > 0.0) || p->kmax < 1 || p->nmin < 1 ||
+        (p->corrector != 0 && p->corrector != 1) || (p->replay != 0 && p->replay != 1))
+        return MSC_ERR_ARG;
+    // the shadow solve bakes nu into the graph: rebuild if it changes
+    if (c->params_set && p->nu != c->params.nu && c->x_march) {
+        cudaGraphExecDestroy(c->x_march);
+        cudaGraphDestroy(c->g_march);
+        c->x_march = nullptr;
+        c->g_march = nullptr;
+    }
+    c->params = *p;
+    c->params_set = true;
+    k_set_params<<<1, 1, 0, c->stream>>>(at<DevState>(c, c->lay.state), *p);
+    CK(cudaGetLastError());
+    return MSC_OK;
+}
+
+int msc_init_fields(msc_ctx* c, const double* p, const double* u, int on_device) {
+    if (!c || !p || !u) return MSC_ERR_ARG;
+    int rc;
+    if (c->desc.dim == 2)
+        rc = c->desc.precision == MSC_FP64 ? run_init<D2Q9, double>(c, p, u, on_device)
+                                           : run_init<D2Q9, float>(c, p, u, on_device);
+    else
+        rc = c->desc.precision == MSC_FP64 ? run_init<D3Q19, double>(c, p, u, on_device)
+                                           : run_init<D3Q19, float>(c, p, u, on_device);
+    if (rc == MSC_OK) c->fields_set = true;
+    return rc;
+}
+
+int msc_march(msc_ctx* c, int n_steps) {
+    if (!c || n_steps < 0) return MSC_ERR_ARG;
+    if (!c->params_set || !c->fields_set) return MSC_ERR_STATE;
+    if (!c->x_march) {
+        int rc;
+        if (c->desc.dim == 2)
+            rc = c->desc.precision == MSC_FP64 ? build_march_graph<D2Q9, double>(c)
+                                               : build_march_graph<D2Q9, float>(c);
+        else
+            rc = c->desc.precision == MSC_FP64 ? build_march_graph<D3Q19, double>(c)
+                                               : build_march_graph<D3Q19, float>(c);
+        if (rc) return rc;
+    }
+    if (c->params.replay && n_steps > c->desc.max_steps) return MSC_ERR_ARG;
+    k_set_target<<<1, 1, 0, c->stream>>>(at<DevState>(c, c->lay.state), n_steps);
+    CK(cudaGetLastError());
+    CK(cudaGraphLaunch(c->x_march, c->stream));
+    return MSC_OK;
+}
+
+int msc_explicit_march(msc_ctx* c, int n_steps) {
+    if (!c || n_steps < 0) return MSC_ERR_ARG;
+    if (!c->fields_set) return MSC_ERR_STATE;
+    if (n_steps == 0) return MSC_OK;
+    if (c->desc.dim == 2)
+        return c->desc.precision == MSC_FP64 ? run_explicit<D2Q9, double>(c, n_steps)
+                                             : run_explicit<D2Q9, float>(c, n_steps);
+    return c->desc.precision == MSC_FP64 ? run_explicit<D3Q19, double>(c, n_steps)
+                                         : run_explicit<D3Q19, float>(c, n_steps);
+}
+
+int msc_get_stats(msc_ctx* c, msc_stats* out) {
+    if (!c || !out) return MSC_ERR_ARG;
+    DevState s;
+    int rc = read_state(c, &s);
+    if (rc) return rc;
+    out->steps_done = s.steps_done;
+    out->inner_total = s.inner_total;
+    out->steps_in_call = s.steps_in_call;
+    out->last_iters = s.last_iters;
+    out->last_q = s.last_q;
+    out->status = s.status;
+    out->last_R = s.R_last;
+    return MSC_OK;
+}
+
+int msc_read_fields(msc_ctx* c, double* p, double* u, int on_device) {
+    if (!c || !p || !u) return MSC_ERR_ARG;
+    DevState s;
+    int rc = read_state(c, &s);
+    if (rc) return rc;
+    const size_t F = c->desc.dim + 1;
+    const double* m = at<double>(c, c->lay.mbuf) + (size_t)s.m_cur * F * c->sites;
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    CK(cudaMemcpyAsync(p, m, c->sites * 8, kind, c->stream));
+    CK(cudaMemcpyAsync(u, m + c->sites, c->sites * 8 * c->desc.dim, kind, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return MSC_OK;
+}
+
+int msc_read_populations(msc_ctx* c, double* f, int on_device) {
+    if (!c || !f) return MSC_ERR_ARG;
+    DevState s;
+    int rc = read_state(c, &s);
+    if (rc) return rc;
+    const size_t cnt = (size_t)c->Q * c->sites;
+    const unsigned char* src = c->ws + c->lay.fbuf + (size_t)s.slot_fn[0] * c->lay.fstride;
+    if (c->desc.precision == MSC_FP64) {
+        CK(cudaMemcpyAsync(f, src, cnt * 8, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                           c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        return MSC_OK;
+    }
+    if (on_device) return MSC_ERR_ARG;  // FP32 storage: host read-back only
+    float* tmp = (float*)malloc(cnt * 4);
+    if (!tmp) return MSC_ERR_ARG;
+    if (cudaMemcpyAsync(tmp, src, cnt * 4, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess) {
+        free(tmp);
+        return MSC_ERR_CUDA;
+    }
+    for (size_t i = 0; i < cnt; ++i) f[i] = (double)tmp[i];
+    free(tmp);
+    return MSC_OK;
+}
+
+int msc_get_residual_history(msc_ctx* c, double* R, int cap, int* n) {
+    if (!c || !R || !n || cap < 0) return MSC_ERR_ARG;
+    DevState s;
+    int rc = read_state(c, &s);
+    if (rc) return rc;
+    const int64_t total = s.hist_pos;
+    const int64_t keep = total < c->desc.hist_cap ? total : c->desc.hist_cap;
+    const int64_t cnt = keep < cap ? keep : cap;
+    std::vector<double> h(c->desc.hist_cap);
+    CK(cudaMemcpy(h.data(), c->ws + c->lay.hist, (size_t)c->desc.hist_cap * 8, cudaMemcpyDeviceToHost));
+    // oldest kept value first
+    const int64_t first = total - keep;
+    for (int64_t i = 0; i < cnt; ++i) R[i] = h[(first + i) % c->desc.hist_cap];
+    *n = (int)cnt;
+    return MSC_OK;
+}
+
+int msc_get_step_iters(msc_ctx* c, int* iters, int cap, int* n) {
+    if (!c || !iters || !n || cap < 0) return MSC_ERR_ARG;
+    DevState s;
+    int rc = read_state(c, &s);
+    if (rc) return rc;
+    int cnt = s.steps_in_call < c->desc.max_steps ? s.steps_in_call : c->desc.max_steps;
+    if (cnt > cap) cnt = cap;
+    if (cnt > 0) CK(cudaMemcpy(iters, c->ws + c->lay.iters, (size_t)cnt * 4, cudaMemcpyDeviceToHost));
+    *n = cnt;
+    return MSC_OK;
+}
+
+int msc_set_replay_counts(msc_ctx* c, const int* counts, int n) {
+    if (!c || !counts || n < 0 || n > c->desc.max_steps) return MSC_ERR_ARG;
+    for (int i = 0; i < n; ++i)
+        if (counts[i] < 1) return MSC_ERR_ARG;
+    CK(cudaMemcpyAsync(c->ws + c->lay.replay, counts, (size_t)n * 4, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return MSC_OK;
+}
+
+// blob: [magic, dim, n, precision, n_avail, pad] int32 x6, steps_done int64, then n_avail population
+// arrays (storage type, newest first), then m^n and m^{n-1} (double)
+int msc_save_state(msc_ctx* c, void* blob, size_t* bytes) {
+    if (!c || !bytes) return MSC_ERR_ARG;
+    DevState s;
+    int rc = read_state(c, &s);
+    if (rc) return rc;
+    const size_t F = c->desc.dim + 1;
+    const size_t need = 32 + (size_t)s.n_avail * c->lay.fstride + 2 * F * c->sites * 8;
+    if (!blob) {
+        *bytes = need;
+        return MSC_OK;
+    }
+    if (*bytes < need) return MSC_ERR_ARG;
+    unsigned char* b = (unsigned char*)blob;
+    int32_t hdr[6] = {0x4d53434c, c->desc.dim, c->desc.n, c->desc.precision, s.n_avail, 0};
+    memcpy(b, hdr, 24);
+    int64_t sd = s.steps_done;
+    memcpy(b + 24, &sd, 8);
+    size_t o = 32;
+    for (int i = 0; i < s.n_avail; ++i) {
+        CK(cudaMemcpy(b + o, c->ws + c->lay.fbuf + (size_t)s.slot_fn[i] * c->lay.fstride, c->lay.fstride,
+                      cudaMemcpyDeviceToHost));
+        o += c->lay.fstride;
+    }
+    const double* mb = at<double>(c, c->lay.mbuf);
+    CK(cudaMemcpy(b + o, mb + (size_t)s.m_cur * F * c->sites, F * c->sites * 8, cudaMemcpyDeviceToHost));
+    o += F * c->sites * 8;
+    CK(cudaMemcpy(b + o, mb + (size_t)s.m_prev * F * c->sites, F * c->sites * 8, cudaMemcpyDeviceToHost));
+    *bytes = need;
+    return MSC_OK;
+}
+
+int msc_load_state(msc_ctx* c, const void* blob, size_t bytes) {
+    if (!c || !blob || bytes < 32) return MSC_ERR_ARG;
+    const unsigned char* b = (const unsigned char*)blob;
+    int32_t hdr[6];
+    memcpy(hdr, b, 24);
+    if (hdr[0] != 0x4d53434c || hdr[1] != c->desc.dim || hdr[2] != c->desc.n || hdr[3] != c->desc.precision ||
+        hdr[4] < 1 || hdr[4] > 3)
+        return MSC_ERR_ARG;
+    int64_t sd;
+    memcpy(&sd, b + 24, 8);
+    const size_t F = c->desc.dim + 1;
+    const size_t need = 32 + (size_t)hdr[4] * c->lay.fstride + 2 * F * c->sites * 8;
+    if (bytes < need) return MSC_ERR_ARG;
+    CK(cudaStreamSynchronize(c->stream));
+    DevState s;
+    int rc = read_state(c, &s);
+    if (rc) return rc;
+    size_t o = 32;
+    for (int i = 0; i < hdr[4]; ++i) {
+        CK(cudaMemcpy(c->ws + c->lay.fbuf + (size_t)i * c->lay.fstride, b + o, c->lay.fstride,
+                      cudaMemcpyHostToDevice));
+        o += c->lay.fstride;
+    }
+    double* mb = at<double>(c, c->lay.mbuf);
+    CK(cudaMemcpy(mb, b + o, F * c->sites * 8, cudaMemcpyHostToDevice));
+    o += F * c->sites * 8;
+    CK(cudaMemcpy(mb + F * c->sites, b + o, F * c->sites * 8, cudaMemcpyHostToDevice));
+    s.n_avail = hdr[4];
+    s.slot_fn[0] = 0;
+    s.slot_fn[1] = 1;
+    s.slot_fn[2] = 2;
+    s.m_cur = 0;
+    s.m_prev = 1;
+    s.steps_done = sd;
+    s.status = MSC_OK;
+    CK(cudaMemcpy(c->ws + c->lay.state, &s, sizeof(DevState), cudaMemcpyHostToDevice));
+    c->fields_set = true;
+    return MSC_OK;
+}
+
+// ---- stage entry points ------------------------------------------------------------------------
+
+size_t msc_stage_scratch_bytes(int dim, int n, int precision) {
+    if (!valid_lattice(dim, n, precision)) return 0;
+    size_t o = 0;
+    o = align_up(o + 256, 256);                                  // counter
+    o = align_up(o + (size_t)sweep_blocks_for(dim, n, precision) * 8, 256);  // partials
+    o = align_up(o + (size_t)(n / 2) * (precision == MSC_FP64 ? 16 : 8), 256);  // twiddles
+    o = align_up(o + spec_bytes(dim, n, precision), 256);         // half spectrum
+    return o;
+}
+
+}  // extern "C"
+
+namespace {
+struct StageScratch {
+    unsigned int* counter;
+    double* partial;
+    void* tw;
+    void* spec;
+};
+StageScratch stage_scratch(int dim, int n, int precision, void* base) {
+    StageScratch s;
+    unsigned char* b = (unsigned char*)base;
+    size_t o = 0;
+    s.counter = (unsigned int*)(b + o);
+    o = align_up(o + 256, 256);
+    s.partial = (double*)(b + o);
+    o = align_up(o + (size_t)sweep_blocks_for(dim, n, precision) * 8, 256);
+    s.tw = b + o;
+    o = align_up(o + (size_t)(n / 2) * (precision == MSC_FP64 ? 16 : 8), 256);
+    s.spec = b + o;
+    return s;
+}
+
+template <typename T>
+int stage_sweep(int dim, int n, double a, const void* fin, const void* dm, const void* h, void* fout,
+                void* pr, double* sumsq, void* scratch, cudaStream_t stream) {
+    StageScratch S = stage_scratch(dim, n, sizeof(T) == 8 ? MSC_FP64 : MSC_FP32, scratch);
+    CK(cudaMemsetAsync(S.counter, 0, 4, stream));
+    if (dim == 2) {
+        Sweep2Args<T> A;
+        memset(&A, 0, sizeof(A));
+        const Sweep2Geom g = sweep2_geometry(n);
+        A.fin = (const T*)fin;
+        A.dm = (const T*)dm;
+        A.h = (const T*)h;
+        A.fout = (T*)fout;
+        A.pr = (T*)pr;
+        A.a = a;
+        A.lift = dm != nullptr;
+        A.sumsq_out = sumsq;
+        A.partial = S.partial;
+        A.counter = S.counter;
+        A.n = n;
+        A.nstrips = g.nstrips;
+        A.hb = g.hb;
+        A.nrowblk = g.nrowblk;
+        k_sweep2<T, false, false><<<g.blocks, kSweepWarps * 32, 0, stream>>>(A);
+    } else {
+        if (set_sweep3_smem_limits<T>(n) != 0) return MSC_ERR_CUDA;
+        Sweep3Args<T> A;
+        memset(&A, 0, sizeof(A));
+        A.g = sweep3_geometry(n, sizeof(T));
+        A.fin = (const T*)fin;
+        A.dm = (const T*)dm;
+        A.h = (const T*)h;
+        A.fout = (T*)fout;
+        A.pr = (T*)pr;
+        A.a = a;
+        A.lift = dm != nullptr;
+        A.sumsq_out = sumsq;
+        A.partial = S.partial;
+        A.counter = S.counter;
+        A.n = n;
+        k_sweep3<T, false, false><<<A.g.blocks, A.g.threads, A.g.smem, stream>>>(A);
+    }
+    CK(cudaGetLastError());
+    return MSC_OK;
+}
+
+template <typename T>
+int stage_shadow(int dim, int n, double a, double nu, const void* pr, void* dm, void* scratch,
+                 cudaStream_t stream) {
+    using C = typename Cplx<T>::type;
+    StageScratch S = stage_scratch(dim, n, sizeof(T) == 8 ? MSC_FP64 : MSC_FP32, scratch);
+    k_twiddles<C><<<(n / 2 + 255) / 256, 256, 0, stream>>>((C*)S.tw, n);
+    CK(cudaGetLastError());
+    int rc = set_smem_limits<T>(dim, n);
+    if (rc) return rc;
+    if (dim == 2) {
+        Spec2Args<T> A;
+        memset(&A, 0, sizeof(A));
+        A.pr = (const T*)pr;
+        A.spec = (C*)S.spec;
+        A.dm = (T*)dm;
+        A.tw = (const C*)S.tw;
+        A.n = n;
+        A.logn = ilog2(n);
+        A.nf = 3;
+        A.rows = n;
+        A.a = a;
+        A.nu = nu;
+        A.st = nullptr;
+        k_rowfft_fwd<T><<<spec2_row_blocks(n), kFftThreads, spec2_row_smem<T>(n), stream>>>(A);
+        k_colsolve<T><<<n / 4 + 1, kFftThreads, spec2_col_smem<T>(n), stream>>>(A);
+        k_rowfft_inv<T><<<spec2_row_blocks(n), kFftThreads, spec2_row_smem<T>(n), stream>>>(A);
+        CK(cudaGetLastError());
+        return MSC_OK;
+    }
+    return launch_spectral3<T>(n, ilog2(n), a, nu, (const T*)pr, (C*)S.spec, (T*)dm, (const C*)S.tw, stream);
+}
+}  // namespace
+
+extern "C" {
+
+int msc_sweep(int dim, int n, int precision, double a, const void* f_in, const void* dm, const void* h,
+              void* f_out, void* pr_out, double* sumsq_out, void* scratch, size_t scratch_bytes,
+              void* stream) {
+    if (!valid_lattice(dim, n, precision) || !f_in || !h || !f_out || !pr_out || !sumsq_out || !scratch ||
+        f_in == f_out || scratch_bytes < msc_stage_scratch_bytes(dim, n, precision) || !(a >= 0.0))
+        return MSC_ERR_ARG;
+    if (precision == MSC_FP64)
+        return stage_sweep<double>(dim, n, a, f_in, dm, h, f_out, pr_out, sumsq_out, scratch, (cudaStream_t)stream);
+    return stage_sweep<float>(dim, n, a, f_in, dm, h, f_out, pr_out, sumsq_out, scratch, (cudaStream_t)stream);
+}
+
+int msc_shadow_solve(int dim, int n, int precision, double a, double nu, const void* pr, void* dm,
+                     void* scratch, size_t scratch_bytes, void* stream) {
+    if (!valid_lattice(dim, n, precision) || !pr || !dm || pr == dm || !scratch ||
+        scratch_bytes < msc_stage_scratch_bytes(dim, n, precision) || !(a > 0.0) || !(nu > 0.0))
+        return MSC_ERR_ARG;
+    if (precision == MSC_FP64)
+        return stage_shadow<double>(dim, n, a, nu, pr, dm, scratch, (cudaStream_t)stream);
+    return stage_shadow<float>(dim, n, a, nu, pr, dm, scratch, (cudaStream_t)stream);
+}
+
+int msc_equilibrium(int dim, int n, int precision, const double* p, const double* u, void* f_out,
+                    void* stream) {
+    if (!valid_lattice(dim, n, precision) || !p || !u || !f_out) return MSC_ERR_ARG;
+    const size_t sites = dim == 2 ? (size_t)n * n : (size_t)n * n * n;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (dim == 2) {
+        if (precision == MSC_FP64)
+            k_equilibrium<D2Q9, double><<<grid_for(sites), kFieldThreads, 0, s>>>(p, u, (double*)f_out, sites);
+        else
+            k_equilibrium<D2Q9, float><<<grid_for(sites), kFieldThreads, 0, s>>>(p, u, (float*)f_out, sites);
+    } else {
+        if (precision == MSC_FP64)
+            k_equilibrium<D3Q19, double><<<grid_for(sites), kFieldThreads, 0, s>>>(p, u, (double*)f_out, sites);
+        else
+            k_equilibrium<D3Q19, float><<<grid_for(sites), kFieldThreads, 0, s>>>(p, u, (float*)f_out, sites);
+    }
+    CK(cudaGetLastError());
+    return MSC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,289 @@
+// D2Q9 fused collide-stream sweep (Eqs. macro-reconstruct, source-moments, source-distribution,
+// collision-operating, sweep, residual) and the explicit LBM step (same kernel, no source).
+//
+// Design: one warp owns a strip of 32 consecutive x columns (30 output columns plus one halo
+// column on each side) and marches down HB output rows of that strip.  For every row j it loads
+// the 9 populations (plus h and the lifted correction) of its 32 columns with coalesced loads,
+// forms the trial populations, the reconstructed field and the operating-point collision
+// C = f_eq + Phi/2 at every column, and pushes the 9 post-collision values to their
+// destinations x + c_k: x-shifts by warp shuffles, y-shifts by keeping the partial output rows
+// j-1, j, j+1 in registers.  Row j-1 is complete after row j is collided, so the residual
+// r = f_T - f, its moments P r and sum r^2 are formed there and the row is stored.  No shared
+// memory and no block barriers in the main loop; each population is read once from memory
+// except the two halo columns per strip and the two halo rows per row block.
+#pragma once
+
+#include "common.cuh"
+
+namespace msc {
+
+constexpr int kSweepWarps = 4;          // warps (strips) per block
+constexpr int kStripOut = 30;           // output columns per warp strip
+
+template <typename T>
+struct Sweep2Args {
+    // stateless mode: explicit pointers; graph mode: pointers resolved from the device state
+    const T* fin;
+    const T* dm;
+    const T* h;
+    T* fout;
+    T* pr;
+    double a;
+    int lift;
+    double* sumsq_out;
+    // reduction scratch
+    double* partial;
+    unsigned int* counter;
+    // geometry
+    int n, nstrips, hb, nrowblk;
+    // graph mode
+    DevState* st;
+    T* fbase;
+    size_t fstride;  // elements
+    double* hist;
+    int hist_cap;
+    const int* replay_counts;
+    int max_steps;
+    cudaGraphConditionalHandle h_iter, h_corr;
+    // explicit graph mode: 0 = a->b, 1 = b->a; ex_count: decrement the pair counter
+    int ex_dir, ex_count;
+    cudaGraphConditionalHandle h_ex;
+};
+
+// Decide acceptance after the residual norm of inner iteration l is known (Algorithm 1).
+__device__ inline void march_after_sweep(DevState* st, double total, double qsites, double* hist,
+                                         int hist_cap, const int* replay_counts, int max_steps,
+                                         cudaGraphConditionalHandle h_iter,
+                                         cudaGraphConditionalHandle h_corr) {
+    const double R = sqrt(total / qsites);
+    const int ell = st->iter + 1;
+    st->iter = ell;
+    st->inner_total += 1;
+    hist[st->hist_pos % hist_cap] = R;
+    st->hist_pos += 1;
+    st->R_last = R;
+    // the sweep output becomes the base of the next trial
+    const int t = st->slot_cur;
+    st->slot_cur = st->slot_nxt;
+    st->slot_nxt = t;
+    int cont = 0, corr = 0;
+    bool accept;
+    if (st->replay) {
+        const int idx = st->steps_in_call;
+        accept = idx < max_steps && ell == replay_counts[idx];
+    } else {
+        accept = ell >= st->nmin && R < st->eps;  // a NaN never passes
+    }
+    if (!isfinite(R)) {
+        st->status = MSC_ERR_NONFINITE;
+    } else if (accept) {
+        st->accepted = 1;
+    } else if (ell >= st->kmax) {
+        st->status = MSC_ERR_NONCONVERGED;
+    } else {
+        cont = 1;
+        corr = st->corrector;
+    }
+    st->lift = corr;
+    cudaGraphSetConditional(h_iter, cont);
+    cudaGraphSetConditional(h_corr, corr);
+}
+
+template <typename T, bool EXPLICIT, bool GRAPH>
+__global__ void __launch_bounds__(kSweepWarps * 32) k_sweep2(Sweep2Args<T> A) {
+    using L = D2Q9;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int n = A.n;
+    const int nmask = n - 1;
+    const size_t NN = (size_t)n * n;
+
+    const T* fin = A.fin;
+    const T* dm = A.dm;
+    const T* hh = A.h;
+    T* fout = A.fout;
+    T* pr = A.pr;
+    T a = (T)A.a;
+    T inv = (T)(1.0 / (1.0 + A.a / 2.0));
+    int lift = A.lift;
+    if (GRAPH) {
+        const volatile DevState* vs = A.st;
+        if (EXPLICIT) {
+            const int sa = vs->ex_a, sb = vs->ex_b;
+            fin = A.fbase + (size_t)(A.ex_dir ? sb : sa) * A.fstride;
+            fout = A.fbase + (size_t)(A.ex_dir ? sa : sb) * A.fstride;
+            if (A.ex_count && blockIdx.x == 0 && threadIdx.x == 0) {
+                DevState* st = A.st;
+                const int left = st->ex_pairs_left - 1;
+                st->ex_pairs_left = left;
+                cudaGraphSetConditional(A.h_ex, left > 0 ? 1u : 0u);
+            }
+        } else {
+            fin = A.fbase + (size_t)vs->slot_cur * A.fstride;
+            fout = A.fbase + (size_t)vs->slot_nxt * A.fstride;
+            const double ad = vs->a;
+            a = (T)ad;
+            inv = (T)(1.0 / (1.0 + ad / 2.0));
+            lift = vs->lift;
+        }
+    }
+
+    const int unit = blockIdx.x * kSweepWarps + warp;
+    double ssq = 0.0;
+    if (unit < A.nstrips * A.nrowblk) {  // warp-uniform
+        const int strip = unit % A.nstrips;
+        const int rb = unit / A.nstrips;
+        const int x0 = strip * kStripOut;
+        const int y0 = rb * A.hb;
+        const int x = (x0 - 1 + lane) & nmask;
+        const bool out_lane = lane >= 1 && lane <= kStripOut && (x0 + lane - 1) < n;
+
+        T Ar[9], Br[9], ftp[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) { Ar[k] = T(0); Br[k] = T(0); ftp[k] = T(0); }
+        T ssq_f = T(0);
+
+        for (int j = y0 - 1; j <= y0 + A.hb; ++j) {
+            const int y = j & nmask;
+            const size_t idx = (size_t)y * n + x;
+            T f[9];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) f[k] = fin[k * NN + idx];
+            if (!EXPLICIT && lift) {  // trial f = f_T,prev + E dm   (Eq. lift)
+                const T dp = dm[idx], dux = dm[NN + idx], duy = dm[2 * NN + idx];
+#pragma unroll
+                for (int k = 0; k < 9; ++k)
+                    f[k] += (T)L::w(k) * (dp + T(3) * (T(L::cx(k)) * dux + T(L::cy(k)) * duy));
+            }
+            // moments (Eq. moments)
+            T rho = T(0), jx = T(0), jy = T(0);
+#pragma unroll
+            for (int k = 0; k < 9; ++k) {
+                rho += f[k];
+                if (L::cx(k)) jx += T(L::cx(k)) * f[k];
+                if (L::cy(k)) jy += T(L::cy(k)) * f[k];
+            }
+            T p, ux, uy, s0 = T(0), sx = T(0), sy = T(0);
+            if (EXPLICIT) {
+                p = rho; ux = jx; uy = jy;
+            } else {  // half-source reconstruction and source moments (Eqs. macro-reconstruct, source-moments)
+                const T h0 = hh[idx], h1 = hh[NN + idx], h2 = hh[2 * NN + idx];
+                p = (rho + h0 * T(0.5)) * inv;
+                ux = (jx + h1 * T(0.5)) * inv;
+                uy = (jy + h2 * T(0.5)) * inv;
+                s0 = h0 - a * p;
+                sx = h1 - a * ux;
+                sy = h2 - a * uy;
+            }
+            // operating-point collision C = f_eq + Phi/2 (Eq. collision-operating)
+            const T A0 = p + T(0.5) * s0 - T(1.5) * (ux * ux + uy * uy) - T(1.5) * (ux * sx + uy * sy);
+            T C[9];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) {
+                const T cu = T(L::cx(k)) * ux + T(L::cy(k)) * uy;
+                const T cs = T(L::cx(k)) * sx + T(L::cy(k)) * sy;
+                C[k] = (T)L::w(k) * (A0 + T(3) * cu + T(1.5) * cs + T(4.5) * cu * (cu + cs));
+            }
+            // push streaming in x: value for column x comes from column x - c_kx
+#pragma unroll
+            for (int k = 0; k < 9; ++k) {
+                if (L::cx(k) == 1) C[k] = __shfl_up_sync(0xffffffffu, C[k], 1);
+                else if (L::cx(k) == -1) C[k] = __shfl_down_sync(0xffffffffu, C[k], 1);
+            }
+            // row j-1 receives the c_y = -1 directions and is complete
+#pragma unroll
+            for (int k = 0; k < 9; ++k)
+                if (L::cy(k) == -1) Ar[k] = C[k];
+            if (j - 1 >= y0 && out_lane) {
+                const size_t oidx = (size_t)((j - 1) & nmask) * n + x;
+#pragma unroll
+                for (int k = 0; k < 9; ++k) fout[k * NN + oidx] = Ar[k];
+                if (!EXPLICIT) {
+                    T r0 = T(0), r1 = T(0), r2 = T(0), rr = T(0);
+#pragma unroll
+                    for (int k = 0; k < 9; ++k) {
+                        const T r = Ar[k] - ftp[k];
+                        r0 += r;
+                        if (L::cx(k)) r1 += T(L::cx(k)) * r;
+                        if (L::cy(k)) r2 += T(L::cy(k)) * r;
+                        rr += r * r;
+                    }
+                    pr[oidx] = r0;
+                    pr[NN + oidx] = r1;
+                    pr[2 * NN + oidx] = r2;
+                    ssq_f += rr;
+                    if (((j - y0) & 7) == 0) { ssq += (double)ssq_f; ssq_f = T(0); }
+                }
+            }
+            // rotate: row j keeps its c_y = 0 values and the c_y = +1 values of row j-1
+#pragma unroll
+            for (int k = 0; k < 9; ++k) {
+                if (L::cy(k) == 0) Ar[k] = C[k];
+                else if (L::cy(k) == 1) { Ar[k] = Br[k]; Br[k] = C[k]; }
+                ftp[k] = f[k];
+            }
+        }
+        ssq += (double)ssq_f;
+    }
+    if (EXPLICIT) return;
+
+    // ---- residual norm: block partials, last block reduces in a fixed order ----
+    __shared__ double wsum[kSweepWarps];
+    __shared__ bool is_last;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) ssq += __shfl_xor_sync(0xffffffffu, ssq, off);
+    if (lane == 0) wsum[warp] = ssq;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double b = 0.0;
+        for (int w = 0; w < kSweepWarps; ++w) b += wsum[w];
+        A.partial[blockIdx.x] = b;
+        __threadfence();
+        const unsigned int t = atomicAdd(A.counter, 1u);
+        is_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    double s = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) s += __ldcg(A.partial + i);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    __syncthreads();
+    if (lane == 0) wsum[warp] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double total = 0.0;
+        for (int w = 0; w < kSweepWarps; ++w) total += wsum[w];
+        *A.counter = 0u;
+        if (GRAPH) {
+            march_after_sweep(A.st, total, 9.0 * (double)NN, A.hist, A.hist_cap, A.replay_counts,
+                              A.max_steps, A.h_iter, A.h_corr);
+        } else {
+            *A.sumsq_out = total;
+        }
+    }
+}
+
+struct Sweep2Geom {
+    int nstrips, hb, nrowblk, blocks;
+};
+
+inline Sweep2Geom sweep2_geometry(int n) {
+    Sweep2Geom g;
+    g.nstrips = (n + kStripOut - 1) / kStripOut;
+    // largest row block (<= 64, dividing n) that still gives enough warps to fill the GPU
+    const int target_units = 148 * 16;
+    int hb = 4;
+    for (int c = 64; c >= 4; c >>= 1) {
+        if (c <= n && g.nstrips * (n / c) >= target_units) { hb = c; break; }
+    }
+    if (hb > n) hb = n;
+    g.hb = hb;
+    g.nrowblk = n / hb;
+    const int units = g.nstrips * g.nrowblk;
+    g.blocks = (units + kSweepWarps - 1) / kSweepWarps;
+    return g;
+}
+
+}  // namespace msc

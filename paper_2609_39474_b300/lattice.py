@@ -1,0 +1,183 @@
+"""Python front end of the MSC-LBM library: torch tensors in, C ABI calls out.
+
+PyTorch provides device memory (the context workspace and field buffers) and the CUDA stream;
+every computation runs in libmsclbm.so.  Field layout: p_hat[(z,) y, x], u[alpha, (z,) y, x],
+populations f[k, (z,) y, x], float64 on the host side of the API.
+"""
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+_DT = {"fp64": (L.MSC_FP64, torch.float64), "fp32": (L.MSC_FP32, torch.float32)}
+
+
+def _ptr(t: torch.Tensor) -> int:
+    return t.data_ptr()
+
+
+def _stream(stream) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def precision_code(precision: str) -> int:
+    return _DT[precision][0]
+
+
+def storage_dtype(precision: str) -> torch.dtype:
+    return _DT[precision][1]
+
+
+class MscLattice:
+    """One periodic D2Q9 (dim=2) or D3Q19 (dim=3) lattice with its device-resident march state."""
+
+    def __init__(self, dim: int, n: int, precision: str = "fp64", max_steps: int = 1 << 16,
+                 hist_cap: int = 1 << 16, device: str = "cuda", stream=None):
+        self.dim, self.n, self.precision = dim, n, precision
+        self.Q = 9 if dim == 2 else 19
+        self.sites = n ** dim
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.desc = L.LatticeDesc(dim, n, precision_code(precision), max_steps, hist_cap)
+        nbytes = L.lib.msc_workspace_bytes(ctypes.byref(self.desc))
+        if nbytes == 0:
+            raise ValueError(f"unsupported lattice dim={dim} n={n} precision={precision}")
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self._ctx = ctypes.c_void_p()
+        L.check(L.lib.msc_create(ctypes.byref(self._ctx), ctypes.byref(self.desc), _ptr(self.workspace),
+                                 nbytes, self.stream.cuda_stream), "msc_create")
+        self.max_steps, self.hist_cap = max_steps, hist_cap
+
+    @property
+    def grid(self):
+        return (self.n,) * self.dim
+
+    def close(self):
+        if self._ctx:
+            L.lib.msc_destroy(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, dt: float, eps: float = 1e-8, nu: float = 1.0 / 6.0, kmax: int = 300,
+                   nmin=None, corrector: bool = True, replay: bool = False):
+        if nmin is None:
+            nmin = 2 if self.dim == 2 else 1
+        p = L.Params(nu, dt, eps, kmax, nmin, int(corrector), int(replay))
+        L.check(L.lib.msc_set_params(self._ctx, ctypes.byref(p)), "msc_set_params")
+
+    def init_fields(self, p_hat, u):
+        """f^0 = f_eq(p_hat, u); accepts numpy arrays or torch tensors (host or device), float64."""
+        p_t = torch.as_tensor(np.asarray(p_hat) if not torch.is_tensor(p_hat) else p_hat, dtype=torch.float64)
+        u_t = torch.as_tensor(np.asarray(u) if not torch.is_tensor(u) else u, dtype=torch.float64)
+        if tuple(p_t.shape) != self.grid or tuple(u_t.shape) != (self.dim,) + self.grid:
+            raise ValueError("field shapes do not match the lattice")
+        on_dev = int(p_t.is_cuda)
+        if on_dev != int(u_t.is_cuda):
+            raise ValueError("p_hat and u must be on the same side")
+        p_t, u_t = p_t.contiguous(), u_t.contiguous()
+        self._init_keep = (p_t, u_t)  # keep the sources alive until the async copy has run
+        L.check(L.lib.msc_init_fields(self._ctx, _ptr(p_t), _ptr(u_t), on_dev), "msc_init_fields")
+
+    def march(self, n_steps: int):
+        L.check(L.lib.msc_march(self._ctx, int(n_steps)), "msc_march")
+
+    def explicit_march(self, n_steps: int):
+        L.check(L.lib.msc_explicit_march(self._ctx, int(n_steps)), "msc_explicit_march")
+
+    def stats(self) -> dict:
+        s = L.Stats()
+        L.check(L.lib.msc_get_stats(self._ctx, ctypes.byref(s)), "msc_get_stats")
+        return {k: getattr(s, k) for k, _ in L.Stats._fields_}
+
+    def fields(self, on_device: bool = True):
+        """(p_hat, u) of the accepted state m^n, float64."""
+        dev = self.device if on_device else torch.device("cpu")
+        p = torch.empty(self.grid, dtype=torch.float64, device=dev)
+        u = torch.empty((self.dim,) + self.grid, dtype=torch.float64, device=dev)
+        L.check(L.lib.msc_read_fields(self._ctx, _ptr(p), _ptr(u), int(on_device)), "msc_read_fields")
+        return p, u
+
+    def populations(self) -> np.ndarray:
+        f = np.empty((self.Q,) + self.grid, dtype=np.float64)
+        L.check(L.lib.msc_read_populations(self._ctx, f.ctypes.data, 0), "msc_read_populations")
+        return f
+
+    def residual_history(self) -> np.ndarray:
+        out = np.empty(self.hist_cap, dtype=np.float64)
+        n = ctypes.c_int()
+        L.check(L.lib.msc_get_residual_history(self._ctx, out.ctypes.data, self.hist_cap, ctypes.byref(n)),
+                "msc_get_residual_history")
+        return out[:n.value].copy()
+
+    def step_iters(self) -> np.ndarray:
+        out = np.empty(self.max_steps, dtype=np.int32)
+        n = ctypes.c_int()
+        L.check(L.lib.msc_get_step_iters(self._ctx, out.ctypes.data, self.max_steps, ctypes.byref(n)),
+                "msc_get_step_iters")
+        return out[:n.value].copy()
+
+    def set_replay_counts(self, counts):
+        c = np.ascontiguousarray(np.asarray(counts, dtype=np.int32))
+        L.check(L.lib.msc_set_replay_counts(self._ctx, c.ctypes.data, len(c)), "msc_set_replay_counts")
+
+    def save_state(self) -> bytes:
+        n = ctypes.c_size_t()
+        L.check(L.lib.msc_save_state(self._ctx, None, ctypes.byref(n)), "msc_save_state")
+        buf = ctypes.create_string_buffer(n.value)
+        L.check(L.lib.msc_save_state(self._ctx, buf, ctypes.byref(n)), "msc_save_state")
+        return buf.raw[:n.value]
+
+    def load_state(self, blob: bytes):
+        L.check(L.lib.msc_load_state(self._ctx, blob, len(blob)), "msc_load_state")
+
+
+# ---- stage calls ---------------------------------------------------------------------------------
+
+class StageScratch:
+    def __init__(self, dim: int, n: int, precision: str, device="cuda"):
+        self.nbytes = L.lib.msc_stage_scratch_bytes(dim, n, precision_code(precision))
+        if self.nbytes == 0:
+            raise ValueError("unsupported lattice")
+        self.buf = torch.empty(self.nbytes, dtype=torch.uint8, device=device)
+
+
+def sweep(dim: int, n: int, precision: str, a: float, f_in: torch.Tensor, h: torch.Tensor,
+          dm: torch.Tensor = None, scratch: StageScratch = None, stream=None):
+    """One fused sweep through msc_sweep: returns (f_out, P r, sum r^2 as a device double)."""
+    dt = storage_dtype(precision)
+    for t in (f_in, h) + ((dm,) if dm is not None else ()):
+        if t.dtype != dt or not t.is_cuda or not t.is_contiguous():
+            raise ValueError("stage inputs must be contiguous device tensors of the storage type")
+    scratch = scratch or StageScratch(dim, n, precision, f_in.device)
+    f_out = torch.empty_like(f_in)
+    pr = torch.empty((dim + 1,) + (n,) * dim, dtype=dt, device=f_in.device)
+    ssq = torch.empty((), dtype=torch.float64, device=f_in.device)
+    L.check(L.lib.msc_sweep(dim, n, precision_code(precision), float(a), _ptr(f_in),
+                            _ptr(dm) if dm is not None else None, _ptr(h), _ptr(f_out), _ptr(pr), _ptr(ssq),
+                            _ptr(scratch.buf), scratch.nbytes, _stream(stream)), "msc_sweep")
+    return f_out, pr, ssq
+
+
+def shadow_solve(dim: int, n: int, precision: str, a: float, nu: float, pr: torch.Tensor,
+                 scratch: StageScratch = None, stream=None):
+    """delta m = F^-1[chi H^-1 F[P r]] through msc_shadow_solve."""
+    scratch = scratch or StageScratch(dim, n, precision, pr.device)
+    dm = torch.empty_like(pr)
+    L.check(L.lib.msc_shadow_solve(dim, n, precision_code(precision), float(a), float(nu), _ptr(pr), _ptr(dm),
+                                   _ptr(scratch.buf), scratch.nbytes, _stream(stream)), "msc_shadow_solve")
+    return dm
+
+
+def equilibrium(dim: int, n: int, precision: str, p_hat: torch.Tensor, u: torch.Tensor, stream=None):
+    f = torch.empty((9 if dim == 2 else 19,) + (n,) * dim, dtype=storage_dtype(precision), device=p_hat.device)
+    L.check(L.lib.msc_equilibrium(dim, n, precision_code(precision), _ptr(p_hat.contiguous()),
+                                  _ptr(u.contiguous()), _ptr(f), _stream(stream)), "msc_equilibrium")
+    return f

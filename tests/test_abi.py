@@ -1,0 +1,69 @@
+"""The C-ABI library loads and exports every entry point the header declares (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2609_39474_b300 import build as B
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "msclbm.h")
+
+
+@pytest.fixture(scope="module")
+def L():
+    B.build()
+    from paper_2609_39474_b300 import _lib
+    return _lib
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(msc_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = declared_functions()
+    assert len(names) >= 20
+    for name in names:
+        assert hasattr(L.lib, name), name
+    assert sorted(L.exported_names()) == names  # the binding covers exactly the header
+
+
+def test_header_compiles_as_plain_c(tmp_path):
+    src = tmp_path / "t.c"
+    src.write_text('#include "msclbm.h"\nint main(void){ msc_lattice_desc d = {2, 64, MSC_FP64, 1, 1};'
+                   ' return (int)msc_workspace_bytes(&d) == 0; }\n')
+    import subprocess
+    r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-c", str(src), "-I", os.path.dirname(HEADER),
+                        "-o", str(tmp_path / "t.o")], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+
+
+def test_workspace_and_scratch_sizes(L):
+    ok = L.LatticeDesc(2, 64, L.MSC_FP64, 16, 16)
+    n64 = L.lib.msc_workspace_bytes(ctypes.byref(ok))
+    # five population arrays of 9 x 64^2 doubles dominate
+    assert n64 > 5 * 9 * 64 * 64 * 8
+    f32 = L.LatticeDesc(2, 64, L.MSC_FP32, 16, 16)
+    assert L.lib.msc_workspace_bytes(ctypes.byref(f32)) < n64
+    for bad in [L.LatticeDesc(2, 48, 0, 1, 1), L.LatticeDesc(2, 4, 0, 1, 1), L.LatticeDesc(4, 64, 0, 1, 1),
+                L.LatticeDesc(2, 64, 7, 1, 1), L.LatticeDesc(2, 64, 0, 0, 1), L.LatticeDesc(2, 8192, 0, 1, 1),
+                L.LatticeDesc(3, 512, 1, 1, 1), L.LatticeDesc(3, 256, 0, 1, 1)]:
+        assert L.lib.msc_workspace_bytes(ctypes.byref(bad)) == 0
+    assert L.lib.msc_workspace_bytes(ctypes.byref(L.LatticeDesc(3, 128, 1, 1, 1))) > 0
+    assert L.lib.msc_stage_scratch_bytes(2, 256, L.MSC_FP32) > 0
+    assert L.lib.msc_stage_scratch_bytes(2, 100, L.MSC_FP32) == 0
+
+
+def test_argument_errors_need_no_device(L):
+    ctx = ctypes.c_void_p()
+    d = L.LatticeDesc(2, 64, L.MSC_FP64, 16, 16)
+    assert L.lib.msc_create(ctypes.byref(ctx), ctypes.byref(d), None, 0, None) == L.MSC_ERR_ARG
+    assert L.lib.msc_create(None, ctypes.byref(d), None, 0, None) == L.MSC_ERR_ARG
+    assert L.lib.msc_sweep(2, 64, 0, 0.1, None, None, None, None, None, None, None, 0, None) == L.MSC_ERR_ARG
+    assert L.lib.msc_shadow_solve(2, 64, 0, 0.1, 1 / 6, None, None, None, 0, None) == L.MSC_ERR_ARG
+    assert L.lib.msc_march(None, 1) == L.MSC_ERR_ARG
+    assert L.strerror(L.MSC_ERR_NONCONVERGED).startswith("physical step")
+    assert L.strerror(99) == "unknown status"

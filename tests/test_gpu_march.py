@@ -1,0 +1,204 @@
+"""GPU parity of the device-resident march (Algorithm 1, Picard, explicit LBM) against the FP64
+oracle, through the C ABI.  Parity runs in replay mode: the oracle's accepted inner counts are
+forced on the GPU so that a residual within rounding of eps cannot change the iteration path."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import kinetics as OK
+from oracle import march as OM
+from oracle.lattice import lattice_for_dim
+from workloads.fields import random_phase, tgv2d, tgv3d
+from workloads.metrics import nint
+from tests.gpu_helpers import host, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+def _lattice(dim, n, precision, **kw):
+    from paper_2609_39474_b300.lattice import MscLattice
+    return MscLattice(dim, n, precision, **kw)
+
+
+def _replay_run(dim, n, precision, p, u, prm: OM.MarchParams, counts, corrector=True):
+    L = _lattice(dim, n, precision)
+    L.set_params(dt=prm.dt, eps=prm.eps, nu=prm.nu, kmax=prm.kmax, nmin=prm.nmin, corrector=corrector,
+                 replay=True)
+    L.set_replay_counts(counts)
+    L.init_fields(p, u)
+    L.march(len(counts))
+    return L
+
+
+def test_config1_tgv_fp64_replay_parity():
+    # D2Q9 N = 64, FP64, Taylor-Green at Re = 1, T_end = nint(0.05 N^2 / nu) = 1229, S = 38 steps
+    N, T_end = 64, nint(0.05 * 64 ** 2 * 6)
+    S = nint(T_end / 32)
+    prm = OM.MarchParams(dt=T_end / S, eps=1e-10)
+    p, u = tgv2d(N, 1.0)
+    st = OM.init_state(lattice_for_dim(2), p, u)
+    recs = OM.march(st, prm, S)
+    counts = [r.iters for r in recs]
+    L = _replay_run(2, N, "fp64", p, u, prm, counts)
+    s = L.stats()
+    assert s["status"] == 0 and s["steps_done"] == S and s["inner_total"] == sum(counts)
+    ph, uu = L.fields(on_device=False)
+    assert rel_l2(uu.numpy(), st.m_n[1:]) < 1e-12
+    assert rel_l2(ph.numpy(), st.m_n[0]) < 1e-10
+    assert rel_l2(L.populations(), st.f) < 1e-12
+    # the residual history follows the oracle's
+    R = L.residual_history()
+    Ro = np.concatenate([r.residuals for r in recs])
+    assert len(R) == len(Ro) and rel_l2(R, Ro) < 1e-9
+    assert list(L.step_iters()) == counts
+
+
+def test_free_running_march_follows_the_oracle():
+    N = 64
+    p, u = random_phase(N, 2, 1.0, seed=11, kmax=8)
+    prm = OM.MarchParams(dt=40.0, eps=1e-9)
+    st = OM.init_state(lattice_for_dim(2), p, u)
+    recs = OM.march(st, prm, 12)
+    L = _lattice(2, N, "fp64")
+    L.set_params(dt=prm.dt, eps=prm.eps)
+    L.init_fields(p, u)
+    L.march(12)
+    s = L.stats()
+    assert s["status"] == 0 and s["steps_done"] == 12
+    it = L.step_iters()
+    assert np.mean(it == np.array([r.iters for r in recs])) >= 0.9
+    assert rel_l2(host(L.fields()[1]), st.m_n[1:]) < 1e-7  # within the tolerance-level path noise
+
+
+def test_picard_replay_parity_fp64():
+    N = 32
+    p, u = tgv2d(N, 1.0)
+    prm = OM.MarchParams(dt=16.0, eps=1e-11, corrector=False, kmax=2000)
+    st = OM.init_state(lattice_for_dim(2), p, u)
+    recs = OM.march(st, prm, 4)
+    L = _replay_run(2, N, "fp64", p, u, prm, [r.iters for r in recs], corrector=False)
+    assert rel_l2(host(L.fields()[1]), st.m_n[1:]) < 1e-12
+
+
+def test_3d_tgv_fp64_replay_parity():
+    N = 16
+    p, u = tgv3d(N, 1.0)
+    prm = OM.MarchParams(dt=4.0, eps=1e-10, nmin=1)
+    st = OM.init_state(lattice_for_dim(3), p, u)
+    recs = OM.march(st, prm, 5)
+    L = _replay_run(3, N, "fp64", p, u, prm, [r.iters for r in recs])
+    assert L.stats()["status"] == 0
+    assert rel_l2(host(L.fields()[1]), st.m_n[1:]) < 1e-12
+
+
+@pytest.mark.parametrize("dim,N,steps", [(2, 64, 10), (3, 16, 4)])
+def test_fp32_storage_against_fp64_oracle(dim, N, steps):
+    # FP32 deviation storage with FP64 history and solve: gate 1e-5 relative L2 in u
+    p, u = random_phase(N, dim, 1.0, seed=12, kmax=8 if dim == 2 else 4)
+    prm = OM.MarchParams(dt=32.0, eps=1e-9, nmin=2 if dim == 2 else 1)
+    st = OM.init_state(lattice_for_dim(dim), p, u)
+    recs = OM.march(st, prm, steps)
+    L = _replay_run(dim, N, "fp32", p, u, prm, [r.iters for r in recs])
+    assert L.stats()["status"] == 0
+    assert rel_l2(host(L.fields()[1]), st.m_n[1:]) < 1e-5
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_explicit_march_matches_oracle(precision):
+    N, steps = 32, 37  # odd count exercises the unpaired last step
+    p, u = tgv2d(N, 10.0)
+    L = _lattice(2, N, precision)
+    L.init_fields(p, u)
+    L.explicit_march(steps)
+    f = OM.explicit_march(lattice_for_dim(2), OM.init_state(lattice_for_dim(2), p, u).f, steps)
+    tol = 1e-12 if precision == "fp64" else 1e-5
+    assert rel_l2(L.populations(), f) < tol
+    m = OK.moments(lattice_for_dim(2), f)
+    assert rel_l2(host(L.fields()[1]), m[1:]) < tol
+
+
+def test_explicit_march_3d():
+    N, steps = 16, 6
+    p, u = tgv3d(N, 10.0)
+    L = _lattice(3, N, "fp64")
+    L.init_fields(p, u)
+    L.explicit_march(steps)
+    f = OM.explicit_march(lattice_for_dim(3), OM.init_state(lattice_for_dim(3), p, u).f, steps)
+    assert rel_l2(L.populations(), f) < 1e-12
+
+
+def test_nonconvergent_step_reports_and_keeps_state():
+    p, u = tgv2d(32, 1.0)
+    L = _lattice(2, 32, "fp64")
+    L.set_params(dt=8.0, eps=1e-30, kmax=3)
+    L.init_fields(p, u)
+    f0 = L.populations()
+    L.march(4)
+    s = L.stats()
+    assert s["status"] == 2 and s["steps_done"] == 0 and s["inner_total"] == 3
+    assert np.array_equal(L.populations(), f0)
+
+
+def test_nonfinite_residual_stops_the_march():
+    p, u = tgv2d(32, 1.0)
+    u = u.copy()
+    u[0, 3, 3] = np.nan
+    L = _lattice(2, 32, "fp64")
+    L.set_params(dt=8.0, eps=1e-8)
+    L.init_fields(p, u)
+    L.march(2)
+    s = L.stats()
+    assert s["status"] == 3 and s["steps_done"] == 0
+
+
+def test_save_load_roundtrip_continues_identically():
+    p, u = tgv2d(32, 1.0)
+    prm = dict(dt=16.0, eps=1e-10)
+    A = _lattice(2, 32, "fp64")
+    A.set_params(**prm)
+    A.init_fields(p, u)
+    A.march(3)
+    blob = A.save_state()
+    A.march(2)
+    B = _lattice(2, 32, "fp64")
+    B.set_params(**prm)
+    B.load_state(blob)
+    B.march(2)
+    assert np.array_equal(A.populations(), B.populations())
+    assert B.stats()["steps_done"] == 5
+
+
+def test_march_continues_across_calls():
+    p, u = tgv2d(32, 1.0)
+    prm = OM.MarchParams(dt=16.0, eps=1e-10)
+    st = OM.init_state(lattice_for_dim(2), p, u)
+    recs = OM.march(st, prm, 6)
+    counts = [r.iters for r in recs]
+    L = _lattice(2, 32, "fp64")
+    L.set_params(dt=16.0, eps=1e-10, replay=True)
+    L.init_fields(p, u)
+    L.set_replay_counts(counts[:2])
+    L.march(2)
+    L.set_replay_counts(counts[2:])
+    L.march(4)
+    assert L.stats()["steps_done"] == 6
+    assert rel_l2(host(L.fields()[1]), st.m_n[1:]) < 1e-12
+
+
+def test_full_size_march_conserves_and_converges():
+    # D2Q9 N = 1024 FP32, the benchmark configuration: a few steps, properties that hold at any size
+    N = 1024
+    p, u = random_phase(N, 2, 1.0, seed=1)
+    L = _lattice(2, N, "fp32")
+    L.set_params(dt=128.0, eps=1e-9)
+    L.init_fields(p, u)
+    m0 = [float(x.sum()) for x in (L.fields()[0], *L.fields()[1])]
+    L.march(4)
+    s = L.stats()
+    assert s["status"] == 0 and s["steps_done"] == 4
+    it = L.step_iters()
+    assert np.all(it >= 2) and np.all(it <= 12)
+    ph, uu = L.fields()
+    m1 = [float(ph.sum()), float(uu[0].sum()), float(uu[1].sum())]
+    scale = float(torch.abs(uu).max()) * N * N
+    assert max(abs(a - b) for a, b in zip(m0, m1)) < 1e-6 * scale

@@ -1,0 +1,121 @@
+"""GPU parity of the single stages (sweep, shadow solve, equilibrium, explicit step) against the
+FP64 oracle on the same seeded inputs, through the C ABI."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import kinetics as OK
+from oracle import shadow as OS
+from oracle import sweep as OSW
+from oracle.lattice import lattice_for_dim
+from workloads.fields import random_moments, random_populations
+from tests.gpu_helpers import dev, host, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+# (dim, n): n = 8 wraps the 32-column warp strip onto itself, 64 leaves a ragged last strip,
+# 256 spans many strips and row blocks, 1024 is the full 2D benchmark size; 3D likewise up to 128.
+SWEEP_CASES = [(2, 8), (2, 16), (2, 64), (2, 256), (3, 8), (3, 16), (3, 32)]
+TOL = {"fp64": dict(f=1e-14, pr=1e-13, ss=1e-12), "fp32": dict(f=1e-6, pr=1e-5, ss=1e-5)}
+
+
+def _lib():
+    from paper_2609_39474_b300 import lattice as PL
+    return PL
+
+
+def _sweep_case(dim, n, precision, lift, seed=0, a=0.05):
+    PL = _lib()
+    lat = lattice_for_dim(dim)
+    shape = (n,) * dim
+    f = random_populations(lat.Q, shape, seed=seed, scale=1e-3)
+    h = random_moments(dim, shape, seed=seed + 1, scale=1e-4)
+    dm = random_moments(dim, shape, seed=seed + 2, scale=1e-4) if lift else None
+    T = PL.storage_dtype(precision)
+    # both sides start from the same (storage-rounded) inputs
+    f_s = dev(f, T)
+    h_s = dev(h, T)
+    dm_s = dev(dm, T) if lift else None
+    f_out, pr, ss = PL.sweep(dim, n, precision, a, f_s, h_s, dm_s)
+    torch.cuda.synchronize()
+    f_in = host(f_s)
+    trial = f_in + (OK.linear_lift(lat, host(dm_s)) if lift else 0.0)
+    f_T = OSW.sweep(lat, trial, a, host(h_s))
+    r, R = OSW.residual(f_T, trial)
+    return host(f_out), host(pr), float(ss.item()), f_T, OK.moments(lat, r), float(np.sum(r * r))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("lift", [False, True], ids=["nolift", "lift"])
+@pytest.mark.parametrize("dim,n", SWEEP_CASES)
+def test_sweep_matches_oracle(dim, n, precision, lift):
+    g_f, g_pr, g_ss, o_f, o_pr, o_ss = _sweep_case(dim, n, precision, lift)
+    tol = TOL[precision]
+    assert rel_l2(g_f, o_f) < tol["f"]
+    assert rel_l2(g_pr, o_pr) < tol["pr"]
+    assert abs(g_ss / o_ss - 1) < tol["ss"]
+
+
+@pytest.mark.parametrize("dim,n", [(2, 1024), (3, 128)])
+def test_sweep_full_size_fp32(dim, n):
+    # the benchmark sizes (D2Q9 N = 1024, D3Q19 N = 128) in the benchmark's launch configuration
+    g_f, g_pr, g_ss, o_f, o_pr, o_ss = _sweep_case(dim, n, "fp32", True, seed=7)
+    assert rel_l2(g_f, o_f) < TOL["fp32"]["f"]
+    assert rel_l2(g_pr, o_pr) < TOL["fp32"]["pr"]
+    assert abs(g_ss / o_ss - 1) < TOL["fp32"]["ss"]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("dim,n", [(2, 8), (2, 16), (2, 64), (2, 256), (3, 8), (3, 16), (3, 32)])
+def test_shadow_solve_matches_oracle(dim, n, precision):
+    PL = _lib()
+    shape = (n,) * dim
+    pr = random_moments(dim, shape, seed=3, scale=1e-6)
+    a, nu = 3.0 / (2 * 32.0), 1.0 / 6.0
+    T = PL.storage_dtype(precision)
+    pr_s = dev(pr, T)
+    dm = host(PL.shadow_solve(dim, n, precision, a, nu, pr_s))
+    ref = OS.shadow_dm(host(pr_s), a, nu)
+    assert rel_l2(dm, ref) < (1e-13 if precision == "fp64" else 2e-6)
+
+
+def test_shadow_solve_full_size_fp32():
+    PL = _lib()
+    n = 1024
+    pr = random_moments(2, (n, n), seed=4, scale=1e-6)
+    a = 3.0 / (2 * 64.0)
+    pr_s = dev(pr, torch.float32)
+    dm = host(PL.shadow_solve(2, n, "fp32", a, 1 / 6, pr_s))
+    ref = OS.shadow_dm(host(pr_s), a, 1 / 6)
+    assert rel_l2(dm, ref) < 2e-6
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("dim,n", [(2, 16), (3, 8)])
+def test_equilibrium_matches_oracle(dim, n, precision):
+    PL = _lib()
+    lat = lattice_for_dim(dim)
+    m = random_moments(dim, (n,) * dim, seed=5, scale=1e-2)
+    f = host(PL.equilibrium(dim, n, precision, dev(m[0]), dev(m[1:])))
+    ref = OK.feq(lat, m[0], m[1:])
+    assert rel_l2(f, ref) < (1e-15 if precision == "fp64" else 1e-7)
+
+
+@pytest.mark.parametrize("dim,n", [(2, 64), (3, 16)])
+def test_sweep_with_zero_source_is_explicit_step(dim, n):
+    PL = _lib()
+    lat = lattice_for_dim(dim)
+    f = random_populations(lat.Q, (n,) * dim, seed=6, scale=1e-3)
+    zero = torch.zeros((dim + 1,) + (n,) * dim, dtype=torch.float64, device="cuda")
+    f_out, _, _ = PL.sweep(dim, n, "fp64", 0.0, dev(f), zero)
+    assert rel_l2(host(f_out), OSW.explicit_step(lat, f)) < 1e-14
+
+
+def test_stage_argument_checks():
+    PL = _lib()
+    from paper_2609_39474_b300 import _lib as L
+    f = torch.zeros((9, 16, 16), dtype=torch.float64, device="cuda")
+    with pytest.raises(L.MscError):
+        PL.sweep(2, 16, "fp64", -1.0, f, torch.zeros((3, 16, 16), dtype=torch.float64, device="cuda"))
+    with pytest.raises(ValueError):
+        PL.sweep(2, 16, "fp32", 0.1, f, torch.zeros((3, 16, 16), dtype=torch.float64, device="cuda"))

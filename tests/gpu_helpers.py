@@ -37,3 +37,15 @@ def oracle_replay(dim, p, u, params: OM.MarchParams, counts):
 
 def oracle_moments(dim, f):
     return OK.moments(lattice_for_dim(dim), f)
+
+
+def state_blob(dim, n, precision, st) -> bytes:
+    """msc_load_state blob of an oracle state: header, step count, f^n.. (storage type), m^n, m^{n-1}."""
+    import struct
+    nav = len(st.f_hist)
+    hdr = struct.pack("<6iq", 0x4D53434C, dim, n, 0 if precision == "fp64" else 1, nav, 0, st.steps_done)
+    dt = np.float64 if precision == "fp64" else np.float32
+    parts = [hdr] + [np.ascontiguousarray(f, dtype=dt).tobytes() for f in st.f_hist]
+    parts += [np.ascontiguousarray(st.m_n, dtype=np.float64).tobytes(),
+              np.ascontiguousarray(st.m_nm1, dtype=np.float64).tobytes()]
+    return b"".join(parts)

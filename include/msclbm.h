@@ -192,6 +192,22 @@ int msc_shadow_solve(int dim, int n, int precision, double a, double nu, const v
 int msc_equilibrium(int dim, int n, int precision, const double* p_hat, const double* u,
                     void* f_out, void* stream);
 
+/* Allocation-free variant of msc_sweep for D2Q9 (dim 2).  The paper has no counterpart: this is
+   an interface convenience for callers that cannot allocate device memory, such as host
+   frameworks that own the whole device-memory budget and forbid plugins from calling cudaMalloc,
+   bindings that can only pass input and output arrays, or latency-critical loops in which an
+   allocation would synchronise the device.  Same computation and arguments as msc_sweep with
+   dim = 2, minus the scratch: the reduction scratch (a counter and one partial sum per block) is
+   a fixed static device array of 33 KB that every device which loads the library holds until the
+   process exits.  Limits: n <= 4096 (FP64 or FP32 storage); larger lattices return MSC_ERR_ARG.
+   The first call on each device looks the array up with that device current (call it once
+   outside any stream capture before relying on it).  Every call shares the same array and clears
+   its counter itself, so calls that may overlap on the GPU (different streams or devices sharing
+   one process-wide array per device, or host threads racing on one device) race with each other:
+   serialise them. */
+int msc_sweep_d2q9_noalloc(int n, int precision, double a, const void* f_in, const void* dm,
+                           const void* h, void* f_out, void* pr_out, double* sumsq_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

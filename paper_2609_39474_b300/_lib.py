@@ -76,6 +76,7 @@ _SIG = {
     "msc_sweep": (_i, [_i, _i, _i, _d, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "msc_shadow_solve": (_i, [_i, _i, _i, _d, _d, _vp, _vp, _vp, _sz, _vp]),
     "msc_equilibrium": (_i, [_i, _i, _i, _vp, _vp, _vp, _vp]),
+    "msc_sweep_d2q9_noalloc": (_i, [_i, _i, _d, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
 }
 for _name, (_res, _args) in _SIG.items():
     _fn = getattr(lib, _name)

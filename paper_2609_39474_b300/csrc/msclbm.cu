@@ -859,3 +859,5 @@ int msc_equilibrium(int dim, int n, int precision, const double* p, const double
 }
 
 }  // extern "C"
+
+#include "sweep_noalloc.cuh"

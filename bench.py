@@ -265,7 +265,10 @@ def run_phase(args):
         L.init_fields(p_d, u_d)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        L.march(S)
+        if args.phase == "msc-stepwise":
+            L.march_stepwise(S)
+        else:
+            L.march(S)
         e1.record()
         torch.cuda.synchronize()
         if i >= args.warmup:
@@ -390,9 +393,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--phase", default="all", choices=["all", "msc", "sweep"],
+    ap.add_argument("--phase", default="all", choices=["all", "msc", "msc-stepwise", "sweep"],
                     help="profiling aids: 'msc' runs only the timed MSC marches of the default candidate, "
-                         "'sweep' only the fused-sweep roofline loop")
+                         "'msc-stepwise' the same marches driven from the host (one launch per kernel, "
+                         "visible to ncu), 'sweep' only the fused-sweep roofline loop")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
 

@@ -13,7 +13,8 @@
  *
  * Conventions shared by every entry point
  *  - Lattices are periodic and cubic: n sites per direction, n a power of two,
- *    8 <= n <= 8192 for D2Q9 (dim 2) and 8 <= n <= 512 for D3Q19 (dim 3).
+ *    8 <= n <= 4096 (FP32 storage) or 2048 (FP64) for D2Q9 (dim 2), and 8 <= n <= 256 (FP32)
+ *    or 128 (FP64) for D3Q19 (dim 3): the shared-memory transforms hold whole lines.
  *  - Layout is structure of arrays with x fastest: populations f[k][z][y][x]
  *    (k in the paper's ordering, Appendix A), fields m[c][z][y][x] with
  *    c = 0 the pressure-like variable p_hat and c = 1..d the velocity
@@ -126,6 +127,12 @@ int msc_init_fields(msc_ctx* ctx, const double* p_hat, const double* u, int on_d
    outcome with msc_get_stats.  A nonconvergent or non-finite step stops the march with the
    state at the last accepted step. */
 int msc_march(msc_ctx* ctx, int n_steps);
+
+/* The same march as msc_march, driven from the host: the same kernels launched one at a time
+   with the acceptance decision read back after every sweep (one stream synchronisation per inner
+   iteration).  Results are identical to msc_march; it exists for profilers that do not descend
+   into conditional graph nodes and for debugging, and is much slower at small lattices. */
+int msc_march_stepwise(msc_ctx* ctx, int n_steps);
 
 /* Run n_steps explicit LBM steps f <- S f_eq(P f) (same collision and streaming with no BDF
    source; Section 4.1) from the current accepted populations.  Afterwards m^n = P f and the

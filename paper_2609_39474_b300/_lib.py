@@ -62,6 +62,7 @@ _SIG = {
     "msc_set_params": (_i, [_vp, ctypes.POINTER(Params)]),
     "msc_init_fields": (_i, [_vp, _vp, _vp, _i]),
     "msc_march": (_i, [_vp, _i]),
+    "msc_march_stepwise": (_i, [_vp, _i]),
     "msc_explicit_march": (_i, [_vp, _i]),
     "msc_get_stats": (_i, [_vp, ctypes.POINTER(Stats)]),
     "msc_read_fields": (_i, [_vp, _vp, _vp, _i]),

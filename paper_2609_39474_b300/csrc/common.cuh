@@ -74,12 +74,14 @@ struct DevState {
     int64_t hist_pos;       // total residuals recorded in the ring this call
     // explicit march
     int ex_a, ex_b;
-    int ex_pairs_left;
+    int ex_loops_left;
+    // the next physical step's h and trial populations were already formed by k_step_end
+    int prepared;
 };
 
 // Layout of the context workspace (byte offsets from the workspace base).
 struct Layout {
-    size_t state, fbuf, mbuf, h, pr, dm, spec, tw, partial, counter, iters, hist, replay, total;
+    size_t state, fbuf, mbuf, h, pr, dm, spec, tw, coef, partial, counter, iters, hist, replay, total;
     size_t fstride;  // bytes of one population array
 };
 
@@ -99,7 +101,7 @@ inline int lattice_q(int dim) { return dim == 2 ? 9 : 19; }
 inline bool valid_lattice(int dim, int n, int precision) {
     if (precision != MSC_FP64 && precision != MSC_FP32) return false;
     if (!is_pow2(n) || n < 8) return false;
-    if (dim == 2) return n <= (precision == MSC_FP64 ? 4096 : 8192);
+    if (dim == 2) return n <= (precision == MSC_FP64 ? 2048 : 4096);
     if (dim == 3) return n <= (precision == MSC_FP64 ? 128 : 256);
     return false;
 }

@@ -3,10 +3,8 @@
 // A block transforms `nfft` independent arrays of length n (power of two) stored contiguously
 // in shared memory.  Forward transforms use e^{-2 pi i j x / n}; inverse transforms use the
 // conjugate twiddles and are unnormalised (the 1/N_Omega of Eq. fft-convention is applied by
-// the caller).  Two orderings are provided so that no explicit permutation pass is needed:
-//   dit: input in bit-reversed order, output in natural order (Cooley-Tukey decimation in time)
-//   dif: input in natural order, output in bit-reversed order (decimation in frequency)
-// Twiddles come from a table tw[j] = e^{-2 pi i j / n}, j < n/2, built once per context in FP64.
+// the caller).  Input and output are in natural order (Stockham autosort, no permutation pass).
+// Twiddles come from a table tw[j] = e^{-2 pi i j / n}, j < n, built once per context in FP64.
 #pragma once
 
 #include "common.cuh"
@@ -28,72 +26,194 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-__device__ __forceinline__ int bitrev(int i, int logn) { return (int)(__brev((unsigned)i) >> (32 - logn)); }
-
 template <typename C>
-__device__ __forceinline__ C twiddle(const C* tw, int idx, bool inverse) {
-    C w = tw[idx];
+__device__ __forceinline__ C twiddle(const C* __restrict__ tw, int idx, bool inverse) {
+    C w = __ldg(tw + idx);
     if (inverse) w.y = -w.y;
     return w;
 }
 
-// In-place decimation-in-time passes over nfft arrays (bit-reversed in, natural out).
+// ---- small DFTs in registers (forward: e^{-2 pi i jk/R}; INV: conjugate) -----------------------
+
 template <typename C>
-__device__ void fft_dit(C* s, int n, int logn, int nfft, const C* __restrict__ tw, bool inverse) {
-    const int hn = n >> 1;
-    const int total = nfft * hn;
-    for (int lg = 1; lg <= logn; ++lg) {
-        const int half = 1 << (lg - 1);
-        const int len = half << 1;
-        const int tstride = n >> lg;
-        for (int b = threadIdx.x; b < total; b += blockDim.x) {
-            const int f = b >> (logn - 1);
-            const int bb = b & (hn - 1);
-            const int grp = bb >> (lg - 1);
-            const int pos = bb & (half - 1);
-            const int i = f * n + grp * len + pos;
-            const int j = i + half;
-            const C w = twiddle(tw, pos * tstride, inverse);
-            const C u = s[i];
-            const C v = cmul(s[j], w);
-            s[i] = cadd(u, v);
-            s[j] = csub(u, v);
+__device__ __forceinline__ C mul_minus_i(C d, bool inv) {  // d * (-i) forward, d * (+i) inverse
+    C r;
+    if (inv) { r.x = -d.y; r.y = d.x; }
+    else { r.x = d.y; r.y = -d.x; }
+    return r;
+}
+
+// multiply by e^{-+ 2 pi i m / 16} with (c, s) = (cos, sin) of 2 pi m / 16
+template <typename C>
+__device__ __forceinline__ C rot(C v, double c, double s, bool inv) {
+    using R = decltype(v.x);
+    const R cc = (R)c, ss = inv ? (R)s : (R)(-s);
+    C r;
+    r.x = v.x * cc - v.y * ss;
+    r.y = v.x * ss + v.y * cc;
+    return r;
+}
+
+template <typename C, bool INV>
+__device__ __forceinline__ void dft4(C& a, C& b, C& c, C& d) {
+    const C a0 = cadd(a, c), a1 = csub(a, c), a2 = cadd(b, d);
+    const C a3 = mul_minus_i(csub(b, d), INV);
+    a = cadd(a0, a2);
+    b = cadd(a1, a3);
+    c = csub(a0, a2);
+    d = csub(a1, a3);
+}
+
+template <typename C, int R, bool INV> struct SmallDft;
+
+template <typename C, bool INV> struct SmallDft<C, 2, INV> {
+    __device__ __forceinline__ static void run(C* v) {
+        const C a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    }
+};
+template <typename C, bool INV> struct SmallDft<C, 4, INV> {
+    __device__ __forceinline__ static void run(C* v) { dft4<C, INV>(v[0], v[1], v[2], v[3]); }
+};
+// 8 = 2 x 4: n = q + 2p, k = s + 4t
+template <typename C, bool INV> struct SmallDft<C, 8, INV> {
+    __device__ __forceinline__ static void run(C* v) {
+        const double h = 0.70710678118654752440;
+        C a0 = v[0], a1 = v[2], a2 = v[4], a3 = v[6];
+        C b0 = v[1], b1 = v[3], b2 = v[5], b3 = v[7];
+        dft4<C, INV>(a0, a1, a2, a3);
+        dft4<C, INV>(b0, b1, b2, b3);
+        b1 = rot(b1, h, h, INV);
+        b2 = mul_minus_i(b2, INV);
+        b3 = rot(b3, -h, h, INV);
+        v[0] = cadd(a0, b0); v[4] = csub(a0, b0);
+        v[1] = cadd(a1, b1); v[5] = csub(a1, b1);
+        v[2] = cadd(a2, b2); v[6] = csub(a2, b2);
+        v[3] = cadd(a3, b3); v[7] = csub(a3, b3);
+    }
+};
+// 16 = 4 x 4: n = q + 4p, k = s + 4t; twiddles e^{-2 pi i q s / 16}
+template <typename C, bool INV> struct SmallDft<C, 16, INV> {
+    __device__ __forceinline__ static void run(C* v) {
+        const double c1 = 0.92387953251128675613, s1 = 0.38268343236508977173, h = 0.70710678118654752440;
+        C A[4][4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            A[q][0] = v[q]; A[q][1] = v[q + 4]; A[q][2] = v[q + 8]; A[q][3] = v[q + 12];
+            dft4<C, INV>(A[q][0], A[q][1], A[q][2], A[q][3]);
         }
-        __syncthreads();
+        // q = 1: m = s;  q = 2: m = 2s;  q = 3: m = 3s
+        A[1][1] = rot(A[1][1], c1, s1, INV);
+        A[1][2] = rot(A[1][2], h, h, INV);
+        A[1][3] = rot(A[1][3], s1, c1, INV);
+        A[2][1] = rot(A[2][1], h, h, INV);
+        A[2][2] = mul_minus_i(A[2][2], INV);
+        A[2][3] = rot(A[2][3], -h, h, INV);
+        A[3][1] = rot(A[3][1], s1, c1, INV);
+        A[3][2] = rot(A[3][2], -h, h, INV);
+        A[3][3] = rot(A[3][3], -c1, -s1, INV);
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            C a = A[0][s], b = A[1][s], c = A[2][s], d = A[3][s];
+            dft4<C, INV>(a, b, c, d);
+            v[s] = a; v[s + 4] = b; v[s + 8] = c; v[s + 12] = d;
+        }
+    }
+};
+
+// Shared-memory layout of the transforms: array f of length n starts at f * padded_len(n) and
+// element i sits at i + i/16.  The padding breaks the power-of-two strides of the Stockham stores
+// that would otherwise hit one shared-memory bank.
+__host__ __device__ __forceinline__ int padded_len(int n) { return n + (n >> 4); }
+__device__ __forceinline__ int pad(int i) { return i + (i >> 4); }
+
+// One in-place Stockham stage of radix R over nfft arrays of length n: every butterfly j reads the
+// R values j + r n/R, multiplies value r by w^(k r n/(Ns R)) with k = j mod Ns, does the R-point DFT
+// in registers and writes value r to (j - k) R + k + r Ns.  All reads of the stage complete before
+// any write (block barrier), so one buffer suffices.  Each thread handles at most 16/R butterflies.
+template <typename C, int R, bool INV>
+__device__ __forceinline__ void stockham_stage(C* x, int n, int logn, int Ns, int nfft, const C* __restrict__ tw) {
+    constexpr int LR = R == 2 ? 1 : (R == 4 ? 2 : (R == 8 ? 3 : 4));
+    constexpr int MB = 16 / R;  // butterflies per thread (host geometry guarantees enough threads)
+    const int lnb = logn - LR;
+    const int nb = 1 << lnb;
+    const int tstride = n / (Ns * R);
+    const int total = nfft << lnb;
+    const int plen = padded_len(n);
+    C v[MB][R];
+#pragma unroll
+    for (int m = 0; m < MB; ++m) {
+        const int b = threadIdx.x + m * blockDim.x;
+        if (b < total) {
+            const int f = b >> lnb;
+            const int j = b & (nb - 1);
+            const C* xs = x + f * plen;
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[m][r] = xs[pad(j + r * nb)];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < MB; ++m) {
+        const int b = threadIdx.x + m * blockDim.x;
+        if (b < total) {
+            const int f = b >> lnb;
+            const int j = b & (nb - 1);
+            const int k = j & (Ns - 1);
+            if (Ns > 1) {
+                const int kt = k * tstride;
+                if (R == 16) {
+                    // two table reads, the other powers by products (at most four deep)
+                    C w[16];
+                    w[1] = twiddle(tw, kt, INV);
+                    w[4] = twiddle(tw, 4 * kt, INV);
+                    w[2] = cmul(w[1], w[1]);
+                    w[3] = cmul(w[2], w[1]);
+                    w[8] = cmul(w[4], w[4]);
+#pragma unroll
+                    for (int r = 5; r < 8; ++r) w[r] = cmul(w[4], w[r - 4]);
+#pragma unroll
+                    for (int r = 9; r < 16; ++r) w[r] = cmul(w[8], w[r - 8]);
+#pragma unroll
+                    for (int r = 1; r < 16; ++r) v[m][r] = cmul(v[m][r], w[r]);
+                } else {
+#pragma unroll
+                    for (int r = 1; r < R; ++r) v[m][r] = cmul(v[m][r], twiddle(tw, r * kt, INV));
+                }
+            }
+            SmallDft<C, R, INV>::run(v[m]);
+            C* ys = x + f * plen;
+            const int base = (j - k) * R + k;
+#pragma unroll
+            for (int r = 0; r < R; ++r) ys[pad(base + r * Ns)] = v[m][r];
+        }
+    }
+    __syncthreads();
+}
+
+// In-place Stockham autosort FFT (natural order in and out) over nfft padded arrays of length n
+// in shared memory.  Mixed radix: one radix-2/4/8 stage for log2(n) mod 4, then radix-16 stages.
+// Must be called by all threads of the block, with blockDim.x >= nfft * n / 16.
+template <typename C, bool INV>
+__device__ void fft_stockham(C* x, int n, int logn, int nfft, const C* __restrict__ tw) {
+    int Ns = 1;
+    const int first = logn & 3;
+    if (first == 1) stockham_stage<C, 2, INV>(x, n, logn, Ns, nfft, tw);
+    else if (first == 2) stockham_stage<C, 4, INV>(x, n, logn, Ns, nfft, tw);
+    else if (first == 3) stockham_stage<C, 8, INV>(x, n, logn, Ns, nfft, tw);
+    Ns <<= first;
+    for (int rem = logn - first; rem > 0; rem -= 4) {
+        stockham_stage<C, 16, INV>(x, n, logn, Ns, nfft, tw);
+        Ns <<= 4;
     }
 }
 
-// In-place decimation-in-frequency passes over nfft arrays (natural in, bit-reversed out).
-template <typename C>
-__device__ void fft_dif(C* s, int n, int logn, int nfft, const C* __restrict__ tw, bool inverse) {
-    const int hn = n >> 1;
-    const int total = nfft * hn;
-    for (int lg = logn; lg >= 1; --lg) {
-        const int half = 1 << (lg - 1);
-        const int len = half << 1;
-        const int tstride = n >> lg;
-        for (int b = threadIdx.x; b < total; b += blockDim.x) {
-            const int f = b >> (logn - 1);
-            const int bb = b & (hn - 1);
-            const int grp = bb >> (lg - 1);
-            const int pos = bb & (half - 1);
-            const int i = f * n + grp * len + pos;
-            const int j = i + half;
-            const C w = twiddle(tw, pos * tstride, inverse);
-            const C u = s[i];
-            const C v = s[j];
-            s[i] = cadd(u, v);
-            s[j] = cmul(csub(u, v), w);
-        }
-        __syncthreads();
-    }
-}
-
-// tw[j] = exp(-2 pi i j / n) for j < n/2, evaluated in FP64 and rounded to the storage type.
+// tw[j] = exp(-2 pi i j / n) for j < n, evaluated in FP64 and rounded to the storage type.
 template <typename C>
 __global__ void k_twiddles(C* tw, int n) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j < n / 2) {
+    if (j < n) {
         double s, c;
         sincospi(2.0 * (double)j / (double)n, &s, &c);
         C w;

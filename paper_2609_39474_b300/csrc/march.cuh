@@ -76,6 +76,7 @@ template <class L, typename T>
 __global__ void k_step_begin(const DevState* __restrict__ st, T* __restrict__ fbase, size_t fstride,
                              const double* __restrict__ mbuf, T* __restrict__ h, size_t sites) {
     const volatile DevState* vs = st;
+    if (vs->prepared) return;  // formed by the previous step's k_step_end
     const int q = vs->q;
     const double dt = vs->dt;
     const int nav = vs->n_avail;
@@ -115,10 +116,15 @@ __global__ void k_step_begin(const DevState* __restrict__ st, T* __restrict__ fb
 }
 
 // Acceptance: m^{n+1} = R_{q,h}(f^{n+1}) with the unrotated histories (Eq. macro-reconstruct),
-// evaluated in FP64 and written into the m^{n-1} slot (rotated by k_step_finish).
+// evaluated in FP64 (P f accumulated in the storage type) and written into the m^{n-1} slot
+// (rotated by k_step_finish).  When another step of this march follows, the same pass also forms
+// that step's BDF2 history term h = (4 m^{n+1} - m^n)/(2 dt) and its population warm start
+// (2 f^{n+1} - f^n, or 3 f^{n+1} - 3 f^n + f^{n-1}; Section 3.1) into the free working slot, so
+// that the next k_step_begin has nothing to do.
 template <class L, typename T>
-__global__ void k_step_end(const DevState* __restrict__ st, const T* __restrict__ fbase, size_t fstride,
-                           double* __restrict__ mbuf, size_t sites) {
+__global__ void __launch_bounds__(kFieldThreads) k_step_end(const DevState* __restrict__ st, T* __restrict__ fbase,
+                                                            size_t fstride, double* __restrict__ mbuf, T* __restrict__ h,
+                                                            size_t sites) {
     const volatile DevState* vs = st;
     if (!vs->accepted) return;
     const int q = vs->q;
@@ -131,23 +137,87 @@ __global__ void k_step_end(const DevState* __restrict__ st, const T* __restrict_
     const T* ft = fbase + (size_t)vs->slot_cur * fstride;
     const double c1 = q == 1 ? 1.0 / dt : 4.0 / (2.0 * dt);
     const double c2 = q == 1 ? 0.0 : 1.0 / (2.0 * dt);
+    const bool next = vs->status == MSC_OK && vs->steps_target > 1;
+    const int nav = vs->n_avail + 1 < 3 ? vs->n_avail + 1 : 3;  // accepted states after rotation
+    const T* f0 = fbase + (size_t)vs->slot_fn[0] * fstride;
+    const T* f1 = fbase + (size_t)vs->slot_fn[1] * fstride;
+    T* trial = fbase + (size_t)vs->slot_nxt * fstride;
+    const double n1 = 4.0 / (2.0 * dt), n2 = 1.0 / (2.0 * dt);  // BDF2 for the next step
+    const double k1 = 0.5 * c1 * inv, k2 = 0.5 * c2 * inv;
+#pragma unroll 2
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < sites;
          i += (size_t)gridDim.x * blockDim.x) {
-        double mom[4] = {0.0, 0.0, 0.0, 0.0};
+        T fv[L::Q];
+        T mom[4] = {T(0), T(0), T(0), T(0)};
 #pragma unroll
         for (int k = 0; k < L::Q; ++k) {
-            const double v = (double)ft[k * sites + i];
+            const T v = ft[k * sites + i];
+            fv[k] = v;
             mom[0] += v;
-            if (L::cx(k)) mom[1] += L::cx(k) * v;
-            if (L::cy(k)) mom[2] += L::cy(k) * v;
-            if (L::D == 3 && L::cz(k)) mom[3] += L::cz(k) * v;
+            if (L::cx(k)) mom[1] += T(L::cx(k)) * v;
+            if (L::cy(k)) mom[2] += T(L::cy(k)) * v;
+            if (L::D == 3 && L::cz(k)) mom[3] += T(L::cz(k)) * v;
         }
 #pragma unroll
         for (int c = 0; c <= L::D; ++c) {
+            // m^{n+1} = (P f + h/2) inv with h = c1 m^n - c2 m^{n-1}, constants folded (FP64)
             const size_t o = c * sites + i;
-            const double hc = c1 * mn[o] - c2 * mnm1[o];
-            mnm1[o] = (mom[c] + 0.5 * hc) * inv;
+            const double mc = mn[o];
+            const double mnew = fma(k1, mc, fma(-k2, mnm1[o], inv * (double)mom[c]));
+            mnm1[o] = mnew;
+            if (next) h[o] = (T)fma(n1, mnew, -n2 * mc);
         }
+        if (next) {
+            if (nav == 2) {
+#pragma unroll
+                for (int k = 0; k < L::Q; ++k) trial[k * sites + i] = T(2) * fv[k] - f0[k * sites + i];
+            } else {
+#pragma unroll
+                for (int k = 0; k < L::Q; ++k) {
+                    const size_t o = k * sites + i;
+                    trial[o] = T(3) * (fv[k] - f0[o]) + f1[o];
+                }
+            }
+        }
+    }
+}
+
+// FP64 coefficients of the closed-form Schur solve (Eq. schur) at every masked wavevector, for
+// BDF1 (a = 1/dt) and BDF2 (a = 3/(2 dt)).  With dv = a + nu|k|^2 and D = a + cs^2 |k|^2 / dv the
+// solve is dp = A rp - i B (k.rm), du = Dv rm - i Cc k dp, and the table stores
+// (A, B, Cc, Dv) = (s/D, s/(D dv), cs^2/dv, s/dv) with s = 1/N_Omega folded in.  Mode index:
+// 2D jx + (n/4+1) jyk, 3D jx + (n/4+1)(jyk + (n/2+1) jzk), with jyk = j_y + n/4, jzk = j_z + n/4.
+__host__ __device__ inline size_t solve_modes(int dim, int n) {
+    const size_t a = n / 4 + 1, b = n / 2 + 1;
+    return dim == 2 ? a * b : a * b * b;
+}
+
+__device__ inline void solve_coefficients(double a, double nu, double k2, double scale, double* out) {
+    const double cs2 = 1.0 / 3.0;
+    const double dv = a + nu * k2;
+    const double idv = 1.0 / dv;
+    const double iD = 1.0 / (a + cs2 * k2 * idv);
+    out[0] = iD * scale;
+    out[1] = iD * idv * scale;
+    out[2] = cs2 * idv;
+    out[3] = idv * scale;
+}
+
+__global__ void k_solve_tables(double* coef, int dim, int n, double dt, double nu) {
+    const size_t nm = solve_modes(dim, n);
+    const int nx4 = n / 4 + 1, ny = n / 2 + 1;
+    const double tpn = 6.283185307179586476925286766559 / (double)n;
+    const double scale = dim == 2 ? 1.0 / ((double)n * n) : 1.0 / ((double)n * n * n);
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < 2 * nm; t += (size_t)gridDim.x * blockDim.x) {
+        const int q = (int)(t / nm) + 1;
+        const size_t m = t - (size_t)(q - 1) * nm;
+        const int jx = (int)(m % nx4);
+        const size_t r = m / nx4;
+        const int jy = (int)(r % ny) - n / 4;
+        const int jz = dim == 3 ? (int)(r / ny) - n / 4 : 0;
+        const double kx = tpn * jx, ky = tpn * jy, kz = tpn * jz;
+        const double a = q == 1 ? 1.0 / dt : 3.0 / (2.0 * dt);
+        solve_coefficients(a, nu, kx * kx + ky * ky + kz * kz, scale, coef + 4 * t);
     }
 }
 
@@ -181,9 +251,11 @@ __global__ void k_reset_history(DevState* st) {
     st->last_iters = 0;
     st->last_q = 0;
     st->R_last = 0.0;
+    st->prepared = 0;
 }
 
 __global__ void k_set_target(DevState* st, int n_steps) {
+    st->prepared = 0;
     st->steps_target = n_steps;
     st->steps_in_call = 0;
     st->inner_total = 0;
@@ -203,7 +275,11 @@ __device__ inline bool slot_in_history(const DevState* st, int s) {
     return false;
 }
 
-__global__ void k_step_setup(DevState* st, cudaGraphConditionalHandle h_iter) {
+__global__ void k_step_setup(DevState* st, cudaGraphConditionalHandle h_iter, int cond) {
+    if (st->prepared) {  // k_step_finish already set up this step
+        if (cond) cudaGraphSetConditional(h_iter, 1u);
+        return;
+    }
     st->q = st->steps_done == 0 ? 1 : 2;
     st->a = st->q == 1 ? 1.0 / st->dt : 3.0 / (2.0 * st->dt);
     st->iter = 0;
@@ -215,11 +291,11 @@ __global__ void k_step_setup(DevState* st, cudaGraphConditionalHandle h_iter) {
         if (picked == 0) st->slot_cur = s; else st->slot_nxt = s;
         ++picked;
     }
-    cudaGraphSetConditional(h_iter, 1u);
+    if (cond) cudaGraphSetConditional(h_iter, 1u);
 }
 
 __global__ void k_step_finish(DevState* st, int* iters_out, int max_steps,
-                              cudaGraphConditionalHandle h_step) {
+                              cudaGraphConditionalHandle h_step, int cond) {
     unsigned int go = 0u;
     if (st->accepted && st->status == MSC_OK) {
         const int k = st->steps_in_call;
@@ -238,7 +314,25 @@ __global__ void k_step_finish(DevState* st, int* iters_out, int max_steps,
         st->last_q = st->q;
         go = st->steps_target > 0 ? 1u : 0u;
     }
-    cudaGraphSetConditional(h_step, go);
+    // the next step's trial was written into the old slot_nxt by k_step_end
+    const int trial = st->slot_nxt;
+    if (go) {
+        st->q = 2;
+        st->a = 3.0 / (2.0 * st->dt);
+        st->iter = 0;
+        st->accepted = 0;
+        st->lift = 0;
+        st->slot_cur = trial;
+        for (int s = 0; s < kNumFBuf; ++s) {
+            if (s == trial || slot_in_history(st, s)) continue;
+            st->slot_nxt = s;
+            break;
+        }
+        st->prepared = 1;
+    } else {
+        st->prepared = 0;
+    }
+    if (cond) cudaGraphSetConditional(h_step, go);
 }
 
 // m^n = P f^n of the accepted slot into both moment slots (after an explicit march)
@@ -269,15 +363,16 @@ __global__ void k_moments_state(const DevState* __restrict__ st, const T* __rest
     }
 }
 
-// explicit march bookkeeping: ping-pong between the accepted slot and one free slot
-__global__ void k_ex_setup(DevState* st, int pairs) {
+// explicit march bookkeeping: ping-pong between the accepted slot and one free slot; the
+// counter holds the remaining iterations of the graph's unrolled loop body
+__global__ void k_ex_setup(DevState* st, int loop_iters) {
     st->ex_a = st->slot_fn[0];
     st->ex_b = (st->slot_fn[0] + 1) % kNumFBuf;
-    st->ex_pairs_left = pairs;
+    st->ex_loops_left = loop_iters;
 }
 
 __global__ void k_ex_arm(DevState* st, cudaGraphConditionalHandle h_ex) {
-    cudaGraphSetConditional(h_ex, st->ex_pairs_left > 0 ? 1u : 0u);
+    cudaGraphSetConditional(h_ex, st->ex_loops_left > 0 ? 1u : 0u);
 }
 
 __global__ void k_ex_finish(DevState* st, int odd) {
@@ -290,6 +385,7 @@ __global__ void k_ex_finish(DevState* st, int odd) {
     st->steps_done = 0;
     st->m_cur = 0;
     st->m_prev = 1;
+    st->prepared = 0;
 }
 
 }  // namespace msc

@@ -16,6 +16,9 @@
 
 using namespace msc;
 
+// explicit LBM steps per iteration of the conditional loop of the explicit-march graph (even)
+constexpr int kExplicitUnroll = 8;
+
 #define CK(call)                                   \
     do {                                           \
         cudaError_t e_ = (call);                   \
@@ -31,6 +34,7 @@ struct msc_ctx {
     unsigned char* ws;
     cudaStream_t stream;
     bool params_set, fields_set;
+    bool coef_dirty;  // solve coefficient tables need (re)computing for the current dt, nu
     msc_params params;
     // graphs
     cudaGraph_t g_march;
@@ -80,7 +84,8 @@ bool compute_layout(const msc_lattice_desc* d, Layout* L) {
     L->pr = take(F * sites * e);
     L->dm = take(F * sites * e);
     L->spec = take(spec_bytes(d->dim, d->n, d->precision));
-    L->tw = take((n / 2) * 2 * e);
+    L->tw = take(n * 2 * e);
+    L->coef = take(2 * 4 * solve_modes(d->dim, d->n) * sizeof(double));
     L->partial = take((size_t)sweep_blocks_for(d->dim, d->n, d->precision) * 8);
     L->counter = take(256);
     L->iters = take((size_t)d->max_steps * 4);
@@ -189,17 +194,20 @@ void add_spectral_nodes(msc_ctx* c, cudaGraph_t g, cudaError_t* err) {
     using C = typename Cplx<T>::type;
     const int n = c->desc.n;
     Spec2Args<T> S = spec3_args<T>(n, c->logn, 0.0, c->params.nu, at<T>(c, c->lay.pr), at<C>(c, c->lay.spec),
-                                   at<T>(c, c->lay.dm), at<C>(c, c->lay.tw), at<DevState>(c, c->lay.state));
+                                   at<T>(c, c->lay.dm), at<C>(c, c->lay.tw), at<DevState>(c, c->lay.state),
+                                   at<double>(c, c->lay.coef));
     void* args[] = {&S};
     if (c->desc.dim == 2) {
+        const RowGeom rg = row_geometry(n, 3, n);
         S.nf = 3;
         S.rows = n;
-        cudaGraphNode_t n1 = add_kernel(g, {}, (const void*)k_rowfft_fwd<T>, dim3(spec2_row_blocks(n)),
-                                        dim3(kFftThreads), spec2_row_smem<T>(n), args, err);
+        S.P = rg.P;
+        cudaGraphNode_t n1 = add_kernel(g, {}, (const void*)k_rowfft_fwd<T>, dim3(rg.blocks), dim3(rg.threads),
+                                        spec_row_smem<T>(n, rg.P), args, err);
         cudaGraphNode_t n2 = add_kernel(g, {n1}, (const void*)k_colsolve<T>, dim3(n / 4 + 1),
-                                        dim3(kFftThreads), spec2_col_smem<T>(n), args, err);
-        add_kernel(g, {n2}, (const void*)k_rowfft_inv<T>, dim3(spec2_row_blocks(n)), dim3(kFftThreads),
-                   spec2_row_smem<T>(n), args, err);
+                                        dim3(spec2_col_threads(n)), spec2_col_smem<T>(n), args, err);
+        add_kernel(g, {n2}, (const void*)k_rowfft_inv<T>, dim3(rg.blocks), dim3(rg.threads),
+                   spec_row_smem<T>(n, rg.P), args, err);
     } else {
         LaunchDesc L[5];
         spectral3_launches<T>(n, L);
@@ -207,6 +215,7 @@ void add_spectral_nodes(msc_ctx* c, cudaGraph_t g, cudaError_t* err) {
         for (int i = 0; i < 5; ++i) {
             std::vector<cudaGraphNode_t> deps;
             if (prev) deps.push_back(prev);
+            spec3_pass_args<T>(n, &S, i);  // node parameters are copied when the node is added
             prev = add_kernel(g, deps, L[i].fn, L[i].grid, L[i].block, L[i].smem, args, err);
         }
     }
@@ -215,10 +224,11 @@ void add_spectral_nodes(msc_ctx* c, cudaGraph_t g, cudaError_t* err) {
 template <typename T>
 int set_smem_limits(int dim, int n) {
     if (dim == 2) {
+        const RowGeom rg = row_geometry(n, 3, n);
         CK(cudaFuncSetAttribute(k_rowfft_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)spec2_row_smem<T>(n)));
+                                (int)spec_row_smem<T>(n, rg.P)));
         CK(cudaFuncSetAttribute(k_rowfft_inv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)spec2_row_smem<T>(n)));
+                                (int)spec_row_smem<T>(n, rg.P)));
         CK(cudaFuncSetAttribute(k_colsolve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)spec2_col_smem<T>(n)));
     } else {
@@ -254,7 +264,8 @@ int build_march_graph(msc_ctx* c) {
     if (err != cudaSuccess) { cudaGraphDestroy(g); return MSC_ERR_CUDA; }
 
     CK(cudaGraphConditionalHandleCreate(&h_iter, body_step, 0, 0));
-    void* a_setup[] = {&st, &h_iter};
+    int cond1 = 1;
+    void* a_setup[] = {&st, &h_iter, &cond1};
     cudaGraphNode_t setup = add_kernel(body_step, {}, (const void*)k_step_setup, dim3(1), dim3(1), 0, a_setup, &err);
     void* a_begin[] = {&st, &fbase, (void*)&fstride, &mbuf, &h, &sites};
     cudaGraphNode_t begin = add_kernel(body_step, {setup}, (const void*)k_step_begin<L, T>, dim3(fgrid),
@@ -262,10 +273,10 @@ int build_march_graph(msc_ctx* c) {
     cudaGraph_t body_iter;
     cudaGraphNode_t wit = add_cond(body_step, {begin}, h_iter, cudaGraphCondTypeWhile, &body_iter, &err);
     if (err != cudaSuccess) { cudaGraphDestroy(g); return MSC_ERR_CUDA; }
-    void* a_end[] = {&st, &fbase, (void*)&fstride, &mbuf, &sites};
+    void* a_end[] = {&st, &fbase, (void*)&fstride, &mbuf, &h, &sites};
     cudaGraphNode_t end = add_kernel(body_step, {wit}, (const void*)k_step_end<L, T>, dim3(fgrid),
                                      dim3(kFieldThreads), 0, a_end, &err);
-    void* a_fin[] = {&st, &iters, &max_steps, &h_step};
+    void* a_fin[] = {&st, &iters, &max_steps, &h_step, &cond1};
     add_kernel(body_step, {end}, (const void*)k_step_finish, dim3(1), dim3(1), 0, a_fin, &err);
 
     CK(cudaGraphConditionalHandleCreate(&h_corr, body_iter, 0, 0));
@@ -274,6 +285,7 @@ int build_march_graph(msc_ctx* c) {
         Sweep2Args<T> A = sweep2_args_graph<T>(c);
         A.h_iter = h_iter;
         A.h_corr = h_corr;
+        A.cond = 1;
         void* a_sw[] = {&A};
         sw = add_kernel(body_iter, {}, (const void*)k_sweep2<T, false, true>, dim3(sweep2_geometry(c->desc.n).blocks),
                         dim3(kSweepWarps * 32), 0, a_sw, &err);
@@ -281,6 +293,7 @@ int build_march_graph(msc_ctx* c) {
         Sweep3Args<T> A = sweep3_args_graph<T>(c);
         A.h_iter = h_iter;
         A.h_corr = h_corr;
+        A.cond = 1;
         void* a_sw[] = {&A};
         sw = add_kernel(body_iter, {}, (const void*)k_sweep3<T, false, true>, dim3(A.g.blocks),
                         dim3(A.g.threads), A.g.smem, a_sw, &err);
@@ -313,29 +326,28 @@ int build_explicit_graph(msc_ctx* c) {
     cudaGraph_t body;
     add_cond(g, {arm}, h_ex, cudaGraphCondTypeWhile, &body, &err);
     if (err != cudaSuccess) { cudaGraphDestroy(g); return MSC_ERR_CUDA; }
-    if (L::D == 2) {
-        Sweep2Args<T> A = sweep2_args_graph<T>(c);
-        Sweep2Args<T> B = A;
-        A.ex_dir = 0; A.ex_count = 0;
-        B.ex_dir = 1; B.ex_count = 1; B.h_ex = h_ex;
-        void* aa[] = {&A};
-        void* ab[] = {&B};
-        const int blocks = sweep2_geometry(c->desc.n).blocks;
-        cudaGraphNode_t n1 = add_kernel(body, {}, (const void*)k_sweep2<T, true, true>, dim3(blocks),
-                                        dim3(kSweepWarps * 32), 0, aa, &err);
-        add_kernel(body, {n1}, (const void*)k_sweep2<T, true, true>, dim3(blocks), dim3(kSweepWarps * 32), 0,
-                   ab, &err);
-    } else {
-        Sweep3Args<T> A = sweep3_args_graph<T>(c);
-        Sweep3Args<T> B = A;
-        A.ex_dir = 0; A.ex_count = 0;
-        B.ex_dir = 1; B.ex_count = 1; B.h_ex = h_ex;
-        void* aa[] = {&A};
-        void* ab[] = {&B};
-        cudaGraphNode_t n1 = add_kernel(body, {}, (const void*)k_sweep3<T, true, true>, dim3(A.g.blocks),
-                                        dim3(A.g.threads), A.g.smem, aa, &err);
-        add_kernel(body, {n1}, (const void*)k_sweep3<T, true, true>, dim3(A.g.blocks), dim3(A.g.threads),
-                   A.g.smem, ab, &err);
+    // kExplicitUnroll steps per loop iteration, alternating a->b and b->a; the last one counts
+    cudaGraphNode_t prev = nullptr;
+    for (int i = 0; i < kExplicitUnroll; ++i) {
+        std::vector<cudaGraphNode_t> deps;
+        if (prev) deps.push_back(prev);
+        if (L::D == 2) {
+            Sweep2Args<T> A = sweep2_args_graph<T>(c);
+            A.ex_dir = i & 1;
+            A.ex_count = i == kExplicitUnroll - 1;
+            A.h_ex = h_ex;
+            void* aa[] = {&A};
+            prev = add_kernel(body, deps, (const void*)k_sweep2<T, true, true>, dim3(sweep2_geometry(c->desc.n).blocks),
+                              dim3(kSweepWarps * 32), 0, aa, &err);
+        } else {
+            Sweep3Args<T> A = sweep3_args_graph<T>(c);
+            A.ex_dir = i & 1;
+            A.ex_count = i == kExplicitUnroll - 1;
+            A.h_ex = h_ex;
+            void* aa[] = {&A};
+            prev = add_kernel(body, deps, (const void*)k_sweep3<T, true, true>, dim3(A.g.blocks), dim3(A.g.threads),
+                              A.g.smem, aa, &err);
+        }
     }
     if (err != cudaSuccess) { cudaGraphDestroy(g); return MSC_ERR_CUDA; }
     cudaGraphExec_t x;
@@ -352,19 +364,20 @@ int run_explicit(msc_ctx* c, int n_steps) {
         if (rc) return rc;
     }
     DevState* st = at<DevState>(c, c->lay.state);
-    const int pairs = n_steps / 2;
-    const int odd = n_steps & 1;
-    k_ex_setup<<<1, 1, 0, c->stream>>>(st, pairs);
+    const int blocks = n_steps / kExplicitUnroll;
+    const int rem = n_steps % kExplicitUnroll;
+    const int odd = rem & 1;
+    k_ex_setup<<<1, 1, 0, c->stream>>>(st, blocks);
     CK(cudaGetLastError());
-    if (pairs > 0) CK(cudaGraphLaunch(c->x_ex, c->stream));
-    if (odd) {
+    if (blocks > 0) CK(cudaGraphLaunch(c->x_ex, c->stream));
+    for (int i = 0; i < rem; ++i) {  // the remainder alternates a->b, b->a, ... as in the loop body
         if (L::D == 2) {
             Sweep2Args<T> A = sweep2_args_graph<T>(c);
-            A.ex_dir = 0;
+            A.ex_dir = i & 1;
             k_sweep2<T, true, true><<<sweep2_geometry(c->desc.n).blocks, kSweepWarps * 32, 0, c->stream>>>(A);
         } else {
             Sweep3Args<T> A = sweep3_args_graph<T>(c);
-            A.ex_dir = 0;
+            A.ex_dir = i & 1;
             k_sweep3<T, true, true><<<A.g.blocks, A.g.threads, A.g.smem, c->stream>>>(A);
         }
         CK(cudaGetLastError());
@@ -395,6 +408,87 @@ int run_init(msc_ctx* c, const double* p, const double* u, int on_device) {
     CK(cudaGetLastError());
     k_moments<L, T><<<grid_for(c->sites), kFieldThreads, 0, c->stream>>>(f0, m0, m1, c->sites);
     CK(cudaGetLastError());
+    return MSC_OK;
+}
+
+int refresh_tables(msc_ctx* c) {
+    if (!c->coef_dirty) return MSC_OK;
+    const size_t nm = solve_modes(c->desc.dim, c->desc.n);
+    int blocks = (int)((2 * nm + 255) / 256);
+    if (blocks > 148 * 16) blocks = 148 * 16;
+    k_solve_tables<<<blocks, 256, 0, c->stream>>>(at<double>(c, c->lay.coef), c->desc.dim, c->desc.n,
+                                                  c->params.dt, c->params.nu);
+    CK(cudaGetLastError());
+    c->coef_dirty = false;
+    return MSC_OK;
+}
+
+int read_state(msc_ctx* c, DevState* hs);
+
+// The march of msc_march driven from the host: the same kernels launched one by one, with the
+// acceptance decision read back after every sweep.  For profilers that do not descend into
+// conditional graph nodes, and for debugging.
+template <class L, typename T>
+int run_stepwise(msc_ctx* c, int n_steps) {
+    using C = typename Cplx<T>::type;
+    int rc = set_smem_limits<T>(c->desc.dim, c->desc.n);
+    if (rc) return rc;
+    DevState* st = at<DevState>(c, c->lay.state);
+    T* fbase = at<T>(c, c->lay.fbuf);
+    const size_t fstride = c->lay.fstride / sizeof(T);
+    double* mbuf = at<double>(c, c->lay.mbuf);
+    T* h = at<T>(c, c->lay.h);
+    const int fgrid = grid_for(c->sites);
+    cudaGraphConditionalHandle none = 0;
+    Spec2Args<T> S = spec3_args<T>(c->desc.n, c->logn, 0.0, c->params.nu, at<T>(c, c->lay.pr), at<C>(c, c->lay.spec),
+                                   at<T>(c, c->lay.dm), at<C>(c, c->lay.tw), st, at<double>(c, c->lay.coef));
+    LaunchDesc spec[5];
+    int nspec = 0;
+    if (c->desc.dim == 2) {
+        const int n = c->desc.n;
+        const RowGeom rg = row_geometry(n, 3, n);
+        S.nf = 3;
+        S.rows = n;
+        S.P = rg.P;
+        spec[0] = {(const void*)k_rowfft_fwd<T>, dim3(rg.blocks), dim3(rg.threads), spec_row_smem<T>(n, rg.P)};
+        spec[1] = {(const void*)k_colsolve<T>, dim3(n / 4 + 1), dim3(spec2_col_threads(n)), spec2_col_smem<T>(n)};
+        spec[2] = {(const void*)k_rowfft_inv<T>, dim3(rg.blocks), dim3(rg.threads), spec_row_smem<T>(n, rg.P)};
+        nspec = 3;
+    } else {
+        spectral3_launches<T>(c->desc.n, spec);
+        nspec = 5;
+    }
+    void* sargs[] = {&S};
+    k_set_target<<<1, 1, 0, c->stream>>>(st, n_steps);
+    DevState hs;
+    for (int step = 0; step < n_steps; ++step) {
+        k_step_setup<<<1, 1, 0, c->stream>>>(st, none, 0);
+        k_step_begin<L, T><<<fgrid, kFieldThreads, 0, c->stream>>>(st, fbase, fstride, mbuf, h, c->sites);
+        for (;;) {
+            if (L::D == 2) {
+                Sweep2Args<T> A = sweep2_args_graph<T>(c);
+                k_sweep2<T, false, true><<<sweep2_geometry(c->desc.n).blocks, kSweepWarps * 32, 0, c->stream>>>(A);
+            } else {
+                Sweep3Args<T> A = sweep3_args_graph<T>(c);
+                k_sweep3<T, false, true><<<A.g.blocks, A.g.threads, A.g.smem, c->stream>>>(A);
+            }
+            CK(cudaGetLastError());
+            rc = read_state(c, &hs);
+            if (rc) return rc;
+            if (hs.lift)
+                for (int i = 0; i < nspec; ++i) {
+                    if (c->desc.dim == 3) spec3_pass_args<T>(c->desc.n, &S, i);
+                    CK(cudaLaunchKernel(spec[i].fn, spec[i].grid, spec[i].block, sargs, spec[i].smem, c->stream));
+                }
+            if (hs.accepted || hs.status != MSC_OK) break;
+        }
+        k_step_end<L, T><<<fgrid, kFieldThreads, 0, c->stream>>>(st, fbase, fstride, mbuf, h, c->sites);
+        k_step_finish<<<1, 1, 0, c->stream>>>(st, at<int>(c, c->lay.iters), c->desc.max_steps, none, 0);
+        CK(cudaGetLastError());
+        rc = read_state(c, &hs);
+        if (rc) return rc;
+        if (hs.status != MSC_OK || hs.steps_target <= 0) break;
+    }
     return MSC_OK;
 }
 
@@ -444,6 +538,7 @@ int msc_create(msc_ctx** out, const msc_lattice_desc* desc, void* ws, size_t byt
     c->lay = L;
     c->ws = (unsigned char*)ws;
     c->stream = (cudaStream_t)stream;
+    c->coef_dirty = true;
     // zero the state, the reduction counter and the correction (first lift reads it only if set)
     if (cudaMemsetAsync(c->ws + L.state, 0, sizeof(DevState), c->stream) != cudaSuccess ||
         cudaMemsetAsync(c->ws + L.counter, 0, 256, c->stream) != cudaSuccess) {
@@ -452,9 +547,9 @@ int msc_create(msc_ctx** out, const msc_lattice_desc* desc, void* ws, size_t byt
     }
     const int n = desc->n;
     if (desc->precision == MSC_FP64)
-        k_twiddles<double2><<<(n / 2 + 255) / 256, 256, 0, c->stream>>>((double2*)(c->ws + L.tw), n);
+        k_twiddles<double2><<<(n + 255) / 256, 256, 0, c->stream>>>((double2*)(c->ws + L.tw), n);
     else
-        k_twiddles<float2><<<(n / 2 + 255) / 256, 256, 0, c->stream>>>((float2*)(c->ws + L.tw), n);
+        k_twiddles<float2><<<(n + 255) / 256, 256, 0, c->stream>>>((float2*)(c->ws + L.tw), n);
     if (cudaGetLastError() != cudaSuccess) {
         free(c);
         return MSC_ERR_CUDA;
@@ -484,6 +579,7 @@ int msc_set_params(msc_ctx* c, const msc_params* p) {
         c->x_march = nullptr;
         c->g_march = nullptr;
     }
+    if (!c->params_set || p->dt != c->params.dt || p->nu != c->params.nu) c->coef_dirty = true;
     c->params = *p;
     c->params_set = true;
     k_set_params<<<1, 1, 0, c->stream>>>(at<DevState>(c, c->lay.state), *p);
@@ -518,10 +614,25 @@ int msc_march(msc_ctx* c, int n_steps) {
         if (rc) return rc;
     }
     if (c->params.replay && n_steps > c->desc.max_steps) return MSC_ERR_ARG;
+    int rc = refresh_tables(c);
+    if (rc) return rc;
     k_set_target<<<1, 1, 0, c->stream>>>(at<DevState>(c, c->lay.state), n_steps);
     CK(cudaGetLastError());
     CK(cudaGraphLaunch(c->x_march, c->stream));
     return MSC_OK;
+}
+
+int msc_march_stepwise(msc_ctx* c, int n_steps) {
+    if (!c || n_steps < 0) return MSC_ERR_ARG;
+    if (!c->params_set || !c->fields_set) return MSC_ERR_STATE;
+    if (c->params.replay && n_steps > c->desc.max_steps) return MSC_ERR_ARG;
+    int rc = refresh_tables(c);
+    if (rc) return rc;
+    if (c->desc.dim == 2)
+        return c->desc.precision == MSC_FP64 ? run_stepwise<D2Q9, double>(c, n_steps)
+                                             : run_stepwise<D2Q9, float>(c, n_steps);
+    return c->desc.precision == MSC_FP64 ? run_stepwise<D3Q19, double>(c, n_steps)
+                                         : run_stepwise<D3Q19, float>(c, n_steps);
 }
 
 int msc_explicit_march(msc_ctx* c, int n_steps) {
@@ -696,6 +807,7 @@ int msc_load_state(msc_ctx* c, const void* blob, size_t bytes) {
     s.m_prev = 1;
     s.steps_done = sd;
     s.status = MSC_OK;
+    s.prepared = 0;
     CK(cudaMemcpy(c->ws + c->lay.state, &s, sizeof(DevState), cudaMemcpyHostToDevice));
     c->fields_set = true;
     return MSC_OK;
@@ -708,7 +820,7 @@ size_t msc_stage_scratch_bytes(int dim, int n, int precision) {
     size_t o = 0;
     o = align_up(o + 256, 256);                                  // counter
     o = align_up(o + (size_t)sweep_blocks_for(dim, n, precision) * 8, 256);  // partials
-    o = align_up(o + (size_t)(n / 2) * (precision == MSC_FP64 ? 16 : 8), 256);  // twiddles
+    o = align_up(o + (size_t)n * (precision == MSC_FP64 ? 16 : 8), 256);  // twiddles
     o = align_up(o + spec_bytes(dim, n, precision), 256);         // half spectrum
     return o;
 }
@@ -731,7 +843,7 @@ StageScratch stage_scratch(int dim, int n, int precision, void* base) {
     s.partial = (double*)(b + o);
     o = align_up(o + (size_t)sweep_blocks_for(dim, n, precision) * 8, 256);
     s.tw = b + o;
-    o = align_up(o + (size_t)(n / 2) * (precision == MSC_FP64 ? 16 : 8), 256);
+    o = align_up(o + (size_t)n * (precision == MSC_FP64 ? 16 : 8), 256);
     s.spec = b + o;
     return s;
 }
@@ -787,7 +899,7 @@ int stage_shadow(int dim, int n, double a, double nu, const void* pr, void* dm, 
                  cudaStream_t stream) {
     using C = typename Cplx<T>::type;
     StageScratch S = stage_scratch(dim, n, sizeof(T) == 8 ? MSC_FP64 : MSC_FP32, scratch);
-    k_twiddles<C><<<(n / 2 + 255) / 256, 256, 0, stream>>>((C*)S.tw, n);
+    k_twiddles<C><<<(n + 255) / 256, 256, 0, stream>>>((C*)S.tw, n);
     CK(cudaGetLastError());
     int rc = set_smem_limits<T>(dim, n);
     if (rc) return rc;
@@ -800,14 +912,16 @@ int stage_shadow(int dim, int n, double a, double nu, const void* pr, void* dm, 
         A.tw = (const C*)S.tw;
         A.n = n;
         A.logn = ilog2(n);
+        const RowGeom rg = row_geometry(n, 3, n);
         A.nf = 3;
         A.rows = n;
+        A.P = rg.P;
         A.a = a;
         A.nu = nu;
         A.st = nullptr;
-        k_rowfft_fwd<T><<<spec2_row_blocks(n), kFftThreads, spec2_row_smem<T>(n), stream>>>(A);
-        k_colsolve<T><<<n / 4 + 1, kFftThreads, spec2_col_smem<T>(n), stream>>>(A);
-        k_rowfft_inv<T><<<spec2_row_blocks(n), kFftThreads, spec2_row_smem<T>(n), stream>>>(A);
+        k_rowfft_fwd<T><<<rg.blocks, rg.threads, spec_row_smem<T>(n, rg.P), stream>>>(A);
+        k_colsolve<T><<<n / 4 + 1, spec2_col_threads(n), spec2_col_smem<T>(n), stream>>>(A);
+        k_rowfft_inv<T><<<rg.blocks, rg.threads, spec_row_smem<T>(n, rg.P), stream>>>(A);
         CK(cudaGetLastError());
         return MSC_OK;
     }

@@ -1,157 +1,118 @@
-// 2D periodic shadow correction (Section 3.2, Eqs. shadow-cont .. shadow-update):
+// Periodic shadow correction (Section 3.2, Eqs. shadow-cont .. shadow-update):
 //   dm = F^{-1}[ chi(k) H(k)^{-1} F[P r] ]
-// as three kernels over the 3 residual-moment fields (r_p, r_mx, r_my):
-//   k_rowfft_fwd   real rows -> half spectrum along x, keeping 0 <= j_x <= n/4 (the mask,
-//                  Eq. shadow-mask; negative j_x follow from Hermitian symmetry).  Two real rows
-//                  share one complex FFT.
-//   k_colsolve     per kept j_x column: FFT along y, closed-form Schur solve (Eq. schur) in FP64
-//                  at |j_y| <= n/4, zero elsewhere, scaling by 1/N_Omega, inverse FFT along y.
-//   k_rowfft_inv   Hermitian-extended half spectrum -> real rows (two rows per complex FFT).
-// Half-spectrum layout: spec[c][y][j_x], c in {p, x, y}, j_x in [0, n/4], row stride n/4 + 1.
+// Shared pieces and the 2D kernels.  Transform convention Eq. fft-convention, wavenumbers
+// Eq. wavenumbers, mask |j_alpha| <= n/4 (Eq. shadow-mask), closed-form Schur solve Eq. schur.
+//
+//   k_rowfft_fwd   real rows -> half spectrum along x, keeping 0 <= j_x <= n/4 (negative j_x
+//                  follow from Hermitian symmetry).  Two real rows share one complex FFT; a block
+//                  transforms 2P consecutive rows of one field.
+//   k_colsolve     (2D) per kept j_x: FFT along y, FP64 Schur solve at |j_y| <= n/4 (zero
+//                  elsewhere, 1/N_Omega folded in), inverse FFT along y.
+//   k_rowfft_inv   Hermitian-extended half spectrum -> real rows.
+// Half-spectrum layout: spec[c][j_x][row], c the field, j_x in [0, n/4], row the index of the
+// length-n line along x (2D: row = y; 3D: row = z n + y), so that the transforms along y (and z)
+// read contiguous memory and the row passes read or write 2P-element contiguous segments.
 #pragma once
 
 #include "common.cuh"
 #include "fft.cuh"
+#include "march.cuh"
 
 namespace msc {
 
 constexpr int kFftThreads = 256;
 constexpr double kCs2 = 1.0 / 3.0;
 
-// number of length-n transforms one block runs together so that every thread has butterflies
-__host__ __device__ inline int ffts_per_block(int n) {
-    const int p = (2 * kFftThreads) / n;
-    return p < 1 ? 1 : p;
+template <typename T>
+struct Spec2Args {
+    const T* pr;                   // nf x sites residual moments
+    typename Cplx<T>::type* spec;  // nf x (n/4+1) x rows half spectrum
+    T* dm;                         // nf x sites correction
+    const typename Cplx<T>::type* tw;
+    int n, logn;
+    int P;               // row passes: complex transforms (row pairs) per block
+    int G;               // 3D passes: lines per block
+    int nf;              // number of fields (d + 1)
+    int rows;            // lines of length n per field (n in 2D, n^2 in 3D)
+    double a, nu;
+    const DevState* st;  // graph mode: a and q from the state
+    const double* coef;  // graph mode: per-mode solve coefficients for q = 1, 2 (k_solve_tables)
+};
+
+// pick the coefficient table of the current BDF order (graph mode) or none (stage calls)
+__device__ inline const double* solve_table(const double* coef, const DevState* st, int dim, int n) {
+    if (!coef) return nullptr;
+    const int q = ((const volatile DevState*)st)->q;
+    return coef + (size_t)(q - 1) * 4 * solve_modes(dim, n);
+}
+
+// Row-pass blocks: P row pairs (one field, consecutive rows), P a power of two dividing rows/2,
+// at most 4096/n so that a block has at most 256 threads (one radix-16 butterfly each), at least
+// 4 where possible so the transposed spectrum segments are >= 64 bytes, fewer when that would
+// leave fewer than two blocks per SM.
+struct RowGeom {
+    int P, threads, blocks;
+};
+inline RowGeom row_geometry(int n, int nf, int rows) {
+    const int npairs = nf * (rows / 2);
+    int P = 4096 / n;
+    if (P < 1) P = 1;
+    if (P > rows / 2) P = rows / 2;
+    while (P > 4 && npairs / P < 2 * 148) P >>= 1;
+    int t = P * n / 16;
+    t = (t + 31) / 32 * 32;
+    if (t < 32) t = 32;
+    return {P, t, npairs / P};
 }
 
 template <typename T>
-struct Spec2Args {
-    const T* pr;       // 3 x n^2 residual moments
-    typename Cplx<T>::type* spec;  // 3 x n x (n/4+1)
-    T* dm;             // 3 x n^2 correction
-    const typename Cplx<T>::type* tw;
-    int n, logn;
-    int nf;              // number of fields (d + 1)
-    int rows;            // rows of length n per field (n in 2D, n^2 in 3D)
-    double a, nu;
-    const DevState* st;  // graph mode: a from the state
-};
+inline size_t spec_row_smem(int n, int P) {
+    return (size_t)P * padded_len(n) * sizeof(typename Cplx<T>::type);
+}
 
-// rows (c, y) and (c, y+1) of the 3 fields form one complex row; 3n/2 row pairs in total
+// 2P consecutive rows (c, y0 .. y0 + 2P - 1) form P complex rows
 template <typename T>
 __global__ void __launch_bounds__(kFftThreads) k_rowfft_fwd(Spec2Args<T> A) {
     using C = typename Cplx<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* s = reinterpret_cast<C*>(smem_raw);
-    const int n = A.n, logn = A.logn;
+    const int n = A.n, logn = A.logn, P = A.P, plen = padded_len(n);
     const int nx4 = n / 4 + 1;
-    const int P = ffts_per_block(n);
     const int hr = A.rows / 2;
-    const int npairs = A.nf * hr;
-    const int pair0 = blockIdx.x * P;
-    const size_t NN = (size_t)n * A.rows;
-    // load with bit-reversed placement
+    const int pair0 = blockIdx.x * P;  // P divides hr: all pairs of the block lie in one field
+    const int c = pair0 / hr;
+    const int y0 = 2 * (pair0 - c * hr);
+    const T* rows = A.pr + ((size_t)c * A.rows + y0) * n;
+    // unrolled so that the global loads of several iterations are in flight together
+#pragma unroll 8
     for (int t = threadIdx.x; t < P * n; t += blockDim.x) {
         const int p = t >> logn;
         const int x = t & (n - 1);
-        const int pair = pair0 + p;
         C z;
-        z.x = T(0); z.y = T(0);
-        if (pair < npairs) {
-            const int c = pair / hr;
-            const int y = 2 * (pair - c * hr);
-            const T* row = A.pr + c * NN + (size_t)y * n;
-            z.x = row[x];
-            z.y = row[n + x];
+        z.x = rows[(size_t)(2 * p) * n + x];
+        z.y = rows[(size_t)(2 * p + 1) * n + x];
+        s[p * plen + pad(x)] = z;
+    }
+    __syncthreads();
+    fft_stockham<C, false>(s, n, logn, P, A.tw);
+    // split the two real transforms; thread t -> (j_x, row r in 0..2P-1), r fastest
+    C* out = A.spec + (size_t)c * nx4 * A.rows + y0;
+    const int l2p = __ffs(2 * P) - 1;  // P is a power of two
+    for (int t = threadIdx.x; t < 2 * P * nx4; t += blockDim.x) {
+        const int r = t & (2 * P - 1);
+        const int jx = t >> l2p;
+        const int p = r >> 1;
+        const C zj = s[p * plen + pad(jx)];
+        const C zm = s[p * plen + pad((n - jx) & (n - 1))];
+        C v;
+        if ((r & 1) == 0) {  // (zj + conj(zm)) / 2
+            v.x = T(0.5) * (zj.x + zm.x);
+            v.y = T(0.5) * (zj.y - zm.y);
+        } else {             // (zj - conj(zm)) / (2i)
+            v.x = T(0.5) * (zj.y + zm.y);
+            v.y = T(-0.5) * (zj.x - zm.x);
         }
-        s[p * n + bitrev(x, logn)] = z;
-    }
-    __syncthreads();
-    fft_dit(s, n, logn, P, A.tw, false);
-    // split the two real transforms and keep 0 <= j <= n/4
-    for (int t = threadIdx.x; t < P * nx4; t += blockDim.x) {
-        const int p = t / nx4;
-        const int jx = t - p * nx4;
-        const int pair = pair0 + p;
-        if (pair >= npairs) continue;
-        const int c = pair / hr;
-        const int y = 2 * (pair - c * hr);
-        const C zj = s[p * n + jx];
-        const C zm = s[p * n + ((n - jx) & (n - 1))];
-        C xa, xb;
-        xa.x = T(0.5) * (zj.x + zm.x);
-        xa.y = T(0.5) * (zj.y - zm.y);
-        // (zj - conj(zm)) / (2i)
-        xb.x = T(0.5) * (zj.y + zm.y);
-        xb.y = T(-0.5) * (zj.x - zm.x);
-        C* out = A.spec + (size_t)c * A.rows * nx4;
-        out[(size_t)y * nx4 + jx] = xa;
-        out[(size_t)(y + 1) * nx4 + jx] = xb;
-    }
-}
-
-// one block per kept j_x column, all three fields
-template <typename T>
-__global__ void __launch_bounds__(kFftThreads) k_colsolve(Spec2Args<T> A) {
-    using C = typename Cplx<T>::type;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* s = reinterpret_cast<C*>(smem_raw);
-    const int n = A.n, logn = A.logn;
-    const int nx4 = n / 4 + 1;
-    const int jx = blockIdx.x;
-    C* sp = A.spec;
-    for (int t = threadIdx.x; t < 3 * n; t += blockDim.x) {
-        const int c = t >> logn;
-        const int y = t & (n - 1);
-        s[c * n + bitrev(y, logn)] = sp[((size_t)c * n + y) * nx4 + jx];
-    }
-    __syncthreads();
-    fft_dit(s, n, logn, 3, A.tw, false);
-    // Schur solve of H(k) [dp, du] = [r_p, r_m] at every masked wavevector (Eq. schur)
-    const double a = A.st ? ((const volatile DevState*)A.st)->a : A.a;
-    const double nu = A.nu;
-    const double two_pi_n = 6.283185307179586476925286766559 / (double)n;
-    const double kx = two_pi_n * (double)jx;
-    const double scale = 1.0 / ((double)n * (double)n);
-    for (int jy = threadIdx.x; jy < n; jy += blockDim.x) {
-        const int jys = jy <= n / 2 ? jy : jy - n;
-        C* p0 = s + jy;
-        C* p1 = s + n + jy;
-        C* p2 = s + 2 * n + jy;
-        if (jys > n / 4 || jys < -(n / 4)) {
-            C z; z.x = T(0); z.y = T(0);
-            *p0 = z; *p1 = z; *p2 = z;
-            continue;
-        }
-        const double ky = two_pi_n * (double)jys;
-        const double k2 = kx * kx + ky * ky;
-        const double dv = a + nu * k2;
-        const double idv = 1.0 / dv;
-        const double iD = 1.0 / (a + kCs2 * k2 * idv);
-        const double rpx = (double)p0->x, rpy = (double)p0->y;
-        const double rxx = (double)p1->x, rxy = (double)p1->y;
-        const double ryx = (double)p2->x, ryy = (double)p2->y;
-        // kr = k . r_m (complex)
-        const double krx = kx * rxx + ky * ryx, kry = kx * rxy + ky * ryy;
-        // dp = (r_p - i kr / dv) / D ;  -i z = (z.y, -z.x)
-        const double dpx = (rpx + kry * idv) * iD;
-        const double dpy = (rpy - krx * idv) * iD;
-        // du = (r_m - cs2 i k dp) / dv ;  i dp = (-dp.y, dp.x)
-        const double uxx = (rxx + kCs2 * kx * dpy) * idv;
-        const double uxy = (rxy - kCs2 * kx * dpx) * idv;
-        const double uyx = (ryx + kCs2 * ky * dpy) * idv;
-        const double uyy = (ryy - kCs2 * ky * dpx) * idv;
-        C z;
-        z.x = (T)(dpx * scale); z.y = (T)(dpy * scale); *p0 = z;
-        z.x = (T)(uxx * scale); z.y = (T)(uxy * scale); *p1 = z;
-        z.x = (T)(uyx * scale); z.y = (T)(uyy * scale); *p2 = z;
-    }
-    __syncthreads();
-    fft_dif(s, n, logn, 3, A.tw, true);
-    for (int t = threadIdx.x; t < 3 * n; t += blockDim.x) {
-        const int c = t >> logn;
-        const int i = t & (n - 1);
-        sp[((size_t)c * n + bitrev(i, logn)) * nx4 + jx] = s[t];
+        out[(size_t)jx * A.rows + r] = v;
     }
 }
 
@@ -160,65 +121,126 @@ __global__ void __launch_bounds__(kFftThreads) k_rowfft_inv(Spec2Args<T> A) {
     using C = typename Cplx<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* s = reinterpret_cast<C*>(smem_raw);
-    const int n = A.n, logn = A.logn;
+    const int n = A.n, logn = A.logn, P = A.P, plen = padded_len(n);
     const int nx4 = n / 4 + 1;
-    const int P = ffts_per_block(n);
     const int hr = A.rows / 2;
-    const int npairs = A.nf * hr;
     const int pair0 = blockIdx.x * P;
-    const size_t NN = (size_t)n * A.rows;
+    const int c = pair0 / hr;
+    const int y0 = 2 * (pair0 - c * hr);
+    const C* in = A.spec + (size_t)c * nx4 * A.rows + y0;
+    // Z[p][j] = Xa + i Xb (j <= n/4), conj(Xa[n-j]) + i conj(Xb[n-j]) (n-j <= n/4), else 0;
+    // thread t -> (j, p), p fastest, so the spectrum reads are contiguous in the row index
+    const int lp = __ffs(P) - 1;
+#pragma unroll 8
     for (int t = threadIdx.x; t < P * n; t += blockDim.x) {
-        const int p = t >> logn;
-        const int j = t & (n - 1);
-        const int pair = pair0 + p;
+        const int p = t & (P - 1);
+        const int j = t >> lp;
         C z;
         z.x = T(0); z.y = T(0);
-        if (pair < npairs) {
-            const int c = pair / hr;
-            const int y = 2 * (pair - c * hr);
-            const C* ra = A.spec + ((size_t)c * A.rows + y) * nx4;
-            const C* rb = ra + nx4;
-            if (j <= n / 4) {  // Z = Xa + i Xb
-                const C xa = ra[j], xb = rb[j];
-                z.x = xa.x - xb.y;
-                z.y = xa.y + xb.x;
-            } else if (n - j <= n / 4) {  // Z = conj(Xa[n-j]) + i conj(Xb[n-j])
-                const C xa = ra[n - j], xb = rb[n - j];
-                z.x = xa.x + xb.y;
-                z.y = xb.x - xa.y;
-            }
+        if (j <= n / 4) {
+            const C xa = in[(size_t)j * A.rows + 2 * p], xb = in[(size_t)j * A.rows + 2 * p + 1];
+            z.x = xa.x - xb.y;
+            z.y = xa.y + xb.x;
+        } else if (n - j <= n / 4) {
+            const C xa = in[(size_t)(n - j) * A.rows + 2 * p], xb = in[(size_t)(n - j) * A.rows + 2 * p + 1];
+            z.x = xa.x + xb.y;
+            z.y = xb.x - xa.y;
         }
-        s[t] = z;
+        s[p * plen + pad(j)] = z;
     }
     __syncthreads();
-    fft_dif(s, n, logn, P, A.tw, true);
+    fft_stockham<C, true>(s, n, logn, P, A.tw);
+    T* rows = A.dm + ((size_t)c * A.rows + y0) * n;
     for (int t = threadIdx.x; t < P * n; t += blockDim.x) {
         const int p = t >> logn;
-        const int i = t & (n - 1);
-        const int pair = pair0 + p;
-        if (pair >= npairs) continue;
-        const int c = pair / hr;
-        const int y = 2 * (pair - c * hr);
-        const int x = bitrev(i, logn);
-        const C z = s[t];
-        T* row = A.dm + c * NN + (size_t)y * n;
-        row[x] = z.x;
-        row[n + x] = z.y;
+        const int x = t & (n - 1);
+        const C z = s[p * plen + pad(x)];
+        rows[(size_t)(2 * p) * n + x] = z.x;
+        rows[(size_t)(2 * p + 1) * n + x] = z.y;
     }
 }
 
+// Schur solve at one masked wavevector in FP64: dp = A rp - i B (k.rm), du = Dv rm - i Cc k dp
+template <typename C, int D>
+__device__ __forceinline__ void schur_apply(C* v[D + 1], const double* kv, const double* cf) {
+    using T = decltype(v[0]->x);
+    double rx[D + 1], ry[D + 1];
+#pragma unroll
+    for (int i = 0; i <= D; ++i) { rx[i] = (double)v[i]->x; ry[i] = (double)v[i]->y; }
+    double krx = 0.0, kry = 0.0;
+#pragma unroll
+    for (int al = 0; al < D; ++al) { krx += kv[al] * rx[al + 1]; kry += kv[al] * ry[al + 1]; }
+    const double dpx = cf[0] * rx[0] + cf[1] * kry;
+    const double dpy = cf[0] * ry[0] - cf[1] * krx;
+    v[0]->x = (T)dpx;
+    v[0]->y = (T)dpy;
+#pragma unroll
+    for (int al = 0; al < D; ++al) {
+        const double ck = cf[2] * kv[al];
+        v[al + 1]->x = (T)(cf[3] * rx[al + 1] + ck * dpy);
+        v[al + 1]->y = (T)(cf[3] * ry[al + 1] - ck * dpx);
+    }
+}
+
+// 2D: one block per kept j_x column, all three fields
 template <typename T>
-inline size_t spec2_row_smem(int n) {
-    return (size_t)ffts_per_block(n) * n * sizeof(typename Cplx<T>::type);
+__global__ void __launch_bounds__(sizeof(T) == 8 ? 384 : 768) k_colsolve(Spec2Args<T> A) {
+    using C = typename Cplx<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* s = reinterpret_cast<C*>(smem_raw);
+    const int n = A.n, logn = A.logn, plen = padded_len(n);
+    const int nx4 = n / 4 + 1;
+    const int jx = blockIdx.x;
+    C* col = A.spec + (size_t)jx * n;  // spec[c][jx][y] at col + c * nx4 * n + y
+    const size_t fs = (size_t)nx4 * n;
+#pragma unroll 4
+    for (int t = threadIdx.x; t < 3 * n; t += blockDim.x) {
+        const int c = t >> logn;
+        const int y = t & (n - 1);
+        s[c * plen + pad(y)] = col[c * fs + y];
+    }
+    __syncthreads();
+    fft_stockham<C, false>(s, n, logn, 3, A.tw);
+    const double a = A.st ? ((const volatile DevState*)A.st)->a : A.a;
+    const double* tab = solve_table(A.coef, A.st, 2, n);
+    const double two_pi_n = 6.283185307179586476925286766559 / (double)n;
+    const double scale = 1.0 / ((double)n * (double)n);
+    double kv[2];
+    kv[0] = two_pi_n * (double)jx;
+    for (int jy = threadIdx.x; jy < n; jy += blockDim.x) {
+        const int jys = jy <= n / 2 ? jy : jy - n;
+        C* v[3] = {s + pad(jy), s + plen + pad(jy), s + 2 * plen + pad(jy)};
+        if (jys > n / 4 || jys < -(n / 4)) {
+            C z; z.x = T(0); z.y = T(0);
+            *v[0] = z; *v[1] = z; *v[2] = z;
+            continue;
+        }
+        kv[1] = two_pi_n * (double)jys;
+        double cf[4];
+        if (tab) {
+            const double* tt = tab + 4 * ((size_t)(jys + n / 4) * nx4 + jx);
+            cf[0] = tt[0]; cf[1] = tt[1]; cf[2] = tt[2]; cf[3] = tt[3];
+        } else {
+            solve_coefficients(a, A.nu, kv[0] * kv[0] + kv[1] * kv[1], scale, cf);
+        }
+        schur_apply<C, 2>(v, kv, cf);
+    }
+    __syncthreads();
+    fft_stockham<C, true>(s, n, logn, 3, A.tw);
+    for (int t = threadIdx.x; t < 3 * n; t += blockDim.x) {
+        const int c = t >> logn;
+        const int y = t & (n - 1);
+        col[c * fs + y] = s[c * plen + pad(y)];
+    }
+}
+
+inline int spec2_col_threads(int n) {
+    const int t = (3 * n / 16 + 31) / 32 * 32;
+    return t < 32 ? 32 : t;
 }
 template <typename T>
 inline size_t spec2_col_smem(int n) {
-    return (size_t)3 * n * sizeof(typename Cplx<T>::type);
+    return (size_t)3 * padded_len(n) * sizeof(typename Cplx<T>::type);
 }
-inline int spec_row_blocks(int n, int nf, int rows) {
-    const int P = ffts_per_block(n);
-    return (nf * (rows / 2) + P - 1) / P;
-}
-inline int spec2_row_blocks(int n) { return spec_row_blocks(n, 3, n); }
 
 }  // namespace msc

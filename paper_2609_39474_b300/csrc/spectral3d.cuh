@@ -3,9 +3,10 @@
 // with H(k) the 4 x 4 shadow matrix solved in closed form (Eq. schur).  Five kernels:
 //   k_rowfft_fwd (x, real -> half spectrum 0 <= j_x <= n/4), k_ypass<fwd> (complex FFT along y),
 //   k_zsolve (FFT along z, FP64 Schur solve at |j_y|, |j_z| <= n/4, inverse FFT along z; only the
-//   n/2 + 1 masked j_y planes are visited), k_ypass<inv> (inverse along y reading only masked j_y),
+//   n/2 + 1 masked j_y lines are visited), k_ypass<inv> (inverse along y reading only masked j_y),
 //   k_rowfft_inv (Hermitian half spectrum -> real rows).
-// Spectrum layout: spec[c][z][y][j_x], row stride n/4 + 1.
+// Spectrum layout: spec[c][j_x][z][y] (the row index of the x pass is z n + y), so the y lines
+// are contiguous and the z lines of G consecutive j_y are G-element contiguous segments.
 #pragma once
 
 #include "common.cuh"
@@ -22,158 +23,147 @@ struct LaunchDesc {
 
 inline size_t spec3_bytes(int n, size_t celem) { return (size_t)4 * n * n * (n / 4 + 1) * celem; }
 
-// j_x columns per block so that one block's shared arrays stay near 32 KB
-template <typename T>
-__host__ __device__ inline int ypass_cols(int n) {
-    int g = (int)(32768 / ((size_t)n * sizeof(typename Cplx<T>::type)));
-    const int nx4 = n / 4 + 1;
-    if (g < 1) g = 1;
-    if (g > nx4) g = nx4;
-    return g;
+// y pass: G consecutive z planes per block, one radix-16 butterfly per thread (G n / 16 <= 256)
+__host__ __device__ inline int ypass_lines(int n) {
+    int g = 4096 / n;
+    return g > n ? n : (g < 1 ? 1 : g);
 }
+// z pass: 4 fields x G masked j_y lines per block (4 G n / 16 <= 768 FP32, 384 FP64)
 template <typename T>
-__host__ __device__ inline int zsolve_cols(int n) {
-    int g = (int)(65536 / ((size_t)4 * n * sizeof(typename Cplx<T>::type)));
-    const int nx4 = n / 4 + 1;
-    if (g < 1) g = 1;
-    if (g > nx4) g = nx4;
-    return g;
+__host__ __device__ inline int zsolve_lines(int n) {
+    int g = (sizeof(T) == 8 ? 1024 : 2048) / n;  // power of two
+    return g < 1 ? 1 : g;
 }
 
-// one block per (field c, plane z, chunk of G j_x columns): transform along y
 template <typename T, bool INV>
 __global__ void __launch_bounds__(kFftThreads) k_ypass(Spec2Args<T> A) {
     using C = typename Cplx<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* s = reinterpret_cast<C*>(smem_raw);
-    const int n = A.n, logn = A.logn;
-    const int nx4 = n / 4 + 1;
-    const int G = ypass_cols<T>(n);
-    const int nchunk = (nx4 + G - 1) / G;
-    const int chunk = blockIdx.x % nchunk;
-    const int plane = blockIdx.x / nchunk;  // c * n + z
-    const int jx0 = chunk * G;
-    const int ng = min(G, nx4 - jx0);
-    C* base = A.spec + (size_t)plane * n * nx4;
+    const int n = A.n, logn = A.logn, plen = padded_len(n);
+    const int G = A.G;
+    const int zch = n / G;
+    const int line0 = blockIdx.x * G;         // (c * nx4 + jx) * n + z0, G divides n
+    C* base = A.spec + (size_t)line0 * n;     // G contiguous lines of length n
+    (void)zch;
+#pragma unroll 8
     for (int t = threadIdx.x; t < G * n; t += blockDim.x) {
         const int g = t >> logn;
         const int y = t & (n - 1);
         C z;
         z.x = T(0); z.y = T(0);
-        if (g < ng) {
-            const int ys = y <= n / 2 ? y : y - n;
-            if (!INV || (ys <= n / 4 && ys >= -(n / 4))) z = base[(size_t)y * nx4 + jx0 + g];
-        }
-        if (INV) s[g * n + y] = z;
-        else s[g * n + bitrev(y, logn)] = z;
+        const int ys = y <= n / 2 ? y : y - n;
+        if (!INV || (ys <= n / 4 && ys >= -(n / 4))) z = base[t];
+        s[g * plen + pad(y)] = z;
     }
     __syncthreads();
-    if (INV) fft_dif(s, n, logn, G, A.tw, true);
-    else fft_dit(s, n, logn, G, A.tw, false);
+    fft_stockham<C, INV>(s, n, logn, G, A.tw);
     for (int t = threadIdx.x; t < G * n; t += blockDim.x) {
         const int g = t >> logn;
-        const int i = t & (n - 1);
-        if (g >= ng) continue;
-        const int y = INV ? bitrev(i, logn) : i;
-        base[(size_t)y * nx4 + jx0 + g] = s[t];
+        const int y = t & (n - 1);
+        base[t] = s[g * plen + pad(y)];
     }
 }
 
-// one block per (masked j_y, chunk of G j_x columns): all 4 fields along z
+// one block per (j_x, chunk of G masked j_y): the z lines of all 4 fields
 template <typename T>
-__global__ void __launch_bounds__(kFftThreads) k_zsolve(Spec2Args<T> A) {
+__global__ void __launch_bounds__(sizeof(T) == 8 ? 384 : 768) k_zsolve(Spec2Args<T> A) {
     using C = typename Cplx<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* s = reinterpret_cast<C*>(smem_raw);  // [4][G][n]
-    const int n = A.n, logn = A.logn;
-    const int nx4 = n / 4 + 1;
-    const int G = zsolve_cols<T>(n);
-    const int nchunk = (nx4 + G - 1) / G;
-    const int chunk = blockIdx.x % nchunk;
-    const int jyk = blockIdx.x / nchunk;         // 0 .. n/2
-    const int jys = jyk - n / 4;                  // signed j_y in [-n/4, n/4]
-    const int jy = jys & (n - 1);
-    const int jx0 = chunk * G;
-    const int ng = min(G, nx4 - jx0);
-    const size_t zstride = (size_t)n * nx4;
-    const size_t fstride = (size_t)n * n * nx4;
-    C* sp = A.spec;
+    C* s = reinterpret_cast<C*>(smem_raw);  // line (c, g) at (c G + g) plen
+    const int n = A.n, logn = A.logn, plen = padded_len(n);
+    const int nx4 = n / 4 + 1, ny = n / 2 + 1;
+    const int G = A.G;  // a power of two
+    const int lg = __ffs(G) - 1;
+    const int nch = (ny + G - 1) / G;
+    const int jx = blockIdx.x / nch;
+    const int jyk0 = (blockIdx.x - jx * nch) * G;
+    const int ng = min(G, ny - jyk0);
+    const size_t n2 = (size_t)n * n;
+    const size_t fstride = (size_t)nx4 * n2;
+    C* sp = A.spec + (size_t)jx * n2;  // + c * fstride + z * n + jy
+#pragma unroll 4
     for (int t = threadIdx.x; t < 4 * G * n; t += blockDim.x) {
-        const int z = t & (n - 1);
-        const int cg = t >> logn;  // c * G + g
-        const int c = cg / G;
-        const int g = cg - c * G;
+        const int g = t & (G - 1);
+        const int cz = t >> lg;
+        const int z = cz & (n - 1);
+        const int c = cz >> logn;
         C v;
         v.x = T(0); v.y = T(0);
-        if (g < ng) v = sp[c * fstride + (size_t)z * zstride + (size_t)jy * nx4 + jx0 + g];
-        s[cg * n + bitrev(z, logn)] = v;
+        if (g < ng) {
+            const int jy = (jyk0 + g - n / 4) & (n - 1);
+            v = sp[c * fstride + (size_t)z * n + jy];
+        }
+        s[(c * G + g) * plen + pad(z)] = v;
     }
     __syncthreads();
-    fft_dit(s, n, logn, 4 * G, A.tw, false);
+    fft_stockham<C, false>(s, n, logn, 4 * G, A.tw);
     const double a = A.st ? ((const volatile DevState*)A.st)->a : A.a;
-    const double nu = A.nu;
+    const double* tab = solve_table(A.coef, A.st, 3, n);
     const double two_pi_n = 6.283185307179586476925286766559 / (double)n;
-    const double ky = two_pi_n * (double)jys;
     const double scale = 1.0 / ((double)n * (double)n * (double)n);
     for (int t = threadIdx.x; t < G * n; t += blockDim.x) {
         const int g = t >> logn;
         const int jz = t & (n - 1);
         const int jzs = jz <= n / 2 ? jz : jz - n;
-        C* p0 = s + (0 * G + g) * n + jz;
-        C* p1 = s + (1 * G + g) * n + jz;
-        C* p2 = s + (2 * G + g) * n + jz;
-        C* p3 = s + (3 * G + g) * n + jz;
+        C* v[4] = {s + (0 * G + g) * plen + pad(jz), s + (1 * G + g) * plen + pad(jz),
+                   s + (2 * G + g) * plen + pad(jz), s + (3 * G + g) * plen + pad(jz)};
         if (jzs > n / 4 || jzs < -(n / 4) || g >= ng) {
             C zz; zz.x = T(0); zz.y = T(0);
-            *p0 = zz; *p1 = zz; *p2 = zz; *p3 = zz;
+            *v[0] = zz; *v[1] = zz; *v[2] = zz; *v[3] = zz;
             continue;
         }
-        const double kx = two_pi_n * (double)(jx0 + g);
-        const double kz = two_pi_n * (double)jzs;
-        const double k2 = kx * kx + ky * ky + kz * kz;
-        const double dv = a + nu * k2;
-        const double idv = 1.0 / dv;
-        const double iD = 1.0 / (a + kCs2 * k2 * idv);
-        const double rpx = (double)p0->x, rpy = (double)p0->y;
-        const double r1x = (double)p1->x, r1y = (double)p1->y;
-        const double r2x = (double)p2->x, r2y = (double)p2->y;
-        const double r3x = (double)p3->x, r3y = (double)p3->y;
-        const double krx = kx * r1x + ky * r2x + kz * r3x;
-        const double kry = kx * r1y + ky * r2y + kz * r3y;
-        const double dpx = (rpx + kry * idv) * iD;
-        const double dpy = (rpy - krx * idv) * iD;
-        C v;
-        v.x = (T)(dpx * scale); v.y = (T)(dpy * scale); *p0 = v;
-        v.x = (T)((r1x + kCs2 * kx * dpy) * idv * scale); v.y = (T)((r1y - kCs2 * kx * dpx) * idv * scale); *p1 = v;
-        v.x = (T)((r2x + kCs2 * ky * dpy) * idv * scale); v.y = (T)((r2y - kCs2 * ky * dpx) * idv * scale); *p2 = v;
-        v.x = (T)((r3x + kCs2 * kz * dpy) * idv * scale); v.y = (T)((r3y - kCs2 * kz * dpx) * idv * scale); *p3 = v;
+        const int jys = jyk0 + g - n / 4;
+        const double kv[3] = {two_pi_n * (double)jx, two_pi_n * (double)jys, two_pi_n * (double)jzs};
+        double cf[4];
+        if (tab) {
+            const size_t mi = (size_t)jx + (size_t)nx4 * ((size_t)(jyk0 + g) + (size_t)ny * (jzs + n / 4));
+            const double* tt = tab + 4 * mi;
+            cf[0] = tt[0]; cf[1] = tt[1]; cf[2] = tt[2]; cf[3] = tt[3];
+        } else {
+            solve_coefficients(a, A.nu, kv[0] * kv[0] + kv[1] * kv[1] + kv[2] * kv[2], scale, cf);
+        }
+        schur_apply<C, 3>(v, kv, cf);
     }
     __syncthreads();
-    fft_dif(s, n, logn, 4 * G, A.tw, true);
+    fft_stockham<C, true>(s, n, logn, 4 * G, A.tw);
     for (int t = threadIdx.x; t < 4 * G * n; t += blockDim.x) {
-        const int i = t & (n - 1);
-        const int cg = t >> logn;
-        const int c = cg / G;
-        const int g = cg - c * G;
+        const int g = t & (G - 1);
+        const int cz = t >> lg;
+        const int z = cz & (n - 1);
+        const int c = cz >> logn;
         if (g >= ng) continue;
-        const int z = bitrev(i, logn);
-        sp[c * fstride + (size_t)z * zstride + (size_t)jy * nx4 + jx0 + g] = s[t];
+        const int jy = (jyk0 + g - n / 4) & (n - 1);
+        sp[c * fstride + (size_t)z * n + jy] = s[(c * G + g) * plen + pad(z)];
     }
 }
 
 template <typename T>
 inline void spectral3_launches(int n, LaunchDesc* L) {
     using C = typename Cplx<T>::type;
-    const int nx4 = n / 4 + 1;
+    const int nx4 = n / 4 + 1, ny = n / 2 + 1;
     const int rows = n * n;
-    const size_t rsm = (size_t)ffts_per_block(n) * n * sizeof(C);
-    const int yg = ypass_cols<T>(n), zg = zsolve_cols<T>(n);
-    const int ych = (nx4 + yg - 1) / yg, zch = (nx4 + zg - 1) / zg;
-    L[0] = {(const void*)k_rowfft_fwd<T>, dim3(spec_row_blocks(n, 4, rows)), dim3(kFftThreads), rsm};
-    L[1] = {(const void*)k_ypass<T, false>, dim3(4 * n * ych), dim3(kFftThreads), (size_t)yg * n * sizeof(C)};
-    L[2] = {(const void*)k_zsolve<T>, dim3((n / 2 + 1) * zch), dim3(kFftThreads), (size_t)4 * zg * n * sizeof(C)};
-    L[3] = {(const void*)k_ypass<T, true>, dim3(4 * n * ych), dim3(kFftThreads), (size_t)yg * n * sizeof(C)};
-    L[4] = {(const void*)k_rowfft_inv<T>, dim3(spec_row_blocks(n, 4, rows)), dim3(kFftThreads), rsm};
+    const RowGeom rg = row_geometry(n, 4, rows);
+    const size_t rsm = spec_row_smem<T>(n, rg.P);
+    const int yg = ypass_lines(n), zg = zsolve_lines<T>(n);
+    const int yth = ((yg * n / 16 + 31) / 32) * 32;
+    const int zth = ((4 * zg * n / 16 + 31) / 32) * 32;
+    const size_t ysm = (size_t)yg * padded_len(n) * sizeof(C);
+    const size_t zsm = (size_t)4 * zg * padded_len(n) * sizeof(C);
+    const int zblocks = nx4 * ((ny + zg - 1) / zg);
+    L[0] = {(const void*)k_rowfft_fwd<T>, dim3(rg.blocks), dim3(rg.threads), rsm};
+    L[1] = {(const void*)k_ypass<T, false>, dim3(4 * nx4 * n / yg), dim3(yth < 32 ? 32 : yth), ysm};
+    L[2] = {(const void*)k_zsolve<T>, dim3(zblocks), dim3(zth < 32 ? 32 : zth), zsm};
+    L[3] = {(const void*)k_ypass<T, true>, dim3(4 * nx4 * n / yg), dim3(yth < 32 ? 32 : yth), ysm};
+    L[4] = {(const void*)k_rowfft_inv<T>, dim3(rg.blocks), dim3(rg.threads), rsm};
+}
+
+// The five launches take one argument block whose P and G fields differ per pass: the row
+// passes read P, the y pass and the z pass read G.  The launchers below set both.
+template <typename T>
+inline void spec3_pass_args(int n, Spec2Args<T>* A, int pass) {
+    A->P = row_geometry(n, 4, n * n).P;
+    A->G = pass == 2 ? zsolve_lines<T>(n) : ypass_lines(n);
 }
 
 template <typename T>
@@ -188,9 +178,11 @@ int set_spec3_smem_limits(int n) {
 
 template <typename T>
 inline Spec2Args<T> spec3_args(int n, int logn, double a, double nu, const T* pr, typename Cplx<T>::type* spec,
-                               T* dm, const typename Cplx<T>::type* tw, const DevState* st) {
+                               T* dm, const typename Cplx<T>::type* tw, const DevState* st,
+                               const double* coef = nullptr) {
     Spec2Args<T> A;
     memset(&A, 0, sizeof(A));
+    A.coef = coef;
     A.pr = pr;
     A.spec = spec;
     A.dm = dm;
@@ -202,6 +194,7 @@ inline Spec2Args<T> spec3_args(int n, int logn, double a, double nu, const T* pr
     A.a = a;
     A.nu = nu;
     A.st = st;
+    spec3_pass_args<T>(n, &A, 0);
     return A;
 }
 
@@ -212,10 +205,12 @@ int launch_spectral3(int n, int logn, double a, double nu, const T* pr, typename
     Spec2Args<T> A = spec3_args<T>(n, logn, a, nu, pr, spec, dm, tw, nullptr);
     LaunchDesc L[5];
     spectral3_launches<T>(n, L);
-    void* args[] = {&A};
-    for (int i = 0; i < 5; ++i)
+    for (int i = 0; i < 5; ++i) {
+        spec3_pass_args<T>(n, &A, i);
+        void* args[] = {&A};
         if (cudaLaunchKernel(L[i].fn, L[i].grid, L[i].block, args, L[i].smem, stream) != cudaSuccess)
             return MSC_ERR_CUDA;
+    }
     return MSC_OK;
 }
 

@@ -45,6 +45,7 @@ struct Sweep2Args {
     const int* replay_counts;
     int max_steps;
     cudaGraphConditionalHandle h_iter, h_corr;
+    int cond;  // set the graph conditionals (0 when the march is driven from the host)
     // explicit graph mode: 0 = a->b, 1 = b->a; ex_count: decrement the pair counter
     int ex_dir, ex_count;
     cudaGraphConditionalHandle h_ex;
@@ -54,7 +55,7 @@ struct Sweep2Args {
 __device__ inline void march_after_sweep(DevState* st, double total, double qsites, double* hist,
                                          int hist_cap, const int* replay_counts, int max_steps,
                                          cudaGraphConditionalHandle h_iter,
-                                         cudaGraphConditionalHandle h_corr) {
+                                         cudaGraphConditionalHandle h_corr, int cond) {
     const double R = sqrt(total / qsites);
     const int ell = st->iter + 1;
     st->iter = ell;
@@ -85,8 +86,10 @@ __device__ inline void march_after_sweep(DevState* st, double total, double qsit
         corr = st->corrector;
     }
     st->lift = corr;
-    cudaGraphSetConditional(h_iter, cont);
-    cudaGraphSetConditional(h_corr, corr);
+    if (cond) {
+        cudaGraphSetConditional(h_iter, cont);
+        cudaGraphSetConditional(h_corr, corr);
+    }
 }
 
 template <typename T, bool EXPLICIT, bool GRAPH>
@@ -114,8 +117,8 @@ __global__ void __launch_bounds__(kSweepWarps * 32) k_sweep2(Sweep2Args<T> A) {
             fout = A.fbase + (size_t)(A.ex_dir ? sa : sb) * A.fstride;
             if (A.ex_count && blockIdx.x == 0 && threadIdx.x == 0) {
                 DevState* st = A.st;
-                const int left = st->ex_pairs_left - 1;
-                st->ex_pairs_left = left;
+                const int left = st->ex_loops_left - 1;
+                st->ex_loops_left = left;
                 cudaGraphSetConditional(A.h_ex, left > 0 ? 1u : 0u);
             }
         } else {
@@ -143,14 +146,25 @@ __global__ void __launch_bounds__(kSweepWarps * 32) k_sweep2(Sweep2Args<T> A) {
         for (int k = 0; k < 9; ++k) { Ar[k] = T(0); Br[k] = T(0); ftp[k] = T(0); }
         T ssq_f = T(0);
 
+        // software pipeline: the loads of row j+1 are issued before row j is collided
+        T nf[9], ndp = T(0), ndx = T(0), ndy = T(0), nh0 = T(0), nh1 = T(0), nh2 = T(0);
+        auto load_row = [&](int jr) {
+            const size_t id = (size_t)(jr & nmask) * n + x;
+#pragma unroll
+            for (int k = 0; k < 9; ++k) nf[k] = fin[k * NN + id];
+            if (!EXPLICIT) {
+                if (lift) { ndp = dm[id]; ndx = dm[NN + id]; ndy = dm[2 * NN + id]; }
+                nh0 = hh[id]; nh1 = hh[NN + id]; nh2 = hh[2 * NN + id];
+            }
+        };
+        load_row(y0 - 1);
         for (int j = y0 - 1; j <= y0 + A.hb; ++j) {
-            const int y = j & nmask;
-            const size_t idx = (size_t)y * n + x;
             T f[9];
 #pragma unroll
-            for (int k = 0; k < 9; ++k) f[k] = fin[k * NN + idx];
+            for (int k = 0; k < 9; ++k) f[k] = nf[k];
+            const T dp = ndp, dux = ndx, duy = ndy, h0 = nh0, h1 = nh1, h2 = nh2;
+            if (j < y0 + A.hb) load_row(j + 1);
             if (!EXPLICIT && lift) {  // trial f = f_T,prev + E dm   (Eq. lift)
-                const T dp = dm[idx], dux = dm[NN + idx], duy = dm[2 * NN + idx];
 #pragma unroll
                 for (int k = 0; k < 9; ++k)
                     f[k] += (T)L::w(k) * (dp + T(3) * (T(L::cx(k)) * dux + T(L::cy(k)) * duy));
@@ -167,7 +181,6 @@ __global__ void __launch_bounds__(kSweepWarps * 32) k_sweep2(Sweep2Args<T> A) {
             if (EXPLICIT) {
                 p = rho; ux = jx; uy = jy;
             } else {  // half-source reconstruction and source moments (Eqs. macro-reconstruct, source-moments)
-                const T h0 = hh[idx], h1 = hh[NN + idx], h2 = hh[2 * NN + idx];
                 p = (rho + h0 * T(0.5)) * inv;
                 ux = (jx + h1 * T(0.5)) * inv;
                 uy = (jy + h2 * T(0.5)) * inv;
@@ -258,7 +271,7 @@ __global__ void __launch_bounds__(kSweepWarps * 32) k_sweep2(Sweep2Args<T> A) {
         *A.counter = 0u;
         if (GRAPH) {
             march_after_sweep(A.st, total, 9.0 * (double)NN, A.hist, A.hist_cap, A.replay_counts,
-                              A.max_steps, A.h_iter, A.h_corr);
+                              A.max_steps, A.h_iter, A.h_corr, A.cond);
         } else {
             *A.sumsq_out = total;
         }

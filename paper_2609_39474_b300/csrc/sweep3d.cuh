@@ -43,6 +43,7 @@ struct Sweep3Args {
     const int* replay_counts;
     int max_steps;
     cudaGraphConditionalHandle h_iter, h_corr;
+    int cond;
     int ex_dir, ex_count;
     cudaGraphConditionalHandle h_ex;
 };
@@ -96,8 +97,8 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 512) k_sweep3(Sweep3Arg
             fout = A.fbase + (size_t)(A.ex_dir ? sa : sb) * A.fstride;
             if (A.ex_count && blockIdx.x == 0 && threadIdx.x == 0) {
                 DevState* st = A.st;
-                const int left = st->ex_pairs_left - 1;
-                st->ex_pairs_left = left;
+                const int left = st->ex_loops_left - 1;
+                st->ex_loops_left = left;
                 cudaGraphSetConditional(A.h_ex, left > 0 ? 1u : 0u);
             }
         } else {
@@ -251,7 +252,7 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 512) k_sweep3(Sweep3Arg
         *A.counter = 0u;
         if (GRAPH) {
             march_after_sweep(A.st, total, 19.0 * (double)NNN, A.hist, A.hist_cap, A.replay_counts,
-                              A.max_steps, A.h_iter, A.h_corr);
+                              A.max_steps, A.h_iter, A.h_corr, A.cond);
         } else {
             *A.sumsq_out = total;
         }

@@ -89,6 +89,10 @@ class MscLattice:
     def march(self, n_steps: int):
         L.check(L.lib.msc_march(self._ctx, int(n_steps)), "msc_march")
 
+    def march_stepwise(self, n_steps: int):
+        """Host-driven march (same kernels, one launch each); for profiling and debugging."""
+        L.check(L.lib.msc_march_stepwise(self._ctx, int(n_steps)), "msc_march_stepwise")
+
     def explicit_march(self, n_steps: int):
         L.check(L.lib.msc_explicit_march(self._ctx, int(n_steps)), "msc_explicit_march")
 

@@ -249,3 +249,18 @@ def test_full_size_march_conserves_and_converges():
     m1 = [float(ph.sum()), float(uu[0].sum()), float(uu[1].sum())]
     scale = float(torch.abs(uu).max()) * N * N
     assert max(abs(a - b) for a, b in zip(m0, m1)) < 1e-6 * scale
+
+
+@pytest.mark.parametrize("dim,N,precision", [(2, 64, "fp64"), (2, 128, "fp32"), (3, 16, "fp64")])
+def test_stepwise_march_equals_graph_march(dim, N, precision):
+    # the host-driven march launches the same kernels: identical bits to the graph march
+    p, u = random_phase(N, dim, 1.0, seed=21, kmax=4)
+    out = []
+    for stepwise in (False, True):
+        L = _lattice(dim, N, precision)
+        L.set_params(dt=24.0, eps=1e-9)
+        L.init_fields(p, u)
+        (L.march_stepwise if stepwise else L.march)(5)
+        out.append((L.populations(), L.step_iters().tolist(), L.stats()))
+    assert np.array_equal(out[0][0], out[1][0])
+    assert out[0][1] == out[1][1] and out[0][2]["steps_done"] == out[1][2]["steps_done"] == 5

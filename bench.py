@@ -45,11 +45,21 @@ SWEEP_BYTES_PER_SITE_FP32 = 2 * 9 * 4 + 3 * 4 + 3 * 4 + 3 * 4  # f in/out, h, li
 ROOF_N = 4096  # out-of-L2 size for the sweep roofline (16.7 M sites, 1.8 GB per sweep)
 
 
-def workload(n: int):
-    p, u = random_phase(n, 2, 1.0, seed=1, kmax=8)
-    t_end = nint(0.15 * n * n)
-    u_ref = navier_stokes_reference(u, NU, float(t_end), M=64)
-    return p, u, t_end, u_ref
+# (dim, N): seed, band limit, T_end, n_min, candidate matrix (Table protocol; FP32 storage cannot
+# reach eps = 1e-12), NS reference resolution
+WORKLOADS = {
+    (2, 1024): dict(seed=1, kmax=8, t_end=nint(0.15 * 1024 ** 2), nmin=2, S=S_LIST, eps=EPS_LIST, M=64, steps=None),
+    (2, 256): dict(seed=1, kmax=8, t_end=nint(0.15 * 256 ** 2), nmin=2, S=S_LIST, eps=EPS_LIST, M=64, steps=None),
+    (3, 128): dict(seed=7, kmax=6, t_end=nint(0.075 * 128 ** 2), nmin=1, S=[3, 4, 5, 8, 16, 32, 64],
+                   eps=EPS_LIST, M=32, steps=100),
+}
+
+
+def workload(n: int, dim: int = 2):
+    w = WORKLOADS[(dim, n)]
+    p, u = random_phase(n, dim, 1.0, seed=w["seed"], kmax=w["kmax"])
+    u_ref = navier_stokes_reference(u, NU, float(w["t_end"]), M=w["M"], n_steps=w["steps"])
+    return p, u, w["t_end"], u_ref
 
 
 def load_peaks():
@@ -78,7 +88,7 @@ class ClockSampler:
         os.close(fd)
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -109,26 +119,19 @@ class ClockSampler:
 # our arm: the CUDA library through its Python binding
 # ---------------------------------------------------------------------------------------------------
 
-def run_ours(args, rank, world, dist):
-    import torch
-    from paper_2609_39474_b300 import lattice as PL
-
-    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
-    torch.cuda.set_device(dev)
-    n = args.n
-    p, u, t_end, u_ref = workload(n)
+def measure_workload(torch, PL, dev, dim, n, steps, warmup, dist=None, full=False):
+    """Explicit baseline, candidate search, timed MSC marches (and, for the headline, e2e)."""
+    w = WORKLOADS[(dim, n)]
+    p, u, t_end, u_ref = workload(n, dim)
     p_d = torch.as_tensor(p, device=dev).contiguous()
     u_d = torch.as_tensor(u, device=dev).contiguous()
-    p_h = torch.as_tensor(p).pin_memory()
-    u_h = torch.as_tensor(u).pin_memory()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # 256 MB > L2
-    stream = torch.cuda.current_stream(dev)
+    nspec = 3 if dim == 2 else 5
 
     def ev():
         return torch.cuda.Event(enable_timing=True)
 
-    L = PL.MscLattice(2, n, "fp32", max_steps=4096, hist_cap=1 << 16, device=str(dev))
-    rms_ref = rms_vector(u_ref)
+    L = PL.MscLattice(dim, n, "fp32", max_steps=4096, hist_cap=1 << 16, device=str(dev))
 
     # -- explicit LBM baseline: graph-captured, same kernels with no source (Section 4.1) --------
     def explicit_once():
@@ -148,8 +151,8 @@ def run_ours(args, rank, world, dist):
     e_ex = velocity_error(u_ex, u_ref)
 
     # -- candidate matrix (Table protocol), untimed selection ------------------------------------
-    def msc_once(S, eps, timed=True):
-        L.set_params(dt=t_end / S, eps=eps, kmax=KMAX, nmin=2)
+    def msc_once(S, eps):
+        L.set_params(dt=t_end / S, eps=eps, kmax=KMAX, nmin=w["nmin"])
         L.init_fields(p_d, u_d)
         flush.zero_()
         e0, e1 = ev(), ev()
@@ -159,43 +162,48 @@ def run_ours(args, rank, world, dist):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1), L.stats()
 
-    msc_once(S_LIST[0], EPS_LIST[0])  # builds the march graph outside any measurement
+    msc_once(w["S"][0], w["eps"][0])  # builds the march graph outside any measurement
     cands = []
-    for S in S_LIST:
-        for eps in EPS_LIST:
+    u0_rms = rms_vector(u)
+    for S in w["S"]:
+        for eps in w["eps"]:
             ms, st = msc_once(S, eps)
             ok = st["status"] == 0 and st["steps_done"] == S
             uu = L.fields()[1].cpu().numpy() if ok else None
             e = velocity_error(uu, u_ref) if ok else float("inf")
             rel = e / max(rms_vector(uu), 1e-12) if ok else float("inf")
-            cands.append(dict(S=S, eps=eps, ms=ms, err=e, rel=rel, ok=ok, inner=st["inner_total"]))
+            c = dict(S=S, eps=eps, ms=ms, err=e, rel=rel, ok=ok, inner=st["inner_total"])
+            if dim == 3 and ok:  # the paper's 3D engineering error: vs the explicit endpoint / initial RMS
+                c["rel_vs_explicit"] = velocity_error(uu, u_ex) / u0_rms
+            cands.append(c)
     matched = [c for c in cands if c["ok"] and c["err"] <= 3.0 * e_ex]
     onepct = [c for c in cands if c["ok"] and c["rel"] <= 0.01]
     if not matched:
-        raise SystemExit("no MSC candidate passes the matched-accuracy gate")
+        raise SystemExit(f"no MSC candidate passes the matched-accuracy gate (dim {dim}, N {n})")
     best = min(matched, key=lambda c: c["ms"])
     best1 = min(onepct, key=lambda c: c["ms"]) if onepct else None
 
     # -- timed region: K full marches of the matched winner --------------------------------------
-    for _ in range(args.warmup):
+    clocks = ClockSampler(dev.index) if full else None
+    if clocks:
+        clocks.start()
+    for _ in range(warmup):
         msc_once(best["S"], best["eps"])
-    clocks = ClockSampler(dev.index)
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
-    clocks.start()
     times, inner = [], []
     launches = 0
-    for _ in range(args.steps):
-        ms, st = msc_once(best["S"], best["eps"])
+    S = best["S"]
+    for _ in range(steps):
+        ms, st = msc_once(S, best["eps"])
         times.append(ms)
         inner.append(st["inner_total"])
-        S = best["S"]
-        # set_target + arm + 4 per physical step + 1 sweep per inner iteration + 3 spectral kernels per
-        # correction (every inner iteration that was not accepted)
-        launches += 2 + 4 * S + st["inner_total"] + 3 * (st["inner_total"] - S)
+        # set_target + arm, 4 per physical step (setup, begin, end, finish), one sweep per inner
+        # iteration and the spectral kernels of every correction (each non-accepted iteration)
+        launches += 2 + 4 * S + st["inner_total"] + nspec * (st["inner_total"] - S)
     torch.cuda.synchronize()
-    clk = clocks.stop()
+    clk = clocks.stop() if clocks else None
     ms_step = statistics.mean(times)
     if dist is not None:
         import torch.distributed as tdist
@@ -204,44 +212,61 @@ def run_ours(args, rank, world, dist):
         ms_step = float(t.item())
     u_msc = L.fields()[1].cpu().numpy()
     e_msc = velocity_error(u_msc, u_ref)
-    s_match = t_ex / ms_step
     s_1pct = t_ex / min(msc_once(best1["S"], best1["eps"])[0] for _ in range(3)) if best1 else None
-    inner_mlups = n * n * statistics.mean(inner) / (ms_step * 1e3)
-
-    # -- end to end through the C ABI with host buffers (H2D of p, u and D2H of the fields) -------
-    def e2e(fn):
-        flush.zero_()
-        torch.cuda.synchronize()
-        e0, e1 = ev(), ev()
-        e0.record()
-        L.init_fields(p_h, u_h)           # host -> device copy of p_hat and u
-        fn()
-        L.fields(on_device=False)         # device -> host copy of the result (synchronises)
-        e1.record()
-        torch.cuda.synchronize()
-        return e0.elapsed_time(e1)
-
-    L.set_params(dt=t_end / best["S"], eps=best["eps"], kmax=KMAX, nmin=2)
-    t_msc_e2e = statistics.mean(e2e(lambda: L.march(best["S"])) for _ in range(3))
-    t_ex_e2e = e2e(lambda: L.explicit_march(t_end))
-    bytes_io = 3 * n * n * 8
-
-    # -- roofline of the dominant kernel (the fused sweep) at an out-of-L2 size -------------------
-    roof = sweep_roofline(torch, PL, dev)
-    # the sweep at the benchmark size (L2-resident working set)
-    at_n = sweep_time(torch, PL, dev, n, reps=50)
-    L.close()
-
     res = {
-        "s_wall_matched": s_match, "s_wall_1pct": s_1pct, "t_explicit_ms": t_ex, "ms_per_step": ms_step,
-        "inner_mlups": inner_mlups, "candidate": best, "candidate_1pct": best1, "e_explicit": e_ex,
-        "e_msc": e_msc, "rms_ref": rms_ref, "clocks": clk, "launches": launches,
-        "e2e": {"value": t_ex_e2e / t_msc_e2e, "t_msc_ms": t_msc_e2e, "t_explicit_ms": t_ex_e2e,
-                "h2d_bytes_per_step": bytes_io, "d2h_bytes_per_step": bytes_io},
-        "roofline": roof, "sweep_at_n": at_n, "t_end": t_end,
-        "inner_per_step": statistics.mean(inner) / best["S"],
-        "candidates": [{k: c[k] for k in ("S", "eps", "ms", "rel", "ok", "inner")} for c in cands],
+        "workload": f"{'D2Q9' if dim == 2 else 'D3Q19'} periodic N={n} Re=1 random-phase seed {w['seed']} FP32",
+        "s_wall_matched": t_ex / ms_step, "s_wall_1pct": s_1pct, "t_explicit_ms": t_ex, "ms_per_step": ms_step,
+        "inner_mlups": n ** dim * statistics.mean(inner) / (ms_step * 1e3),
+        "inner_iters_per_step": statistics.mean(inner) / S, "candidate": best, "candidate_1pct": best1,
+        "e_explicit": e_ex, "e_msc": e_msc, "rms_ref": rms_vector(u_ref), "t_end": t_end,
+        "explicit_mlups": n ** dim * t_end / (t_ex * 1e3),
+        "candidates": [{k: c[k] for k in c if k != "err"} for c in cands],
+        "clocks": clk, "launches": launches,
     }
+    if full:
+        # -- end to end through the C ABI with host buffers (H2D of p, u and D2H of the fields) ---
+        p_h = torch.as_tensor(p).pin_memory()
+        u_h = torch.as_tensor(u).pin_memory()
+
+        def e2e(fn):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = ev(), ev()
+            e0.record()
+            L.init_fields(p_h, u_h)           # host -> device copy of p_hat and u
+            fn()
+            L.fields(on_device=False)         # device -> host copy of the result (synchronises)
+            e1.record()
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1)
+
+        L.set_params(dt=t_end / S, eps=best["eps"], kmax=KMAX, nmin=w["nmin"])
+        t_msc_e2e = statistics.mean(e2e(lambda: L.march(S)) for _ in range(3))
+        t_ex_e2e = e2e(lambda: L.explicit_march(t_end))
+        bytes_io = (dim + 1) * n ** dim * 8
+        res["e2e"] = {"value": t_ex_e2e / t_msc_e2e, "t_msc_ms": t_msc_e2e, "t_explicit_ms": t_ex_e2e,
+                      "h2d_bytes_per_step": bytes_io, "d2h_bytes_per_step": bytes_io}
+    L.close()
+    return res
+
+
+def run_ours(args, rank, world, dist):
+    import torch
+    from paper_2609_39474_b300 import lattice as PL
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    res = measure_workload(torch, PL, dev, 2, args.n, args.steps, args.warmup, dist, full=True)
+    # roofline of the dominant kernel (the fused sweep) at an out-of-L2 size, and at the bench size
+    res["roofline"] = sweep_roofline(torch, PL, dev)
+    res["sweep_at_n"] = sweep_time(torch, PL, dev, args.n, reps=50)
+    res["secondary"] = []
+    if not args.no_secondary:
+        for dim, n in ((2, 256), (3, 128)):
+            if (dim, n) != (2, args.n):
+                sec = measure_workload(torch, PL, dev, dim, n, max(3, min(args.steps, 10)), 3, dist, full=False)
+                sec.pop("clocks", None)
+                res["secondary"].append(sec)
     return res
 
 
@@ -388,11 +413,12 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true", help="skip the N=256 and D3Q19 N=128 workloads")
     ap.add_argument("--phase", default="all", choices=["all", "msc", "msc-stepwise", "sweep"],
                     help="profiling aids: 'msc' runs only the timed MSC marches of the default candidate, "
                          "'msc-stepwise' the same marches driven from the host (one launch per kernel, "
@@ -456,12 +482,14 @@ def main():
         "time_to_solution_ms": res["ms_per_step"],
         "explicit_ms": res["t_explicit_ms"],
         "inner_mlups": res["inner_mlups"],
-        "inner_iters_per_step": res["inner_per_step"],
+        "inner_iters_per_step": res["inner_iters_per_step"],
         "errors": {"e_msc": res["e_msc"], "e_explicit": res["e_explicit"], "rms_ref": res["rms_ref"],
                    "matched_gate": "e_msc <= 3 e_explicit"},
         "candidate_1pct": res["candidate_1pct"],
+        "explicit_mlups": res["explicit_mlups"],
         "sweep_at_n": res["sweep_at_n"],
         "candidates": res["candidates"],
+        "secondary": res["secondary"],
     }
     print(json.dumps(line))
     if dist is not None:

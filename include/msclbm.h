@@ -80,6 +80,12 @@ typedef struct {
     int corrector;  /* 1: MSC-LBM shadow correction (Algorithm 1); 0: plain Picard */
     int replay;     /* 1: accept step i at the inner count set by msc_set_replay_counts,
                        regardless of the residual (parity testing); 0: normal acceptance */
+    int warm_order; /* accepted population states used by the warm start of each step:
+                       3 = 3f^n - 3f^{n-1} + f^{n-2} (Section 3.1), 2 = 2f^n - f^{n-1}, 1 = f^n;
+                       0 = default: 3 for FP64 storage; for FP32 storage 2 on D2Q9 and 1 on
+                       D3Q19 (extrapolation grows FP32 rounding in weakly damped modes that lie
+                       outside the shadow mask).  The warm start sets only the first iterate,
+                       never the accepted fixed point. */
 } msc_params;
 
 typedef struct {

@@ -46,6 +46,8 @@ class MarchParams:
     nmin: int = 2             # minimum accepted inner count
     corrector: bool = True    # True: MSC-LBM; False: plain Picard dual-time stepping
     omega: Optional[tuple] = None  # None: operating point; (w+, w-): general TRT collision
+    warm_order: int = 3       # accepted states used by the warm start: 3 is Section 3.1 (cubic);
+                              # 1 (f^n) and 2 (2f^n - f^{n-1}) truncate it
 
 
 @dataclass
@@ -81,11 +83,18 @@ def init_state(lat: Lattice, p_hat: np.ndarray, u: np.ndarray) -> DualTimeState:
     return DualTimeState(lat, [f0], m0, m0.copy(), 0)
 
 
-def warm_start(f_hist: list) -> np.ndarray:
-    """Population-history extrapolation used to start the inner solve (Section 3.1)."""
-    if len(f_hist) == 1:
+def warm_start(f_hist: list, order: int = 3) -> np.ndarray:
+    """Population-history extrapolation used to start the inner solve (Section 3.1).
+
+    Uses min(order, available) accepted states: f^n, then 2f^n - f^{n-1}, then
+    3f^n - 3f^{n-1} + f^{n-2}.  The paper's rule is order 3; lower orders are offered for
+    reduced-precision storage, where the cubic extrapolation amplifies rounding in slowly damped
+    modes.  The warm start only sets the first iterate, never the accepted fixed point.
+    """
+    k = min(len(f_hist), order)
+    if k == 1:
         return f_hist[0].copy()
-    if len(f_hist) == 2:
+    if k == 2:
         return 2.0 * f_hist[0] - f_hist[1]
     return 3.0 * f_hist[0] - 3.0 * f_hist[1] + f_hist[2]
 
@@ -95,7 +104,7 @@ def physical_step(st: DualTimeState, prm: MarchParams, replay_count: Optional[in
     lat = st.lat
     q = 1 if st.steps_done == 0 else 2
     a, h = bdf_coefficients(q, prm.dt, st.m_n, st.m_nm1)
-    f = warm_start(st.f_hist)
+    f = warm_start(st.f_hist, prm.warm_order)
     res = []
     for ell in range(1, prm.kmax + 1):
         f_T = sweep(lat, f, a, h, prm.omega)

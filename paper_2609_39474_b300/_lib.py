@@ -28,7 +28,7 @@ class LatticeDesc(ctypes.Structure):
 class Params(ctypes.Structure):
     _fields_ = [("nu", ctypes.c_double), ("dt", ctypes.c_double), ("eps", ctypes.c_double),
                 ("kmax", ctypes.c_int), ("nmin", ctypes.c_int), ("corrector", ctypes.c_int),
-                ("replay", ctypes.c_int)]
+                ("replay", ctypes.c_int), ("warm_order", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):

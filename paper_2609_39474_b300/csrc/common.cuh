@@ -53,6 +53,7 @@ struct DevState {
     // parameters (set by msc_set_params)
     double nu, dt, eps;
     int kmax, nmin, corrector, replay;
+    int warm_order;         // accepted states used by the warm start (1..3)
     int params_ok;
     // physical-step bookkeeping
     int64_t steps_done;     // accepted steps since init

@@ -79,7 +79,7 @@ __global__ void k_step_begin(const DevState* __restrict__ st, T* __restrict__ fb
     if (vs->prepared) return;  // formed by the previous step's k_step_end
     const int q = vs->q;
     const double dt = vs->dt;
-    const int nav = vs->n_avail;
+    const int nav = vs->n_avail < vs->warm_order ? vs->n_avail : vs->warm_order;
     const size_t mstride = (size_t)(L::D + 1) * sites;
     const double* mn = mbuf + (size_t)vs->m_cur * mstride;
     const double* mnm1 = mbuf + (size_t)vs->m_prev * mstride;
@@ -138,7 +138,8 @@ __global__ void __launch_bounds__(kFieldThreads) k_step_end(const DevState* __re
     const double c1 = q == 1 ? 1.0 / dt : 4.0 / (2.0 * dt);
     const double c2 = q == 1 ? 0.0 : 1.0 / (2.0 * dt);
     const bool next = vs->status == MSC_OK && vs->steps_target > 1;
-    const int nav = vs->n_avail + 1 < 3 ? vs->n_avail + 1 : 3;  // accepted states after rotation
+    int nav = vs->n_avail + 1 < 3 ? vs->n_avail + 1 : 3;  // accepted states after rotation
+    if (nav > vs->warm_order) nav = vs->warm_order;
     const T* f0 = fbase + (size_t)vs->slot_fn[0] * fstride;
     const T* f1 = fbase + (size_t)vs->slot_fn[1] * fstride;
     T* trial = fbase + (size_t)vs->slot_nxt * fstride;
@@ -168,7 +169,10 @@ __global__ void __launch_bounds__(kFieldThreads) k_step_end(const DevState* __re
             if (next) h[o] = (T)fma(n1, mnew, -n2 * mc);
         }
         if (next) {
-            if (nav == 2) {
+            if (nav == 1) {
+#pragma unroll
+                for (int k = 0; k < L::Q; ++k) trial[k * sites + i] = fv[k];
+            } else if (nav == 2) {
 #pragma unroll
                 for (int k = 0; k < L::Q; ++k) trial[k * sites + i] = T(2) * fv[k] - f0[k * sites + i];
             } else {
@@ -231,6 +235,7 @@ __global__ void k_set_params(DevState* st, msc_params p) {
     st->nmin = p.nmin;
     st->corrector = p.corrector;
     st->replay = p.replay;
+    st->warm_order = p.warm_order;
     st->params_ok = 1;
 }
 

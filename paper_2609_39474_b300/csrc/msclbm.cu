@@ -570,7 +570,8 @@ void msc_destroy(msc_ctx* c) {
 int msc_set_params(msc_ctx* c, const msc_params* p) {
     if (!c || !p) return MSC_ERR_ARG;
     if (!(p->dt > 0.0) || !(p->eps >= 0.0) || !(p->nu > 0.0) || p->kmax < 1 || p->nmin < 1 ||
-        (p->corrector != 0 && p->corrector != 1) || (p->replay != 0 && p->replay != 1))
+        (p->corrector != 0 && p->corrector != 1) || (p->replay != 0 && p->replay != 1) || p->warm_order < 0 ||
+        p->warm_order > 3)
         return MSC_ERR_ARG;
     // the shadow solve bakes nu into the graph: rebuild if it changes
     if (c->params_set && p->nu != c->params.nu && c->x_march) {
@@ -581,8 +582,10 @@ int msc_set_params(msc_ctx* c, const msc_params* p) {
     }
     if (!c->params_set || p->dt != c->params.dt || p->nu != c->params.nu) c->coef_dirty = true;
     c->params = *p;
+    if (c->params.warm_order == 0)  // FP32 storage: the cubic rule grows rounding in weakly damped modes
+        c->params.warm_order = c->desc.precision == MSC_FP64 ? 3 : (c->desc.dim == 2 ? 2 : 1);
     c->params_set = true;
-    k_set_params<<<1, 1, 0, c->stream>>>(at<DevState>(c, c->lay.state), *p);
+    k_set_params<<<1, 1, 0, c->stream>>>(at<DevState>(c, c->lay.state), c->params);
     CK(cudaGetLastError());
     return MSC_OK;
 }

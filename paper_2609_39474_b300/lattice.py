@@ -67,10 +67,11 @@ class MscLattice:
             pass
 
     def set_params(self, dt: float, eps: float = 1e-8, nu: float = 1.0 / 6.0, kmax: int = 300,
-                   nmin=None, corrector: bool = True, replay: bool = False):
+                   nmin=None, corrector: bool = True, replay: bool = False, warm_order: int = 0):
+        """warm_order: 3 cubic (Section 3.1), 2 linear, 1 none; 0 = 3 for FP64, FP32: 2 (D2Q9) / 1 (D3Q19)."""
         if nmin is None:
             nmin = 2 if self.dim == 2 else 1
-        p = L.Params(nu, dt, eps, kmax, nmin, int(corrector), int(replay))
+        p = L.Params(nu, dt, eps, kmax, nmin, int(corrector), int(replay), int(warm_order))
         L.check(L.lib.msc_set_params(self._ctx, ctypes.byref(p)), "msc_set_params")
 
     def init_fields(self, p_hat, u):

@@ -23,7 +23,7 @@ def _lattice(dim, n, precision, **kw):
 def _replay_run(dim, n, precision, p, u, prm: OM.MarchParams, counts, corrector=True):
     L = _lattice(dim, n, precision)
     L.set_params(dt=prm.dt, eps=prm.eps, nu=prm.nu, kmax=prm.kmax, nmin=prm.nmin, corrector=corrector,
-                 replay=True)
+                 replay=True, warm_order=prm.warm_order)
     L.set_replay_counts(counts)
     L.init_fields(p, u)
     L.march(len(counts))
@@ -142,7 +142,8 @@ def test_3d_tgv_fp64_replay_parity():
 def test_fp32_storage_against_fp64_oracle(dim, N, steps):
     # FP32 deviation storage with FP64 history and solve: gate 1e-5 relative L2 in u
     p, u = random_phase(N, dim, 1.0, seed=12, kmax=8 if dim == 2 else 4)
-    prm = OM.MarchParams(dt=32.0, eps=1e-9, nmin=2 if dim == 2 else 1)
+    # the FP32 path's default warm start is the linear one (warm_order 2); the oracle uses the same
+    prm = OM.MarchParams(dt=32.0, eps=1e-9, nmin=2 if dim == 2 else 1, warm_order=2)
     st = OM.init_state(lattice_for_dim(dim), p, u)
     recs = OM.march(st, prm, steps)
     L = _replay_run(dim, N, "fp32", p, u, prm, [r.iters for r in recs])
@@ -264,3 +265,29 @@ def test_stepwise_march_equals_graph_march(dim, N, precision):
         out.append((L.populations(), L.step_iters().tolist(), L.stats()))
     assert np.array_equal(out[0][0], out[1][0])
     assert out[0][1] == out[1][1] and out[0][2]["steps_done"] == out[1][2]["steps_done"] == 5
+
+
+def test_fp32_long_run_stays_at_a_few_iterations():
+    # D2Q9 N = 256, Re = 1, 64 steps of dt = 153.6: with FP32 storage the cubic warm start grows the
+    # rounding in the staggered modes (k = (pi, 0), (0, pi): P Z E has eigenvalue -1 there, outside the
+    # mask) until the inner solve stalls; the linear warm start (FP32 default) keeps 2-3 iterations
+    N, S = 256, 64
+    p, u = random_phase(N, 2, 1.0, seed=1)
+    L = _lattice(2, N, "fp32")
+    L.set_params(dt=9830.0 / S, eps=1e-8)
+    L.init_fields(p, u)
+    L.march(S)
+    s = L.stats()
+    assert s["status"] == 0 and s["steps_done"] == S
+    assert np.max(L.step_iters()) <= 4
+
+
+@pytest.mark.parametrize("order", [1, 2])
+def test_warm_order_parity_fp64(order):
+    # truncated warm starts against the oracle with the same rule (replay mode)
+    p, u = tgv2d(32, 1.0)
+    prm = OM.MarchParams(dt=16.0, eps=1e-10, warm_order=order)
+    st = OM.init_state(lattice_for_dim(2), p, u)
+    recs = OM.march(st, prm, 5)
+    L = _replay_run(2, 32, "fp64", p, u, prm, [r.iters for r in recs])
+    assert rel_l2(host(L.fields()[1]), st.m_n[1:]) < 1e-12

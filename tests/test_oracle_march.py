@@ -146,3 +146,17 @@ def test_temporal_order_table_3d():
     # the final raw residuals span the printed range exactly (to the printed digits)
     lo, hi = g["final_residual_range"]
     assert abs(min(finals) / lo - 1) < 2e-3 and abs(max(finals) / hi - 1) < 2e-3
+
+
+def test_warm_start_orders():
+    f0, f1, f2 = (np.full((2, 2), v) for v in (3.0, 2.0, 0.5))
+    assert np.all(M.warm_start([f0, f1, f2], 3) == 3 * 3.0 - 3 * 2.0 + 0.5)
+    assert np.all(M.warm_start([f0, f1, f2], 2) == 2 * 3.0 - 2.0)
+    assert np.all(M.warm_start([f0, f1, f2], 1) == 3.0)
+    assert np.all(M.warm_start([f0], 3) == 3.0) and np.all(M.warm_start([f0, f1], 3) == 4.0)
+    # the cubic rule is exact for quadratic-in-time data, the linear one for linear data
+    t = np.array([3.0, 2.0, 1.0])
+    quad = [np.full(1, tt ** 2) for tt in t]
+    assert np.allclose(M.warm_start(quad, 3), 16.0)
+    lin = [np.full(1, 2 * tt + 1) for tt in t]
+    assert np.allclose(M.warm_start(lin, 2), 9.0)

@@ -86,6 +86,12 @@ typedef struct {
                        D3Q19 (extrapolation grows FP32 rounding in weakly damped modes that lie
                        outside the shadow mask).  The warm start sets only the first iterate,
                        never the accepted fixed point. */
+    int count_multiple; /* a step is accepted only at an inner count that is a multiple of this:
+                       1 = Algorithm 1 as printed; 2 = sweeps in pairs.  On D2Q9 the staggered
+                       modes k = (pi,0), (0,pi) have sweep eigenvalue -1 and lie outside the mask,
+                       so an odd count leaves them with a negative per-step factor that a warm
+                       start extrapolation amplifies; even counts keep the factor positive.
+                       0 = default: 2 for FP32 storage on D2Q9, else 1. */
 } msc_params;
 
 typedef struct {
@@ -220,6 +226,75 @@ int msc_equilibrium(int dim, int n, int precision, const double* p_hat, const do
    serialise them. */
 int msc_sweep_d2q9_noalloc(int n, int precision, double a, const void* f_in, const void* dm,
                            const void* h, void* f_out, void* pr_out, double* sumsq_out, void* stream);
+
+/* ---------------------------------------------------------------------------------------------
+ * Batched march (a parameter sweep, Section 4.6 "Operating envelope": the same method over a range
+ * of Reynolds numbers and lattice sizes).  A batch groups up to MSC_BATCH_MAX existing D2Q9
+ * contexts of one storage precision, created on one stream, with any mix of n (and each with its
+ * own msc_set_params: nu, dt, eps, K_max, n_min, replay) and advances all of them in one CUDA
+ * graph: every loop round performs one inner iteration (sweep, acceptance test, shadow correction
+ * or step end) of every instance still running, so each instance converges in its own number of
+ * inner iterations without waiting for the others.  Each instance computes exactly what
+ * msc_march computes for its context; only the grid geometry of the kernels differs (the per-site
+ * and per-line arithmetic is the same, the residual-norm summation order follows the tuned tiling).
+ * Contexts stay owned by the caller and keep their own calls: msc_set_params, msc_init_fields,
+ * msc_set_replay_counts before a batch march; msc_get_stats, msc_read_fields, msc_get_step_iters,
+ * msc_get_residual_history after it.  A context must not be destroyed while a batch holds it.
+ * ------------------------------------------------------------------------------------------- */
+#define MSC_BATCH_MAX 64
+#define MSC_BATCH_CLASSES 8 /* distinct lattice sizes in one batch */
+
+typedef struct msc_batch msc_batch;
+
+/* Kernel tiling of a batch, per distinct lattice size (class c, sizes in descending order).
+   sweep_rows: output rows per warp unit of the sweep (4..64, a power of two, <= n);
+   fft_rows: complex row transforms per block of the row passes (a power of two, <= n/2,
+   fft_rows * n / 16 <= 256); col_lines: j_x columns per block of the column solve (a power of
+   two, 3 col_lines n / 16 <= 768 threads for FP32, 384 for FP64); sweep_ctas_per_sm: resident
+   blocks of 4 warps per SM of the persistent sweep (1..16).  The *_us fields are the last
+   msc_batch_autotune timings of the chosen tiling (one launch over the whole batch, microseconds;
+   0 when not measured). */
+typedef struct {
+    int n_classes;
+    int n[MSC_BATCH_CLASSES];
+    int sweep_rows[MSC_BATCH_CLASSES];
+    int fft_rows[MSC_BATCH_CLASSES];
+    int col_lines[MSC_BATCH_CLASSES];
+    int sweep_ctas_per_sm;
+    float sweep_us, rowfft_us, colsolve_us;
+} msc_batch_tuning;
+
+/* Device workspace bytes of a batch over n_inst contexts (0 if the list is invalid: NULL, more than
+   MSC_BATCH_MAX, not D2Q9, mixed precision, more than MSC_BATCH_CLASSES distinct n). */
+size_t msc_batch_workspace_bytes(msc_ctx* const* ctxs, int n_inst);
+
+/* Create a batch over ctxs[0..n_inst) in a caller-provided device workspace (256-byte aligned,
+   >= msc_batch_workspace_bytes).  Every context must have been created with `stream`.  The initial
+   tiling is the single-context geometry of each size; msc_batch_autotune improves it. */
+int msc_batch_create(msc_batch** out, msc_ctx* const* ctxs, int n_inst, void* dev_workspace, size_t bytes,
+                     void* stream);
+void msc_batch_destroy(msc_batch* b);
+
+/* Advance instance i by n_steps[i] >= 0 physical steps (host array of n_inst counts, in the order
+   of ctxs).  Asynchronous.  Each instance stops on its own at its count or at its first
+   nonconvergent or non-finite step (its status, readable by msc_get_stats, says which; the other
+   instances carry on).  MSC_ERR_STATE if a context with a nonzero count lacks parameters or
+   fields; MSC_ERR_ARG for a negative count or a replay count list shorter than the steps. */
+int msc_batch_march(msc_batch* b, const int* n_steps);
+
+/* Explicit LBM steps for every instance (n_steps[i] >= 0 each), batched the same way; the same
+   result as msc_explicit_march on each context. */
+int msc_batch_explicit_march(msc_batch* b, const int* n_steps);
+
+/* Project-written autotuner: times the batched sweep, row transforms and column solve on the
+   instances' own arrays (stateless: no instance state changes; the next step's working arrays are
+   scratch until a march rewrites them) for every candidate tiling, one class and one kernel at a
+   time (coordinate descent, best of `reps` launches each, reps >= 1), keeps the fastest and
+   rebuilds the batch graph.  Synchronises the stream.  `out` (optional) receives the result. */
+int msc_batch_autotune(msc_batch* b, int reps, msc_batch_tuning* out);
+int msc_batch_get_tuning(msc_batch* b, msc_batch_tuning* out);
+/* Install a tiling (validated as described above; MSC_ERR_ARG otherwise, batch unchanged). */
+int msc_batch_set_tuning(msc_batch* b, const msc_batch_tuning* t);
 
 #ifdef __cplusplus
 }

@@ -48,6 +48,8 @@ class MarchParams:
     omega: Optional[tuple] = None  # None: operating point; (w+, w-): general TRT collision
     warm_order: int = 3       # accepted states used by the warm start: 3 is Section 3.1 (cubic);
                               # 1 (f^n) and 2 (2f^n - f^{n-1}) truncate it
+    count_multiple: int = 1   # accept only at inner counts that are multiples of this (1: Algorithm 1;
+                              # 2: sweeps in pairs, for reduced-precision storage)
 
 
 @dataclass
@@ -113,7 +115,7 @@ def physical_step(st: DualTimeState, prm: MarchParams, replay_count: Optional[in
         if replay_count is not None:
             accept = ell == replay_count
         else:
-            accept = ell >= prm.nmin and R < prm.eps
+            accept = ell >= prm.nmin and R < prm.eps and ell % prm.count_multiple == 0
         if accept:
             m_new = reconstruct(moments(lat, f_T), a, h)
             st.f_hist = [f_T] + st.f_hist[:2]

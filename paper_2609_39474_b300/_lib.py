@@ -28,13 +28,24 @@ class LatticeDesc(ctypes.Structure):
 class Params(ctypes.Structure):
     _fields_ = [("nu", ctypes.c_double), ("dt", ctypes.c_double), ("eps", ctypes.c_double),
                 ("kmax", ctypes.c_int), ("nmin", ctypes.c_int), ("corrector", ctypes.c_int),
-                ("replay", ctypes.c_int), ("warm_order", ctypes.c_int)]
+                ("replay", ctypes.c_int), ("warm_order", ctypes.c_int), ("count_multiple", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
     _fields_ = [("steps_done", ctypes.c_int64), ("inner_total", ctypes.c_int64),
                 ("steps_in_call", ctypes.c_int32), ("last_iters", ctypes.c_int32),
                 ("last_q", ctypes.c_int32), ("status", ctypes.c_int32), ("last_R", ctypes.c_double)]
+
+
+MSC_BATCH_MAX = 64
+MSC_BATCH_CLASSES = 8
+
+
+class BatchTuning(ctypes.Structure):
+    _fields_ = [("n_classes", ctypes.c_int), ("n", ctypes.c_int * MSC_BATCH_CLASSES),
+                ("sweep_rows", ctypes.c_int * MSC_BATCH_CLASSES), ("fft_rows", ctypes.c_int * MSC_BATCH_CLASSES),
+                ("col_lines", ctypes.c_int * MSC_BATCH_CLASSES), ("sweep_ctas_per_sm", ctypes.c_int),
+                ("sweep_us", ctypes.c_float), ("rowfft_us", ctypes.c_float), ("colsolve_us", ctypes.c_float)]
 
 
 class MscError(RuntimeError):
@@ -78,6 +89,14 @@ _SIG = {
     "msc_shadow_solve": (_i, [_i, _i, _i, _d, _d, _vp, _vp, _vp, _sz, _vp]),
     "msc_equilibrium": (_i, [_i, _i, _i, _vp, _vp, _vp, _vp]),
     "msc_sweep_d2q9_noalloc": (_i, [_i, _i, _d, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "msc_batch_workspace_bytes": (_sz, [ctypes.POINTER(_vp), _i]),
+    "msc_batch_create": (_i, [ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i, _vp, _sz, _vp]),
+    "msc_batch_destroy": (None, [_vp]),
+    "msc_batch_march": (_i, [_vp, ctypes.POINTER(_i)]),
+    "msc_batch_explicit_march": (_i, [_vp, ctypes.POINTER(_i)]),
+    "msc_batch_autotune": (_i, [_vp, _i, ctypes.POINTER(BatchTuning)]),
+    "msc_batch_get_tuning": (_i, [_vp, ctypes.POINTER(BatchTuning)]),
+    "msc_batch_set_tuning": (_i, [_vp, ctypes.POINTER(BatchTuning)]),
 }
 for _name, (_res, _args) in _SIG.items():
     _fn = getattr(lib, _name)

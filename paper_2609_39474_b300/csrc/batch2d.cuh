@@ -1,0 +1,300 @@
+// Batched D2Q9 march: many independent periodic lattices of uneven n (and their own nu, dt, eps,
+// Re) advanced by one CUDA graph.  Every instance keeps its own context (device state, population
+// ring, BDF history, spectrum, solve tables) and runs exactly the per-instance algorithm of the
+// single march (Algorithm 1, Section 3); the batch only changes how the work is scheduled.
+//
+// One round of the graph's loop performs one inner iteration of every active instance:
+//   k_bsweep2   persistent sweep: a fixed grid of warps walks the work list of (instance, strip,
+//               row block) units of all active instances; the last unit of an instance reduces its
+//               residual norm in a fixed order and takes the acceptance decision (Algorithm 1)
+//   k_browfft   forward / inverse row transforms and k_bcolsolve the column FFT + FP64 solve, for
+//               the instances whose sweep asked for a shadow correction; a block finds its
+//               instance in a prefix table
+//   k_bstep_end acceptance (m^{n+1}) and the next step's h and warm start, accepted instances only
+//   k_bfinish   history rotation per instance and the loop condition (any instance still active)
+// Instances therefore drift apart in phase (each converges in its own number of inner
+// iterations) without waiting for one another; an instance leaves the work list when its steps
+// are done or it stops with an error.
+#pragma once
+
+#include "common.cuh"
+#include "march.cuh"
+#include "spectral2d.cuh"
+#include "sweep2d.cuh"
+
+namespace msc {
+
+constexpr int kBatchMax = 64;
+
+// per-instance arguments, in device memory
+template <typename T>
+struct BInst {
+    Sweep2Args<T> sw;       // graph-mode sweep arguments (hist, replay counts, pointers, geometry)
+    Spec2Args<T> sp;        // graph-mode spectral arguments with this instance's P and G
+    DevState* st;
+    T* fbase;
+    size_t fstride;         // elements
+    double* mbuf;
+    T* h;
+    size_t sites;
+    int* iters;
+    int max_steps;
+    int units;              // sweep warp units (nstrips x nrowblk)
+    double* upart;          // per-unit partial sums of r^2 (batch workspace)
+    unsigned int* ucount;   // finished units of the current sweep (batch workspace)
+    // tuning mode: stateless sweep from t_fin into t_fout, norm into t_sumsq
+    const T* t_fin;
+    T* t_fout;
+    double* t_sumsq;
+};
+
+// work-list prefix tables: instance i owns units [unit_off[i], unit_off[i+1]) and so on
+struct BMap {
+    int n_inst;
+    int unit_off[kBatchMax + 1];
+    int row_off[kBatchMax + 1];
+    int col_off[kBatchMax + 1];
+    int fld_off[kBatchMax + 1];
+    int col_g[kBatchMax];       // columns per block of the column solve
+    DevState* st[kBatchMax];
+    int* iters[kBatchMax];
+    int max_steps[kBatchMax];
+};
+
+// per-call step counts (kernel parameter)
+struct BSteps {
+    int n[kBatchMax];
+};
+
+// largest i with off[i] <= x, for off[0] = 0 <= x < off[n_inst]
+__device__ __forceinline__ int find_inst(const int* __restrict__ off, int n_inst, int x) {
+    int lo = 0, hi = n_inst;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(off + mid) <= x) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ bool inst_active(const volatile DevState* vs) {
+    return vs->params_ok && vs->status == MSC_OK && vs->steps_target > 0;
+}
+
+// MODE 0: march (state from the device), 1: tuning (stateless, every instance), 2: explicit LBM
+// step `ex_node` of the unrolled explicit loop body.
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kSweepWarps * 32) k_bsweep2(const BInst<T>* __restrict__ I,
+                                                             const BMap* __restrict__ M, int ex_node) {
+    const int lane = threadIdx.x & 31;
+    const int nw = gridDim.x * kSweepWarps;
+    const int n_inst = M->n_inst;
+    const int total = __ldg(M->unit_off + n_inst);
+    for (int u = blockIdx.x * kSweepWarps + (threadIdx.x >> 5); u < total; u += nw) {  // warp-uniform
+        const int i = find_inst(M->unit_off, n_inst, u);
+        const BInst<T>& B = I[i];
+        const int lu = u - __ldg(M->unit_off + i);
+        const Sweep2Args<T>& A = B.sw;
+        const T* fin;
+        T* fout;
+        T a, inv;
+        int lift;
+        if (MODE == 0) {
+            const volatile DevState* vs = B.st;
+            if (!inst_active(vs)) continue;
+            fin = B.fbase + (size_t)vs->slot_cur * B.fstride;
+            fout = B.fbase + (size_t)vs->slot_nxt * B.fstride;
+            const double ad = vs->a;
+            a = (T)ad;
+            inv = (T)(1.0 / (1.0 + ad / 2.0));
+            lift = vs->lift;
+        } else if (MODE == 1) {
+            fin = B.t_fin;
+            fout = B.t_fout;
+            a = (T)A.a;
+            inv = (T)(1.0 / (1.0 + A.a / 2.0));
+            lift = 1;
+        } else {
+            const volatile DevState* vs = B.st;
+            if (vs->ex_loops_left <= ex_node) continue;
+            const int sa = vs->ex_a, sb = vs->ex_b;
+            fin = B.fbase + (size_t)((ex_node & 1) ? sb : sa) * B.fstride;
+            fout = B.fbase + (size_t)((ex_node & 1) ? sa : sb) * B.fstride;
+            a = T(0);
+            inv = T(1);
+            lift = 0;
+        }
+        double ssq = sweep2_unit<T, MODE == 2>(fin, A.dm, A.h, fout, A.pr, a, inv, lift, A.n, A.hb,
+                                               lu % A.nstrips, lu / A.nstrips, lane);
+        if (MODE == 2) continue;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) ssq += __shfl_xor_sync(0xffffffffu, ssq, off);
+        unsigned int last = 0;
+        if (lane == 0) {
+            B.upart[lu] = ssq;
+            __threadfence();
+            last = atomicAdd(B.ucount, 1u) == (unsigned int)(B.units - 1);
+        }
+        last = __shfl_sync(0xffffffffu, last, 0);
+        if (!last) continue;
+        // the last unit of instance i: every partial of the sweep is visible, sum in a fixed order
+        __threadfence();
+        double s = 0.0;
+        for (int k = lane; k < B.units; k += 32) s += __ldcg(B.upart + k);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+        if (lane == 0) {
+            *B.ucount = 0u;
+            if (MODE == 0)
+                march_after_sweep(B.st, s, 9.0 * (double)B.sites, A.hist, A.hist_cap, A.replay_counts, A.max_steps,
+                                  0, 0, 0);
+            else
+                *B.t_sumsq = s;
+        }
+    }
+}
+
+// spectral passes; MODE 0 runs for instances whose last sweep asked for a correction, MODE 1 (tuning)
+// for every instance with the solve coefficients evaluated in place
+template <typename T, int MODE>
+__device__ __forceinline__ bool spec_inst(const BInst<T>& B, Spec2Args<T>* A) {
+    *A = B.sp;
+    if (MODE == 1) {
+        A->st = nullptr;
+        A->coef = nullptr;
+        return true;
+    }
+    const volatile DevState* vs = B.st;
+    return inst_active(vs) && vs->lift;
+}
+
+template <typename T, bool INV, int MODE>
+__global__ void __launch_bounds__(kFftThreads) k_browfft(const BInst<T>* __restrict__ I, const BMap* __restrict__ M) {
+    const int i = find_inst(M->row_off, M->n_inst, blockIdx.x);
+    Spec2Args<T> A;
+    if (!spec_inst<T, MODE>(I[i], &A)) return;
+    const int bid = blockIdx.x - __ldg(M->row_off + i);
+    if (INV) rowfft_inv_block<T>(A, bid);
+    else rowfft_fwd_block<T>(A, bid);
+}
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(sizeof(T) == 8 ? 384 : 768) k_bcolsolve(const BInst<T>* __restrict__ I,
+                                                                          const BMap* __restrict__ M) {
+    const int i = find_inst(M->col_off, M->n_inst, blockIdx.x);
+    Spec2Args<T> A;
+    if (!spec_inst<T, MODE>(I[i], &A)) return;
+    colsolve_block<T>(A, blockIdx.x - __ldg(M->col_off + i), __ldg(M->col_g + i));
+}
+
+// field kernels: instance i owns blocks [fld_off[i], fld_off[i+1]) of a grid-stride loop
+template <typename T>
+__device__ __forceinline__ void fld_range(const BMap* __restrict__ M, int* inst, size_t* i0, size_t* istride) {
+    const int i = find_inst(M->fld_off, M->n_inst, blockIdx.x);
+    const int b0 = __ldg(M->fld_off + i), nb = __ldg(M->fld_off + i + 1) - b0;
+    *inst = i;
+    *i0 = (size_t)(blockIdx.x - b0) * blockDim.x + threadIdx.x;
+    *istride = (size_t)nb * blockDim.x;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kFieldThreads) k_bstep_begin(const BInst<T>* __restrict__ I,
+                                                               const BMap* __restrict__ M) {
+    int i;
+    size_t i0, is;
+    fld_range<T>(M, &i, &i0, &is);
+    const BInst<T>& B = I[i];
+    if (!inst_active(B.st)) return;
+    step_begin_range<D2Q9, T>(B.st, B.fbase, B.fstride, B.mbuf, B.h, B.sites, i0, is);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kFieldThreads) k_bstep_end(const BInst<T>* __restrict__ I,
+                                                             const BMap* __restrict__ M) {
+    int i;
+    size_t i0, is;
+    fld_range<T>(M, &i, &i0, &is);
+    const BInst<T>& B = I[i];
+    step_end_range<D2Q9, T>(B.st, B.fbase, B.fstride, B.mbuf, B.h, B.sites, i0, is);  // accepted only
+}
+
+// m^n = P f^n after a batched explicit march, for the instances that took steps
+template <typename T>
+__global__ void __launch_bounds__(kFieldThreads) k_bmoments_state(const BInst<T>* __restrict__ I,
+                                                                  const BMap* __restrict__ M, BSteps steps) {
+    int i;
+    size_t i0, is;
+    fld_range<T>(M, &i, &i0, &is);
+    if (steps.n[i] <= 0) return;
+    const BInst<T>& B = I[i];
+    moments_state_range<D2Q9, T>(B.st, B.fbase, B.fstride, B.mbuf, B.sites, i0, is);
+}
+
+// ---- control kernels: one thread per instance, one block ---------------------------------------
+
+__global__ void k_btargets(const BMap* __restrict__ M, BSteps steps) {
+    const int i = threadIdx.x;
+    if (i < M->n_inst) set_target(M->st[i], steps.n[i]);
+}
+
+// first step of every instance that runs, and the loop condition
+__global__ void k_bsetup(const BMap* __restrict__ M, cudaGraphConditionalHandle h_round) {
+    const int i = threadIdx.x;
+    bool go = false;
+    if (i < M->n_inst) {
+        DevState* st = M->st[i];
+        if (arm_state(st)) {
+            step_setup(st);
+            go = true;
+        }
+    }
+    go = __syncthreads_or(go);
+    if (threadIdx.x == 0) cudaGraphSetConditional(h_round, go ? 1u : 0u);
+}
+
+__global__ void k_bfinish(const BMap* __restrict__ M, cudaGraphConditionalHandle h_round) {
+    const int i = threadIdx.x;
+    bool active = false;
+    if (i < M->n_inst) {
+        DevState* st = M->st[i];
+        if (st->accepted) {
+            step_finish(st, M->iters[i], M->max_steps[i]);
+            st->accepted = 0;  // k_bstep_end of the next round must not see this step again
+        }
+        active = st->params_ok && st->status == MSC_OK && st->steps_target > 0;
+    }
+    active = __syncthreads_or(active);
+    if (threadIdx.x == 0) cudaGraphSetConditional(h_round, active ? 1u : 0u);
+}
+
+// explicit march: ping-pong from the accepted slot, `left` = steps still to take
+__global__ void k_bex_setup(const BMap* __restrict__ M, BSteps steps) {
+    const int i = threadIdx.x;
+    if (i < M->n_inst) {
+        DevState* st = M->st[i];
+        const int n = steps.n[i];
+        st->ex_a = st->slot_fn[0];
+        st->ex_b = (st->slot_fn[0] + 1) % kNumFBuf;
+        st->ex_loops_left = n > 0 ? n : 0;
+    }
+}
+
+// subtract the steps of one loop round and set the loop condition (unroll = 0: condition only)
+__global__ void k_bex_count(const BMap* __restrict__ M, int unroll, cudaGraphConditionalHandle h_ex) {
+    const int i = threadIdx.x;
+    bool go = false;
+    if (i < M->n_inst) {
+        DevState* st = M->st[i];
+        const int left = st->ex_loops_left - unroll;
+        st->ex_loops_left = left > 0 ? left : 0;
+        go = left > 0;
+    }
+    go = __syncthreads_or(go);
+    if (threadIdx.x == 0) cudaGraphSetConditional(h_ex, go ? 1u : 0u);
+}
+
+__global__ void k_bex_finish(const BMap* __restrict__ M, BSteps steps) {
+    const int i = threadIdx.x;
+    if (i < M->n_inst && steps.n[i] > 0) ex_finish(M->st[i], steps.n[i] & 1);
+}
+
+}  // namespace msc

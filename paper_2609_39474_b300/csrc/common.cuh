@@ -54,6 +54,7 @@ struct DevState {
     double nu, dt, eps;
     int kmax, nmin, corrector, replay;
     int warm_order;         // accepted states used by the warm start (1..3)
+    int count_multiple;     // accepted inner counts are multiples of this (1 or 2)
     int params_ok;
     // physical-step bookkeeping
     int64_t steps_done;     // accepted steps since init

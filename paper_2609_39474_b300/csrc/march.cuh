@@ -73,8 +73,9 @@ __global__ void k_moments(const T* __restrict__ f, double* __restrict__ m, doubl
 // Start of a physical step: h_q from the accepted moment histories (Eq. bdf2) and the trial
 // populations from the population-history extrapolation (Section 3.1) into the working slot.
 template <class L, typename T>
-__global__ void k_step_begin(const DevState* __restrict__ st, T* __restrict__ fbase, size_t fstride,
-                             const double* __restrict__ mbuf, T* __restrict__ h, size_t sites) {
+__device__ __forceinline__ void step_begin_range(const DevState* __restrict__ st, T* __restrict__ fbase,
+                                                 size_t fstride, const double* __restrict__ mbuf,
+                                                 T* __restrict__ h, size_t sites, size_t i0, size_t istride) {
     const volatile DevState* vs = st;
     if (vs->prepared) return;  // formed by the previous step's k_step_end
     const int q = vs->q;
@@ -89,8 +90,7 @@ __global__ void k_step_begin(const DevState* __restrict__ st, T* __restrict__ fb
     T* ft = fbase + (size_t)vs->slot_cur * fstride;
     const double c1 = q == 1 ? 1.0 / dt : 4.0 / (2.0 * dt);
     const double c2 = q == 1 ? 0.0 : 1.0 / (2.0 * dt);
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < sites;
-         i += (size_t)gridDim.x * blockDim.x) {
+    for (size_t i = i0; i < sites; i += istride) {
 #pragma unroll
         for (int c = 0; c <= L::D; ++c) {
             const size_t o = c * sites + i;
@@ -115,6 +115,13 @@ __global__ void k_step_begin(const DevState* __restrict__ st, T* __restrict__ fb
     }
 }
 
+template <class L, typename T>
+__global__ void k_step_begin(const DevState* __restrict__ st, T* __restrict__ fbase, size_t fstride,
+                             const double* __restrict__ mbuf, T* __restrict__ h, size_t sites) {
+    step_begin_range<L, T>(st, fbase, fstride, mbuf, h, sites, blockIdx.x * (size_t)blockDim.x + threadIdx.x,
+                           (size_t)gridDim.x * blockDim.x);
+}
+
 // Acceptance: m^{n+1} = R_{q,h}(f^{n+1}) with the unrotated histories (Eq. macro-reconstruct),
 // evaluated in FP64 (P f accumulated in the storage type) and written into the m^{n-1} slot
 // (rotated by k_step_finish).  When another step of this march follows, the same pass also forms
@@ -122,9 +129,9 @@ __global__ void k_step_begin(const DevState* __restrict__ st, T* __restrict__ fb
 // (2 f^{n+1} - f^n, or 3 f^{n+1} - 3 f^n + f^{n-1}; Section 3.1) into the free working slot, so
 // that the next k_step_begin has nothing to do.
 template <class L, typename T>
-__global__ void __launch_bounds__(kFieldThreads) k_step_end(const DevState* __restrict__ st, T* __restrict__ fbase,
-                                                            size_t fstride, double* __restrict__ mbuf, T* __restrict__ h,
-                                                            size_t sites) {
+__device__ __forceinline__ void step_end_range(const DevState* __restrict__ st, T* __restrict__ fbase,
+                                               size_t fstride, double* __restrict__ mbuf, T* __restrict__ h,
+                                               size_t sites, size_t i0, size_t istride) {
     const volatile DevState* vs = st;
     if (!vs->accepted) return;
     const int q = vs->q;
@@ -146,8 +153,7 @@ __global__ void __launch_bounds__(kFieldThreads) k_step_end(const DevState* __re
     const double n1 = 4.0 / (2.0 * dt), n2 = 1.0 / (2.0 * dt);  // BDF2 for the next step
     const double k1 = 0.5 * c1 * inv, k2 = 0.5 * c2 * inv;
 #pragma unroll 2
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < sites;
-         i += (size_t)gridDim.x * blockDim.x) {
+    for (size_t i = i0; i < sites; i += istride) {
         T fv[L::Q];
         T mom[4] = {T(0), T(0), T(0), T(0)};
 #pragma unroll
@@ -184,6 +190,14 @@ __global__ void __launch_bounds__(kFieldThreads) k_step_end(const DevState* __re
             }
         }
     }
+}
+
+template <class L, typename T>
+__global__ void __launch_bounds__(kFieldThreads) k_step_end(const DevState* __restrict__ st, T* __restrict__ fbase,
+                                                            size_t fstride, double* __restrict__ mbuf, T* __restrict__ h,
+                                                            size_t sites) {
+    step_end_range<L, T>(st, fbase, fstride, mbuf, h, sites, blockIdx.x * (size_t)blockDim.x + threadIdx.x,
+                         (size_t)gridDim.x * blockDim.x);
 }
 
 // FP64 coefficients of the closed-form Schur solve (Eq. schur) at every masked wavevector, for
@@ -236,6 +250,7 @@ __global__ void k_set_params(DevState* st, msc_params p) {
     st->corrector = p.corrector;
     st->replay = p.replay;
     st->warm_order = p.warm_order;
+    st->count_multiple = p.count_multiple;
     st->params_ok = 1;
 }
 
@@ -259,7 +274,7 @@ __global__ void k_reset_history(DevState* st) {
     st->prepared = 0;
 }
 
-__global__ void k_set_target(DevState* st, int n_steps) {
+__device__ inline void set_target(DevState* st, int n_steps) {
     st->prepared = 0;
     st->steps_target = n_steps;
     st->steps_in_call = 0;
@@ -268,10 +283,19 @@ __global__ void k_set_target(DevState* st, int n_steps) {
     st->status = MSC_OK;
 }
 
+__global__ void k_set_target(DevState* st, int n_steps) { set_target(st, n_steps); }
+
+// a march may run: parameters set (else MSC_ERR_STATE), steps left and no error recorded
+__device__ inline bool arm_state(DevState* st) {
+    if (!st->params_ok) {
+        if (st->steps_target > 0) st->status = MSC_ERR_STATE;
+        return false;
+    }
+    return st->steps_target > 0 && st->status == MSC_OK;
+}
+
 __global__ void k_arm(DevState* st, cudaGraphConditionalHandle h_step) {
-    const bool go = st->steps_target > 0 && st->params_ok && st->status == MSC_OK;
-    if (!st->params_ok) st->status = MSC_ERR_STATE;
-    cudaGraphSetConditional(h_step, go ? 1u : 0u);
+    cudaGraphSetConditional(h_step, arm_state(st) ? 1u : 0u);
 }
 
 __device__ inline bool slot_in_history(const DevState* st, int s) {
@@ -280,11 +304,9 @@ __device__ inline bool slot_in_history(const DevState* st, int s) {
     return false;
 }
 
-__global__ void k_step_setup(DevState* st, cudaGraphConditionalHandle h_iter, int cond) {
-    if (st->prepared) {  // k_step_finish already set up this step
-        if (cond) cudaGraphSetConditional(h_iter, 1u);
-        return;
-    }
+// start of a physical step (BDF order, a_q, working slots) unless k_step_finish already did it
+__device__ inline void step_setup(DevState* st) {
+    if (st->prepared) return;
     st->q = st->steps_done == 0 ? 1 : 2;
     st->a = st->q == 1 ? 1.0 / st->dt : 3.0 / (2.0 * st->dt);
     st->iter = 0;
@@ -296,11 +318,17 @@ __global__ void k_step_setup(DevState* st, cudaGraphConditionalHandle h_iter, in
         if (picked == 0) st->slot_cur = s; else st->slot_nxt = s;
         ++picked;
     }
+}
+
+__global__ void k_step_setup(DevState* st, cudaGraphConditionalHandle h_iter, int cond) {
+    step_setup(st);
     if (cond) cudaGraphSetConditional(h_iter, 1u);
 }
 
-__global__ void k_step_finish(DevState* st, int* iters_out, int max_steps,
-                              cudaGraphConditionalHandle h_step, int cond) {
+// End of an accepted step: rotate the population and moment histories, count the step and, when
+// another step of this call follows, set that step up (its h and trial were formed by k_step_end).
+// Returns whether another step follows.
+__device__ inline unsigned int step_finish(DevState* st, int* iters_out, int max_steps) {
     unsigned int go = 0u;
     if (st->accepted && st->status == MSC_OK) {
         const int k = st->steps_in_call;
@@ -337,20 +365,26 @@ __global__ void k_step_finish(DevState* st, int* iters_out, int max_steps,
     } else {
         st->prepared = 0;
     }
+    return go;
+}
+
+__global__ void k_step_finish(DevState* st, int* iters_out, int max_steps,
+                              cudaGraphConditionalHandle h_step, int cond) {
+    const unsigned int go = step_finish(st, iters_out, max_steps);
     if (cond) cudaGraphSetConditional(h_step, go);
 }
 
 // m^n = P f^n of the accepted slot into both moment slots (after an explicit march)
 template <class L, typename T>
-__global__ void k_moments_state(const DevState* __restrict__ st, const T* __restrict__ fbase, size_t fstride,
-                                double* __restrict__ mbuf, size_t sites) {
+__device__ __forceinline__ void moments_state_range(const DevState* __restrict__ st, const T* __restrict__ fbase,
+                                                    size_t fstride, double* __restrict__ mbuf, size_t sites,
+                                                    size_t i0, size_t istride) {
     const volatile DevState* vs = st;
     const T* f = fbase + (size_t)vs->slot_fn[0] * fstride;
     const size_t mstride = (size_t)(L::D + 1) * sites;
     double* m0 = mbuf + (size_t)vs->m_cur * mstride;
     double* m1 = mbuf + (size_t)vs->m_prev * mstride;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < sites;
-         i += (size_t)gridDim.x * blockDim.x) {
+    for (size_t i = i0; i < sites; i += istride) {
         double mom[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
         for (int k = 0; k < L::Q; ++k) {
@@ -368,6 +402,13 @@ __global__ void k_moments_state(const DevState* __restrict__ st, const T* __rest
     }
 }
 
+template <class L, typename T>
+__global__ void k_moments_state(const DevState* __restrict__ st, const T* __restrict__ fbase, size_t fstride,
+                                double* __restrict__ mbuf, size_t sites) {
+    moments_state_range<L, T>(st, fbase, fstride, mbuf, sites, blockIdx.x * (size_t)blockDim.x + threadIdx.x,
+                              (size_t)gridDim.x * blockDim.x);
+}
+
 // explicit march bookkeeping: ping-pong between the accepted slot and one free slot; the
 // counter holds the remaining iterations of the graph's unrolled loop body
 __global__ void k_ex_setup(DevState* st, int loop_iters) {
@@ -380,7 +421,7 @@ __global__ void k_ex_arm(DevState* st, cudaGraphConditionalHandle h_ex) {
     cudaGraphSetConditional(h_ex, st->ex_loops_left > 0 ? 1u : 0u);
 }
 
-__global__ void k_ex_finish(DevState* st, int odd) {
+__device__ inline void ex_finish(DevState* st, int odd) {
     st->slot_fn[0] = odd ? st->ex_b : st->ex_a;
     int s1 = (st->slot_fn[0] + 1) % kNumFBuf;
     int s2 = (st->slot_fn[0] + 2) % kNumFBuf;
@@ -392,5 +433,7 @@ __global__ void k_ex_finish(DevState* st, int odd) {
     st->m_prev = 1;
     st->prepared = 0;
 }
+
+__global__ void k_ex_finish(DevState* st, int odd) { ex_finish(st, odd); }
 
 }  // namespace msc

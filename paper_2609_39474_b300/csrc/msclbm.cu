@@ -571,7 +571,7 @@ int msc_set_params(msc_ctx* c, const msc_params* p) {
     if (!c || !p) return MSC_ERR_ARG;
     if (!(p->dt > 0.0) || !(p->eps >= 0.0) || !(p->nu > 0.0) || p->kmax < 1 || p->nmin < 1 ||
         (p->corrector != 0 && p->corrector != 1) || (p->replay != 0 && p->replay != 1) || p->warm_order < 0 ||
-        p->warm_order > 3)
+        p->warm_order > 3 || p->count_multiple < 0 || p->count_multiple > 2)
         return MSC_ERR_ARG;
     // the shadow solve bakes nu into the graph: rebuild if it changes
     if (c->params_set && p->nu != c->params.nu && c->x_march) {
@@ -584,6 +584,8 @@ int msc_set_params(msc_ctx* c, const msc_params* p) {
     c->params = *p;
     if (c->params.warm_order == 0)  // FP32 storage: the cubic rule grows rounding in weakly damped modes
         c->params.warm_order = c->desc.precision == MSC_FP64 ? 3 : (c->desc.dim == 2 ? 2 : 1);
+    if (c->params.count_multiple == 0)  // FP32 D2Q9: keep the staggered modes' per-step factor positive
+        c->params.count_multiple = c->desc.precision == MSC_FP32 && c->desc.dim == 2 ? 2 : 1;
     c->params_set = true;
     k_set_params<<<1, 1, 0, c->stream>>>(at<DevState>(c, c->lay.state), c->params);
     CK(cudaGetLastError());
@@ -978,3 +980,4 @@ int msc_equilibrium(int dim, int n, int precision, const double* p, const double
 }  // extern "C"
 
 #include "sweep_noalloc.cuh"
+#include "batch_api.cuh"

@@ -72,14 +72,14 @@ inline size_t spec_row_smem(int n, int P) {
 
 // 2P consecutive rows (c, y0 .. y0 + 2P - 1) form P complex rows
 template <typename T>
-__global__ void __launch_bounds__(kFftThreads) k_rowfft_fwd(Spec2Args<T> A) {
+__device__ __forceinline__ void rowfft_fwd_block(const Spec2Args<T>& A, int bid) {
     using C = typename Cplx<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* s = reinterpret_cast<C*>(smem_raw);
     const int n = A.n, logn = A.logn, P = A.P, plen = padded_len(n);
     const int nx4 = n / 4 + 1;
     const int hr = A.rows / 2;
-    const int pair0 = blockIdx.x * P;  // P divides hr: all pairs of the block lie in one field
+    const int pair0 = bid * P;  // P divides hr: all pairs of the block lie in one field
     const int c = pair0 / hr;
     const int y0 = 2 * (pair0 - c * hr);
     const T* rows = A.pr + ((size_t)c * A.rows + y0) * n;
@@ -117,14 +117,19 @@ __global__ void __launch_bounds__(kFftThreads) k_rowfft_fwd(Spec2Args<T> A) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kFftThreads) k_rowfft_inv(Spec2Args<T> A) {
+__global__ void __launch_bounds__(kFftThreads) k_rowfft_fwd(Spec2Args<T> A) {
+    rowfft_fwd_block<T>(A, blockIdx.x);
+}
+
+template <typename T>
+__device__ __forceinline__ void rowfft_inv_block(const Spec2Args<T>& A, int bid) {
     using C = typename Cplx<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* s = reinterpret_cast<C*>(smem_raw);
     const int n = A.n, logn = A.logn, P = A.P, plen = padded_len(n);
     const int nx4 = n / 4 + 1;
     const int hr = A.rows / 2;
-    const int pair0 = blockIdx.x * P;
+    const int pair0 = bid * P;
     const int c = pair0 / hr;
     const int y0 = 2 * (pair0 - c * hr);
     const C* in = A.spec + (size_t)c * nx4 * A.rows + y0;
@@ -160,6 +165,11 @@ __global__ void __launch_bounds__(kFftThreads) k_rowfft_inv(Spec2Args<T> A) {
     }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(kFftThreads) k_rowfft_inv(Spec2Args<T> A) {
+    rowfft_inv_block<T>(A, blockIdx.x);
+}
+
 // Schur solve at one masked wavevector in FP64: dp = A rp - i B (k.rm), du = Dv rm - i Cc k dp
 template <typename C, int D>
 __device__ __forceinline__ void schur_apply(C* v[D + 1], const double* kv, const double* cf) {
@@ -182,39 +192,49 @@ __device__ __forceinline__ void schur_apply(C* v[D + 1], const double* kv, const
     }
 }
 
-// 2D: one block per kept j_x column, all three fields
+// 2D: G consecutive kept j_x columns per block (G a power of two; the last block of a lattice may
+// hold fewer), all three fields of each.  Line (c, g) of the block sits at (c G + g) plen in shared memory.
 template <typename T>
-__global__ void __launch_bounds__(sizeof(T) == 8 ? 384 : 768) k_colsolve(Spec2Args<T> A) {
+__device__ __forceinline__ void colsolve_block(const Spec2Args<T>& A, int bid, int G) {
     using C = typename Cplx<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* s = reinterpret_cast<C*>(smem_raw);
     const int n = A.n, logn = A.logn, plen = padded_len(n);
     const int nx4 = n / 4 + 1;
-    const int jx = blockIdx.x;
-    C* col = A.spec + (size_t)jx * n;  // spec[c][jx][y] at col + c * nx4 * n + y
+    const int jx0 = bid * G;
+    const int ng = min(G, nx4 - jx0);
+    const int lgn = logn + __ffs(G) - 1;  // G is a power of two
+    const int gn = 1 << lgn;
+    C* col = A.spec + (size_t)jx0 * n;  // spec[c][jx0 + g][y] at col + c * nx4 * n + g * n + y
     const size_t fs = (size_t)nx4 * n;
 #pragma unroll 4
-    for (int t = threadIdx.x; t < 3 * n; t += blockDim.x) {
-        const int c = t >> logn;
-        const int y = t & (n - 1);
-        s[c * plen + pad(y)] = col[c * fs + y];
+    for (int t = threadIdx.x; t < 3 * gn; t += blockDim.x) {
+        const int c = t >> lgn;
+        const int gy = t & (gn - 1);  // g * n + y
+        C v;
+        v.x = T(0); v.y = T(0);
+        if ((gy >> logn) < ng) v = col[c * fs + gy];
+        s[(c * G + (gy >> logn)) * plen + pad(gy & (n - 1))] = v;
     }
     __syncthreads();
-    fft_stockham<C, false>(s, n, logn, 3, A.tw);
+    fft_stockham<C, false>(s, n, logn, 3 * G, A.tw);
     const double a = A.st ? ((const volatile DevState*)A.st)->a : A.a;
     const double* tab = solve_table(A.coef, A.st, 2, n);
     const double two_pi_n = 6.283185307179586476925286766559 / (double)n;
     const double scale = 1.0 / ((double)n * (double)n);
-    double kv[2];
-    kv[0] = two_pi_n * (double)jx;
-    for (int jy = threadIdx.x; jy < n; jy += blockDim.x) {
+    for (int t = threadIdx.x; t < gn; t += blockDim.x) {
+        const int g = t >> logn;
+        const int jy = t & (n - 1);
+        const int jx = jx0 + g;
         const int jys = jy <= n / 2 ? jy : jy - n;
-        C* v[3] = {s + pad(jy), s + plen + pad(jy), s + 2 * plen + pad(jy)};
-        if (jys > n / 4 || jys < -(n / 4)) {
+        C* v[3] = {s + g * plen + pad(jy), s + (G + g) * plen + pad(jy), s + (2 * G + g) * plen + pad(jy)};
+        if (jys > n / 4 || jys < -(n / 4) || g >= ng) {
             C z; z.x = T(0); z.y = T(0);
             *v[0] = z; *v[1] = z; *v[2] = z;
             continue;
         }
+        double kv[2];
+        kv[0] = two_pi_n * (double)jx;
         kv[1] = two_pi_n * (double)jys;
         double cf[4];
         if (tab) {
@@ -226,12 +246,17 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 384 : 768) k_colsolve(Spec2Ar
         schur_apply<C, 2>(v, kv, cf);
     }
     __syncthreads();
-    fft_stockham<C, true>(s, n, logn, 3, A.tw);
-    for (int t = threadIdx.x; t < 3 * n; t += blockDim.x) {
-        const int c = t >> logn;
-        const int y = t & (n - 1);
-        col[c * fs + y] = s[c * plen + pad(y)];
+    fft_stockham<C, true>(s, n, logn, 3 * G, A.tw);
+    for (int t = threadIdx.x; t < 3 * gn; t += blockDim.x) {
+        const int c = t >> lgn;
+        const int gy = t & (gn - 1);
+        if ((gy >> logn) < ng) col[c * fs + gy] = s[(c * G + (gy >> logn)) * plen + pad(gy & (n - 1))];
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(sizeof(T) == 8 ? 384 : 768) k_colsolve(Spec2Args<T> A) {
+    colsolve_block<T>(A, blockIdx.x, 1);
 }
 
 inline int spec2_col_threads(int n) {

@@ -73,7 +73,7 @@ __device__ inline void march_after_sweep(DevState* st, double total, double qsit
         const int idx = st->steps_in_call;
         accept = idx < max_steps && ell == replay_counts[idx];
     } else {
-        accept = ell >= st->nmin && R < st->eps;  // a NaN never passes
+        accept = ell >= st->nmin && R < st->eps && ell % st->count_multiple == 0;  // a NaN never passes
     }
     if (!isfinite(R)) {
         st->status = MSC_ERR_NONFINITE;
@@ -92,13 +92,124 @@ __device__ inline void march_after_sweep(DevState* st, double total, double qsit
     }
 }
 
+// One warp unit of the sweep: output columns [strip*30, strip*30 + 30) of rows [rb*hb, rb*hb + hb).
+// Returns this lane's share of sum r^2 (zero in EXPLICIT mode).  Called by all 32 lanes.
+template <typename T, bool EXPLICIT>
+__device__ __forceinline__ double sweep2_unit(const T* fin, const T* dm, const T* hh, T* fout, T* pr, T a, T inv,
+                                              int lift, int n, int hb, int strip, int rb, int lane) {
+    using L = D2Q9;
+    const int nmask = n - 1;
+    const size_t NN = (size_t)n * n;
+    double ssq = 0.0;
+    const int x0 = strip * kStripOut;
+    const int y0 = rb * hb;
+    const int x = (x0 - 1 + lane) & nmask;
+    const bool out_lane = lane >= 1 && lane <= kStripOut && (x0 + lane - 1) < n;
+
+    T Ar[9], Br[9], ftp[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) { Ar[k] = T(0); Br[k] = T(0); ftp[k] = T(0); }
+    T ssq_f = T(0);
+
+    // software pipeline: the loads of row j+1 are issued before row j is collided
+    T nf[9], ndp = T(0), ndx = T(0), ndy = T(0), nh0 = T(0), nh1 = T(0), nh2 = T(0);
+    auto load_row = [&](int jr) {
+        const size_t id = (size_t)(jr & nmask) * n + x;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) nf[k] = fin[k * NN + id];
+        if (!EXPLICIT) {
+            if (lift) { ndp = dm[id]; ndx = dm[NN + id]; ndy = dm[2 * NN + id]; }
+            nh0 = hh[id]; nh1 = hh[NN + id]; nh2 = hh[2 * NN + id];
+        }
+    };
+    load_row(y0 - 1);
+    for (int j = y0 - 1; j <= y0 + hb; ++j) {
+        T f[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) f[k] = nf[k];
+        const T dp = ndp, dux = ndx, duy = ndy, h0 = nh0, h1 = nh1, h2 = nh2;
+        if (j < y0 + hb) load_row(j + 1);
+        if (!EXPLICIT && lift) {  // trial f = f_T,prev + E dm   (Eq. lift)
+#pragma unroll
+            for (int k = 0; k < 9; ++k)
+                f[k] += (T)L::w(k) * (dp + T(3) * (T(L::cx(k)) * dux + T(L::cy(k)) * duy));
+        }
+        // moments (Eq. moments)
+        T rho = T(0), jx = T(0), jy = T(0);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            rho += f[k];
+            if (L::cx(k)) jx += T(L::cx(k)) * f[k];
+            if (L::cy(k)) jy += T(L::cy(k)) * f[k];
+        }
+        T p, ux, uy, s0 = T(0), sx = T(0), sy = T(0);
+        if (EXPLICIT) {
+            p = rho; ux = jx; uy = jy;
+        } else {  // half-source reconstruction and source moments (Eqs. macro-reconstruct, source-moments)
+            p = (rho + h0 * T(0.5)) * inv;
+            ux = (jx + h1 * T(0.5)) * inv;
+            uy = (jy + h2 * T(0.5)) * inv;
+            s0 = h0 - a * p;
+            sx = h1 - a * ux;
+            sy = h2 - a * uy;
+        }
+        // operating-point collision C = f_eq + Phi/2 (Eq. collision-operating)
+        const T A0 = p + T(0.5) * s0 - T(1.5) * (ux * ux + uy * uy) - T(1.5) * (ux * sx + uy * sy);
+        T C[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const T cu = T(L::cx(k)) * ux + T(L::cy(k)) * uy;
+            const T cs = T(L::cx(k)) * sx + T(L::cy(k)) * sy;
+            C[k] = (T)L::w(k) * (A0 + T(3) * cu + T(1.5) * cs + T(4.5) * cu * (cu + cs));
+        }
+        // push streaming in x: value for column x comes from column x - c_kx
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            if (L::cx(k) == 1) C[k] = __shfl_up_sync(0xffffffffu, C[k], 1);
+            else if (L::cx(k) == -1) C[k] = __shfl_down_sync(0xffffffffu, C[k], 1);
+        }
+        // row j-1 receives the c_y = -1 directions and is complete
+#pragma unroll
+        for (int k = 0; k < 9; ++k)
+            if (L::cy(k) == -1) Ar[k] = C[k];
+        if (j - 1 >= y0 && out_lane) {
+            const size_t oidx = (size_t)((j - 1) & nmask) * n + x;
+#pragma unroll
+            for (int k = 0; k < 9; ++k) fout[k * NN + oidx] = Ar[k];
+            if (!EXPLICIT) {
+                T r0 = T(0), r1 = T(0), r2 = T(0), rr = T(0);
+#pragma unroll
+                for (int k = 0; k < 9; ++k) {
+                    const T r = Ar[k] - ftp[k];
+                    r0 += r;
+                    if (L::cx(k)) r1 += T(L::cx(k)) * r;
+                    if (L::cy(k)) r2 += T(L::cy(k)) * r;
+                    rr += r * r;
+                }
+                pr[oidx] = r0;
+                pr[NN + oidx] = r1;
+                pr[2 * NN + oidx] = r2;
+                ssq_f += rr;
+                if (((j - y0) & 7) == 0) { ssq += (double)ssq_f; ssq_f = T(0); }
+            }
+        }
+        // rotate: row j keeps its c_y = 0 values and the c_y = +1 values of row j-1
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            if (L::cy(k) == 0) Ar[k] = C[k];
+            else if (L::cy(k) == 1) { Ar[k] = Br[k]; Br[k] = C[k]; }
+            ftp[k] = f[k];
+        }
+    }
+    ssq += (double)ssq_f;
+    return ssq;
+}
+
 template <typename T, bool EXPLICIT, bool GRAPH>
 __global__ void __launch_bounds__(kSweepWarps * 32) k_sweep2(Sweep2Args<T> A) {
-    using L = D2Q9;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int n = A.n;
-    const int nmask = n - 1;
     const size_t NN = (size_t)n * n;
 
     const T* fin = A.fin;
@@ -133,111 +244,9 @@ __global__ void __launch_bounds__(kSweepWarps * 32) k_sweep2(Sweep2Args<T> A) {
 
     const int unit = blockIdx.x * kSweepWarps + warp;
     double ssq = 0.0;
-    if (unit < A.nstrips * A.nrowblk) {  // warp-uniform
-        const int strip = unit % A.nstrips;
-        const int rb = unit / A.nstrips;
-        const int x0 = strip * kStripOut;
-        const int y0 = rb * A.hb;
-        const int x = (x0 - 1 + lane) & nmask;
-        const bool out_lane = lane >= 1 && lane <= kStripOut && (x0 + lane - 1) < n;
-
-        T Ar[9], Br[9], ftp[9];
-#pragma unroll
-        for (int k = 0; k < 9; ++k) { Ar[k] = T(0); Br[k] = T(0); ftp[k] = T(0); }
-        T ssq_f = T(0);
-
-        // software pipeline: the loads of row j+1 are issued before row j is collided
-        T nf[9], ndp = T(0), ndx = T(0), ndy = T(0), nh0 = T(0), nh1 = T(0), nh2 = T(0);
-        auto load_row = [&](int jr) {
-            const size_t id = (size_t)(jr & nmask) * n + x;
-#pragma unroll
-            for (int k = 0; k < 9; ++k) nf[k] = fin[k * NN + id];
-            if (!EXPLICIT) {
-                if (lift) { ndp = dm[id]; ndx = dm[NN + id]; ndy = dm[2 * NN + id]; }
-                nh0 = hh[id]; nh1 = hh[NN + id]; nh2 = hh[2 * NN + id];
-            }
-        };
-        load_row(y0 - 1);
-        for (int j = y0 - 1; j <= y0 + A.hb; ++j) {
-            T f[9];
-#pragma unroll
-            for (int k = 0; k < 9; ++k) f[k] = nf[k];
-            const T dp = ndp, dux = ndx, duy = ndy, h0 = nh0, h1 = nh1, h2 = nh2;
-            if (j < y0 + A.hb) load_row(j + 1);
-            if (!EXPLICIT && lift) {  // trial f = f_T,prev + E dm   (Eq. lift)
-#pragma unroll
-                for (int k = 0; k < 9; ++k)
-                    f[k] += (T)L::w(k) * (dp + T(3) * (T(L::cx(k)) * dux + T(L::cy(k)) * duy));
-            }
-            // moments (Eq. moments)
-            T rho = T(0), jx = T(0), jy = T(0);
-#pragma unroll
-            for (int k = 0; k < 9; ++k) {
-                rho += f[k];
-                if (L::cx(k)) jx += T(L::cx(k)) * f[k];
-                if (L::cy(k)) jy += T(L::cy(k)) * f[k];
-            }
-            T p, ux, uy, s0 = T(0), sx = T(0), sy = T(0);
-            if (EXPLICIT) {
-                p = rho; ux = jx; uy = jy;
-            } else {  // half-source reconstruction and source moments (Eqs. macro-reconstruct, source-moments)
-                p = (rho + h0 * T(0.5)) * inv;
-                ux = (jx + h1 * T(0.5)) * inv;
-                uy = (jy + h2 * T(0.5)) * inv;
-                s0 = h0 - a * p;
-                sx = h1 - a * ux;
-                sy = h2 - a * uy;
-            }
-            // operating-point collision C = f_eq + Phi/2 (Eq. collision-operating)
-            const T A0 = p + T(0.5) * s0 - T(1.5) * (ux * ux + uy * uy) - T(1.5) * (ux * sx + uy * sy);
-            T C[9];
-#pragma unroll
-            for (int k = 0; k < 9; ++k) {
-                const T cu = T(L::cx(k)) * ux + T(L::cy(k)) * uy;
-                const T cs = T(L::cx(k)) * sx + T(L::cy(k)) * sy;
-                C[k] = (T)L::w(k) * (A0 + T(3) * cu + T(1.5) * cs + T(4.5) * cu * (cu + cs));
-            }
-            // push streaming in x: value for column x comes from column x - c_kx
-#pragma unroll
-            for (int k = 0; k < 9; ++k) {
-                if (L::cx(k) == 1) C[k] = __shfl_up_sync(0xffffffffu, C[k], 1);
-                else if (L::cx(k) == -1) C[k] = __shfl_down_sync(0xffffffffu, C[k], 1);
-            }
-            // row j-1 receives the c_y = -1 directions and is complete
-#pragma unroll
-            for (int k = 0; k < 9; ++k)
-                if (L::cy(k) == -1) Ar[k] = C[k];
-            if (j - 1 >= y0 && out_lane) {
-                const size_t oidx = (size_t)((j - 1) & nmask) * n + x;
-#pragma unroll
-                for (int k = 0; k < 9; ++k) fout[k * NN + oidx] = Ar[k];
-                if (!EXPLICIT) {
-                    T r0 = T(0), r1 = T(0), r2 = T(0), rr = T(0);
-#pragma unroll
-                    for (int k = 0; k < 9; ++k) {
-                        const T r = Ar[k] - ftp[k];
-                        r0 += r;
-                        if (L::cx(k)) r1 += T(L::cx(k)) * r;
-                        if (L::cy(k)) r2 += T(L::cy(k)) * r;
-                        rr += r * r;
-                    }
-                    pr[oidx] = r0;
-                    pr[NN + oidx] = r1;
-                    pr[2 * NN + oidx] = r2;
-                    ssq_f += rr;
-                    if (((j - y0) & 7) == 0) { ssq += (double)ssq_f; ssq_f = T(0); }
-                }
-            }
-            // rotate: row j keeps its c_y = 0 values and the c_y = +1 values of row j-1
-#pragma unroll
-            for (int k = 0; k < 9; ++k) {
-                if (L::cy(k) == 0) Ar[k] = C[k];
-                else if (L::cy(k) == 1) { Ar[k] = Br[k]; Br[k] = C[k]; }
-                ftp[k] = f[k];
-            }
-        }
-        ssq += (double)ssq_f;
-    }
+    if (unit < A.nstrips * A.nrowblk)  // warp-uniform
+        ssq = sweep2_unit<T, EXPLICIT>(fin, dm, hh, fout, pr, a, inv, lift, n, A.hb, unit % A.nstrips,
+                                       unit / A.nstrips, lane);
     if (EXPLICIT) return;
 
     // ---- residual norm: block partials, last block reduces in a fixed order ----

@@ -67,11 +67,14 @@ class MscLattice:
             pass
 
     def set_params(self, dt: float, eps: float = 1e-8, nu: float = 1.0 / 6.0, kmax: int = 300,
-                   nmin=None, corrector: bool = True, replay: bool = False, warm_order: int = 0):
-        """warm_order: 3 cubic (Section 3.1), 2 linear, 1 none; 0 = 3 for FP64, FP32: 2 (D2Q9) / 1 (D3Q19)."""
+                   nmin=None, corrector: bool = True, replay: bool = False, warm_order: int = 0,
+                   count_multiple: int = 0):
+        """warm_order: 3 cubic (Section 3.1), 2 linear, 1 none; 0 = 3 for FP64, FP32: 2 (D2Q9) / 1 (D3Q19).
+        count_multiple: accepted inner counts are multiples of it (1 = Algorithm 1, 2 = sweeps in pairs);
+        0 = 2 for FP32 D2Q9, else 1."""
         if nmin is None:
             nmin = 2 if self.dim == 2 else 1
-        p = L.Params(nu, dt, eps, kmax, nmin, int(corrector), int(replay), int(warm_order))
+        p = L.Params(nu, dt, eps, kmax, nmin, int(corrector), int(replay), int(warm_order), int(count_multiple))
         L.check(L.lib.msc_set_params(self._ctx, ctypes.byref(p)), "msc_set_params")
 
     def init_fields(self, p_hat, u):
@@ -145,6 +148,80 @@ class MscLattice:
 
 
 # ---- stage calls ---------------------------------------------------------------------------------
+
+class MscBatch:
+    """Several D2Q9 lattices (one precision, one stream, any mix of n and parameters) marched by one
+    CUDA graph; see msc_batch_* in include/msclbm.h.  Per-instance setup and read-back stay on the
+    MscLattice objects (set_params, init_fields, stats, fields, step_iters ...)."""
+
+    def __init__(self, lattices):
+        self.lattices = list(lattices)
+        k = len(self.lattices)
+        if k == 0:
+            raise ValueError("empty batch")
+        self.stream = self.lattices[0].stream
+        arr = (ctypes.c_void_p * k)(*[lat._ctx.value for lat in self.lattices])
+        nbytes = L.lib.msc_batch_workspace_bytes(arr, k)
+        if nbytes == 0:
+            raise ValueError("invalid batch: D2Q9 lattices of one precision, at most "
+                             f"{L.MSC_BATCH_MAX} of them and {L.MSC_BATCH_CLASSES} distinct n")
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.lattices[0].device)
+        self._b = ctypes.c_void_p()
+        L.check(L.lib.msc_batch_create(ctypes.byref(self._b), arr, k, _ptr(self.workspace), nbytes,
+                                       self.stream.cuda_stream), "msc_batch_create")
+
+    def close(self):
+        if self._b:
+            L.lib.msc_batch_destroy(self._b)
+            self._b = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _counts(self, n_steps):
+        if isinstance(n_steps, int):
+            n_steps = [n_steps] * len(self.lattices)
+        if len(n_steps) != len(self.lattices):
+            raise ValueError("one step count per lattice")
+        return (ctypes.c_int * len(n_steps))(*[int(v) for v in n_steps])
+
+    def march(self, n_steps):
+        """n_steps: one count per lattice (or one int for all)."""
+        L.check(L.lib.msc_batch_march(self._b, self._counts(n_steps)), "msc_batch_march")
+
+    def explicit_march(self, n_steps):
+        L.check(L.lib.msc_batch_explicit_march(self._b, self._counts(n_steps)), "msc_batch_explicit_march")
+
+    @staticmethod
+    def _tuning_dict(t) -> dict:
+        k = t.n_classes
+        return {"n": list(t.n[:k]), "sweep_rows": list(t.sweep_rows[:k]), "fft_rows": list(t.fft_rows[:k]),
+                "col_lines": list(t.col_lines[:k]), "sweep_ctas_per_sm": t.sweep_ctas_per_sm,
+                "sweep_us": t.sweep_us, "rowfft_us": t.rowfft_us, "colsolve_us": t.colsolve_us}
+
+    def autotune(self, reps: int = 5) -> dict:
+        t = L.BatchTuning()
+        L.check(L.lib.msc_batch_autotune(self._b, int(reps), ctypes.byref(t)), "msc_batch_autotune")
+        return self._tuning_dict(t)
+
+    @property
+    def tuning(self) -> dict:
+        t = L.BatchTuning()
+        L.check(L.lib.msc_batch_get_tuning(self._b, ctypes.byref(t)), "msc_batch_get_tuning")
+        return self._tuning_dict(t)
+
+    def set_tuning(self, tun: dict):
+        t = L.BatchTuning()
+        L.check(L.lib.msc_batch_get_tuning(self._b, ctypes.byref(t)), "msc_batch_get_tuning")
+        for key in ("sweep_rows", "fft_rows", "col_lines"):
+            for c, v in enumerate(tun[key]):
+                getattr(t, key)[c] = int(v)
+        t.sweep_ctas_per_sm = int(tun["sweep_ctas_per_sm"])
+        L.check(L.lib.msc_batch_set_tuning(self._b, ctypes.byref(t)), "msc_batch_set_tuning")
+
 
 class StageScratch:
     def __init__(self, dim: int, n: int, precision: str, device="cuda"):

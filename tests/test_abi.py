@@ -67,3 +67,33 @@ def test_argument_errors_need_no_device(L):
     assert L.lib.msc_march(None, 1) == L.MSC_ERR_ARG
     assert L.strerror(L.MSC_ERR_NONCONVERGED).startswith("physical step")
     assert L.strerror(99) == "unknown status"
+
+
+def test_batch_tuning_struct_matches_header(L, tmp_path):
+    # the ctypes mirror of msc_batch_tuning has the C layout (size and field offsets)
+    src = tmp_path / "t.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "msclbm.h"\nint main(void){'
+                   'printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(msc_batch_tuning),'
+                   ' offsetof(msc_batch_tuning, sweep_rows), offsetof(msc_batch_tuning, col_lines),'
+                   ' offsetof(msc_batch_tuning, sweep_ctas_per_sm), offsetof(msc_batch_tuning, sweep_us),'
+                   ' offsetof(msc_batch_tuning, colsolve_us)); return 0; }\n')
+    import subprocess
+    exe = tmp_path / "t"
+    r = subprocess.run(["gcc", "-std=c99", str(src), "-I", os.path.dirname(HEADER), "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
+    T = L.BatchTuning
+    assert got == [ctypes.sizeof(T), T.sweep_rows.offset, T.col_lines.offset, T.sweep_ctas_per_sm.offset,
+                   T.sweep_us.offset, T.colsolve_us.offset]
+    assert L.MSC_BATCH_MAX == 64 and L.MSC_BATCH_CLASSES == 8
+
+
+def test_batch_rejects_invalid_lists_without_a_device(L):
+    # validation happens before any device work: an empty or NULL list sizes to 0 and create refuses it
+    assert L.lib.msc_batch_workspace_bytes(None, 0) == 0
+    assert L.lib.msc_batch_workspace_bytes(None, 3) == 0
+    h = ctypes.c_void_p()
+    assert L.lib.msc_batch_create(ctypes.byref(h), None, 0, None, 0, None) == L.MSC_ERR_ARG
+    assert L.lib.msc_batch_march(None, None) == L.MSC_ERR_ARG
+    assert L.lib.msc_batch_autotune(None, 1, None) == L.MSC_ERR_ARG

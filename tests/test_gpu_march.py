@@ -23,7 +23,7 @@ def _lattice(dim, n, precision, **kw):
 def _replay_run(dim, n, precision, p, u, prm: OM.MarchParams, counts, corrector=True):
     L = _lattice(dim, n, precision)
     L.set_params(dt=prm.dt, eps=prm.eps, nu=prm.nu, kmax=prm.kmax, nmin=prm.nmin, corrector=corrector,
-                 replay=True, warm_order=prm.warm_order)
+                 replay=True, warm_order=prm.warm_order, count_multiple=prm.count_multiple)
     L.set_replay_counts(counts)
     L.init_fields(p, u)
     L.march(len(counts))
@@ -143,7 +143,8 @@ def test_fp32_storage_against_fp64_oracle(dim, N, steps):
     # FP32 deviation storage with FP64 history and solve: gate 1e-5 relative L2 in u
     p, u = random_phase(N, dim, 1.0, seed=12, kmax=8 if dim == 2 else 4)
     # the FP32 path's default warm start is the linear one (warm_order 2); the oracle uses the same
-    prm = OM.MarchParams(dt=32.0, eps=1e-9, nmin=2 if dim == 2 else 1, warm_order=2)
+    prm = OM.MarchParams(dt=32.0, eps=1e-9, nmin=2 if dim == 2 else 1, warm_order=2,
+                         count_multiple=2 if dim == 2 else 1)
     st = OM.init_state(lattice_for_dim(dim), p, u)
     recs = OM.march(st, prm, steps)
     L = _replay_run(dim, N, "fp32", p, u, prm, [r.iters for r in recs])
@@ -270,7 +271,8 @@ def test_stepwise_march_equals_graph_march(dim, N, precision):
 def test_fp32_long_run_stays_at_a_few_iterations():
     # D2Q9 N = 256, Re = 1, 64 steps of dt = 153.6: with FP32 storage the cubic warm start grows the
     # rounding in the staggered modes (k = (pi, 0), (0, pi): P Z E has eigenvalue -1 there, outside the
-    # mask) until the inner solve stalls; the linear warm start (FP32 default) keeps 2-3 iterations
+    # mask) until the inner solve stalls; the linear warm start with inner sweeps in pairs (the FP32
+    # D2Q9 defaults) keeps 2-4 iterations
     N, S = 256, 64
     p, u = random_phase(N, 2, 1.0, seed=1)
     L = _lattice(2, N, "fp32")
@@ -291,3 +293,20 @@ def test_warm_order_parity_fp64(order):
     recs = OM.march(st, prm, 5)
     L = _replay_run(2, 32, "fp64", p, u, prm, [r.iters for r in recs])
     assert rel_l2(host(L.fields()[1]), st.m_n[1:]) < 1e-12
+
+
+def test_count_multiple_free_run_fp64():
+    # sweeps in pairs: the free-running GPU march takes the oracle's (even) inner counts
+    N = 32
+    p, u = random_phase(N, 2, 1.0, seed=8, kmax=4)
+    prm = OM.MarchParams(dt=30.0, eps=1e-11, warm_order=2, count_multiple=2)
+    st = OM.init_state(lattice_for_dim(2), p, u)
+    recs = OM.march(st, prm, 6)
+    L = _lattice(2, N, "fp64")
+    L.set_params(dt=prm.dt, eps=prm.eps, warm_order=2, count_multiple=2)
+    L.init_fields(p, u)
+    L.march(6)
+    it = L.step_iters().tolist()
+    assert all(k % 2 == 0 for k in it) and L.stats()["status"] == 0
+    assert np.mean(np.array(it) == np.array([r.iters for r in recs])) >= 0.8
+    assert rel_l2(host(L.fields()[1]), st.m_n[1:]) < 1e-8

@@ -160,3 +160,46 @@ def test_warm_start_orders():
     assert np.allclose(M.warm_start(quad, 3), 16.0)
     lin = [np.full(1, 2 * tt + 1) for tt in t]
     assert np.allclose(M.warm_start(lin, 2), 9.0)
+
+
+def _staggered_amplitudes(warm_order, count, steps=8):
+    # u_x perturbed by 1e-9 (-1)^x: the k = (pi, 0) staggered mode, sweep eigenvalue -1 and outside
+    # the shadow mask; the inner count is forced (replay) so only the warm start and its parity act
+    N = 32
+    p, u = random_phase(N, 2, 1.0, seed=3, kmax=4)
+    stag = (-1.0) ** np.arange(N)[None, :] * np.ones((N, 1))
+    st = M.init_state(D2Q9, p, u + 1e-9 * np.stack([stag, 0 * stag]))
+    prm = M.MarchParams(dt=40.0, eps=1.0, warm_order=warm_order)
+    amps = []
+    for _ in range(steps):
+        M.physical_step(st, prm, replay_count=count)
+        amps.append(abs(np.fft.fft2(st.m_n[1])[0, N // 2]) / N ** 2)
+    return np.array(amps)
+
+
+def test_staggered_mode_under_warm_start_and_count_parity():
+    # per step the staggered mode is multiplied by c = (-gamma)^l after the warm start; with the
+    # linear extrapolation e' = c (2e - e_prev) an odd count (c ~ -1) grows it by ~1 + sqrt(2),
+    # the cubic one by more, while an even count (c ~ +1) or no extrapolation keeps it bounded
+    lin_odd = _staggered_amplitudes(2, 3)
+    assert np.all(lin_odd[3:] / lin_odd[2:-1] > 2.0)
+    cub_odd = _staggered_amplitudes(3, 3)
+    assert cub_odd[-1] / cub_odd[-2] > 3.0
+    for wo, cnt in ((2, 2), (2, 4), (1, 3)):
+        a = _staggered_amplitudes(wo, cnt)
+        assert a.max() < 1.1e-9, (wo, cnt)
+
+
+def test_count_multiple_accepts_even_counts_at_the_same_fixed_point():
+    N = 32
+    p, u = random_phase(N, 2, 1.0, seed=8, kmax=4)
+    out = {}
+    for cm in (1, 2):
+        st = M.init_state(D2Q9, p, u)
+        recs = M.march(st, M.MarchParams(dt=30.0, eps=1e-11, warm_order=2, count_multiple=cm), 6)
+        assert all(r.converged for r in recs)
+        out[cm] = (st.fields()[1].copy(), [r.iters for r in recs])
+    assert all(k % 2 == 0 for k in out[2][1])
+    assert any(k % 2 == 1 for k in out[1][1])  # the case exercises the rule
+    # both accept at R < eps: the states agree to the tolerance amplified by the slow rate
+    assert velocity_error(out[1][0], out[2][0]) < 1e-11 / (1 - gamma(3 / 60.0)) * 10

@@ -33,6 +33,7 @@ sys.path.insert(0, ROOT)
 from workloads.fields import random_phase  # noqa: E402
 from workloads.metrics import nint, rms_vector, velocity_error  # noqa: E402
 from workloads.nsref import navier_stokes_reference  # noqa: E402
+from paper_2609_39474_b300 import diagnostics as DG  # noqa: E402  (pure Python, no library load)
 
 METRIC = "Matched-accuracy speedup vs explicit GPU LBM; inner MLUPS and HBM GB/s"
 NU = 1.0 / 6.0
@@ -212,6 +213,12 @@ def measure_workload(torch, PL, dev, dim, n, steps, warmup, dist=None, full=Fals
         ms_step = float(t.item())
     u_msc = L.fields()[1].cpu().numpy()
     e_msc = velocity_error(u_msc, u_ref)
+    # diagnostics of the last timed march (Eqs. rho-observed, swork)
+    per_step = DG.step_residuals(L.residual_history(), L.step_iters())
+    rho = [DG.rho_observed(r, 10 if dim == 2 else 8) for r in per_step]
+    rho = [x for x in rho if x is not None]
+    diag = {"s_work": DG.work_ratio(t_end, inner[-1], S), "rho_obs_max": max(rho) if rho else None,
+            "rho_obs_steps": len(rho), "final_residual": per_step[-1][-1] if per_step else None}
     s_1pct = t_ex / min(msc_once(best1["S"], best1["eps"])[0] for _ in range(3)) if best1 else None
     res = {
         "workload": f"{'D2Q9' if dim == 2 else 'D3Q19'} periodic N={n} Re=1 random-phase seed {w['seed']} FP32",
@@ -221,7 +228,7 @@ def measure_workload(torch, PL, dev, dim, n, steps, warmup, dist=None, full=Fals
         "e_explicit": e_ex, "e_msc": e_msc, "rms_ref": rms_vector(u_ref), "t_end": t_end,
         "explicit_mlups": n ** dim * t_end / (t_ex * 1e3),
         "candidates": [{k: c[k] for k in c if k != "err"} for c in cands],
-        "clocks": clk, "launches": launches,
+        "clocks": clk, "launches": launches, "diagnostics": diag,
     }
     if full:
         # -- end to end through the C ABI with host buffers (H2D of p, u and D2H of the fields) ---
@@ -668,6 +675,7 @@ def main():
         "errors": {"e_msc": res["e_msc"], "e_explicit": res["e_explicit"], "rms_ref": res["rms_ref"],
                    "matched_gate": "e_msc <= 3 e_explicit"},
         "candidate_1pct": res["candidate_1pct"],
+        "diagnostics": res["diagnostics"],
         "explicit_mlups": res["explicit_mlups"],
         "sweep_at_n": res["sweep_at_n"],
         "candidates": res["candidates"],

@@ -19,9 +19,10 @@
  *    (k in the paper's ordering, Appendix A), fields m[c][z][y][x] with
  *    c = 0 the pressure-like variable p_hat and c = 1..d the velocity
  *    components.  2D arrays drop the z index.  "sites" = n^dim.
- *  - Storage precision (MSC_FP64 / MSC_FP32) fixes the element type of
- *    population and working-field arrays (double / float).  Host-facing
- *    fields (p_hat, u, residual norms, BDF moment history) are always double.
+ *  - Storage precision (MSC_FP64 / MSC_FP32 / MSC_FP16) fixes the element type of
+ *    population arrays (double / float / half) and working-field arrays (double /
+ *    float / float).  Host-facing fields (p_hat, u, residual norms, BDF moment history)
+ *    are always double.
  *  - Device pointers must come from cudaMalloc-class allocations of the
  *    current device; the library never frees caller memory and never
  *    allocates device memory itself (the context lives in a caller-provided
@@ -59,13 +60,18 @@ extern "C" {
 /* Storage precisions. */
 #define MSC_FP64 0
 #define MSC_FP32 1
+#define MSC_FP16 2 /* D2Q9 only: populations in IEEE binary16 as f / sigma, sigma = the power of two
+                      just above max |f^0| (chosen by msc_init_fields; exact scaling), rounded to
+                      nearest on every store; h, P r, dm and the spectrum FP32, BDF moment history,
+                      residual norm and per-wavenumber solve FP64, arithmetic FP32.  Stage entry
+                      points take FP16 population arrays (sigma = 1) and FP32 field arrays. */
 
 typedef struct msc_ctx msc_ctx; /* opaque; lives inside the caller's workspace */
 
 typedef struct {
     int dim;        /* 2: D2Q9, 3: D3Q19 (Appendix A orderings) */
     int n;          /* sites per direction (power of two, see limits above) */
-    int precision;  /* MSC_FP64 or MSC_FP32 population storage */
+    int precision;  /* MSC_FP64, MSC_FP32 or MSC_FP16 (D2Q9) population storage */
     int max_steps;  /* capacity of the per-step statistics and replay tables (>= 1) */
     int hist_cap;   /* capacity of the inner-residual history ring (>= 1) */
 } msc_lattice_desc;

@@ -18,6 +18,7 @@ MSC_ERR_CUDA = 5
 MSC_ERR_STATE = 6
 MSC_FP64 = 0
 MSC_FP32 = 1
+MSC_FP16 = 2
 
 
 class LatticeDesc(ctypes.Structure):

@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(kSweepWarps * 32) k_bsweep2(const BInst<T>* __
             inv = T(1);
             lift = 0;
         }
-        double ssq = sweep2_unit<T, MODE == 2>(fin, A.dm, A.h, fout, A.pr, a, inv, lift, A.n, A.hb,
+        double ssq = sweep2_unit<T, T, MODE == 2>(fin, A.dm, A.h, fout, A.pr, a, inv, lift, A.n, A.hb,
                                                lu % A.nstrips, lu / A.nstrips, lane);
         if (MODE == 2) continue;
 #pragma unroll

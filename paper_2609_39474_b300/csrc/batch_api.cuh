@@ -42,6 +42,7 @@ bool batch_list_ok(msc_ctx* const* ctxs, int n_inst, int* n_classes) {
     for (int i = 0; i < n_inst; ++i) {
         const msc_ctx* c = ctxs[i];
         if (!c || c->desc.dim != 2 || c->desc.precision != ctxs[0]->desc.precision) return false;
+        if (c->desc.precision == MSC_FP16) return false;  // batches hold FP32 or FP64 storage
         for (int j = 0; j < i; ++j)
             if (ctxs[j] == c) return false;  // one context once
         bool seen = false;

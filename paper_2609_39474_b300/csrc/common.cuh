@@ -2,8 +2,11 @@
 // helpers.  Internal header (not part of the C ABI).
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <type_traits>
 
 #include "../../include/msclbm.h"
 
@@ -79,6 +82,9 @@ struct DevState {
     int ex_loops_left;
     // the next physical step's h and trial populations were already formed by k_step_end
     int prepared;
+    // population storage scale sigma (a power of two): FP16 storage holds f / sigma; 1 otherwise
+    double fscale;
+    unsigned long long fmax_bits;  // max |f^0| (bits of a non-negative double) while sigma is chosen
 };
 
 // Layout of the context workspace (byte offsets from the workspace base).
@@ -99,13 +105,31 @@ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 inline int lattice_q(int dim) { return dim == 2 ? 9 : 19; }
 
-// size limits: shared-memory transforms hold one full line (2D) or plane chunk (3D) per block
+// size limits: shared-memory transforms hold one full line (2D) or plane chunk (3D) per block;
+// FP16 population storage exists for D2Q9
 inline bool valid_lattice(int dim, int n, int precision) {
-    if (precision != MSC_FP64 && precision != MSC_FP32) return false;
+    if (precision != MSC_FP64 && precision != MSC_FP32 && precision != MSC_FP16) return false;
     if (!is_pow2(n) || n < 8) return false;
     if (dim == 2) return n <= (precision == MSC_FP64 ? 2048 : 4096);
-    if (dim == 3) return n <= (precision == MSC_FP64 ? 128 : 256);
+    if (dim == 3) return precision != MSC_FP16 && n <= (precision == MSC_FP64 ? 128 : 256);
     return false;
+}
+
+// bytes of one stored population value and of one working-field value (h, P r, dm)
+inline size_t pop_elem(int precision) { return precision == MSC_FP64 ? 8 : (precision == MSC_FP32 ? 4 : 2); }
+inline size_t field_elem(int precision) { return precision == MSC_FP64 ? 8 : 4; }
+
+// Population loads and stores in the compute type T.  FP16 storage (S = __half) holds f / sigma
+// with sigma a power of two (exact scaling), rounded to nearest; other storage holds f itself.
+template <typename T, typename S>
+__device__ __forceinline__ T ld_pop(const S* p, size_t i, T sig) {
+    if constexpr (std::is_same<S, __half>::value) return sig * (T)__half2float(p[i]);
+    else return (T)p[i];
+}
+template <typename T, typename S>
+__device__ __forceinline__ void st_pop(S* p, size_t i, T v, T isig) {
+    if constexpr (std::is_same<S, __half>::value) p[i] = __float2half_rn((float)(v * isig));
+    else p[i] = (S)v;
 }
 
 }  // namespace msc

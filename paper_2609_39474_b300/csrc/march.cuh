@@ -20,10 +20,16 @@ __device__ __forceinline__ double cdotu(int k, const double* u) {
     return s;
 }
 
-// f = f_eq(p_hat, u)   (Eq. feq); p and u are double fields, f in the storage type
-template <class L, typename T>
+// storage scale of the populations: from the state when there is one, else 1
+__device__ __forceinline__ double pop_scale(const DevState* st) {
+    return st ? ((const volatile DevState*)st)->fscale : 1.0;
+}
+
+// f = f_eq(p_hat, u)   (Eq. feq); p and u are double fields, f in the storage type S
+template <class L, typename S>
 __global__ void k_equilibrium(const double* __restrict__ p, const double* __restrict__ u,
-                              T* __restrict__ f, size_t sites) {
+                              S* __restrict__ f, size_t sites, const DevState* st = nullptr) {
+    const double isig = 1.0 / pop_scale(st);
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < sites;
          i += (size_t)gridDim.x * blockDim.x) {
         double uv[3] = {0.0, 0.0, 0.0};
@@ -37,21 +43,62 @@ __global__ void k_equilibrium(const double* __restrict__ p, const double* __rest
 #pragma unroll
         for (int k = 0; k < L::Q; ++k) {
             const double cu = cdotu<L>(k, uv);
-            f[k * sites + i] = (T)(L::w(k) * (ph + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu));
+            st_pop<double, S>(f, k * sites + i, L::w(k) * (ph + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu), isig);
         }
     }
 }
 
+// max |f_eq(p_hat, u)| over sites and directions into st->fmax_bits (FP16 storage scale)
+template <class L>
+__global__ void k_feq_absmax(const double* __restrict__ p, const double* __restrict__ u, size_t sites,
+                             DevState* st) {
+    double mx = 0.0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < sites;
+         i += (size_t)gridDim.x * blockDim.x) {
+        double uv[3] = {0.0, 0.0, 0.0};
+        double uu = 0.0;
+#pragma unroll
+        for (int al = 0; al < L::D; ++al) {
+            uv[al] = u[al * sites + i];
+            uu += uv[al] * uv[al];
+        }
+        const double ph = p[i];
+#pragma unroll
+        for (int k = 0; k < L::Q; ++k) {
+            const double cu = cdotu<L>(k, uv);
+            mx = fmax(mx, fabs(L::w(k) * (ph + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu)));
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    // non-negative doubles order like their bit patterns
+    if ((threadIdx.x & 31) == 0 && mx > 0.0)
+        atomicMax(&st->fmax_bits, (unsigned long long)__double_as_longlong(mx));
+}
+
+// sigma = the power of two just above max |f^0| (1 for a zero field): stored values |f| / sigma < 1
+__global__ void k_set_scale(DevState* st) {
+    const double mx = __longlong_as_double((long long)st->fmax_bits);
+    double sig = 1.0;
+    if (mx > 0.0 && isfinite(mx)) {
+        int e;
+        frexp(mx, &e);  // mx = m 2^e with 0.5 <= m < 1
+        sig = ldexp(1.0, e);
+    }
+    st->fscale = sig;
+}
+
 // m = P f in double (Eq. moments); optionally a second copy
-template <class L, typename T>
-__global__ void k_moments(const T* __restrict__ f, double* __restrict__ m, double* __restrict__ m2,
-                          size_t sites) {
+template <class L, typename S>
+__global__ void k_moments(const S* __restrict__ f, double* __restrict__ m, double* __restrict__ m2,
+                          size_t sites, const DevState* st = nullptr) {
+    const double sig = pop_scale(st);
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < sites;
          i += (size_t)gridDim.x * blockDim.x) {
         double r = 0.0, jx = 0.0, jy = 0.0, jz = 0.0;
 #pragma unroll
         for (int k = 0; k < L::Q; ++k) {
-            const double v = (double)f[k * sites + i];
+            const double v = ld_pop<double, S>(f, k * sites + i, sig);
             r += v;
             if (L::cx(k)) jx += L::cx(k) * v;
             if (L::cy(k)) jy += L::cy(k) * v;
@@ -72,8 +119,8 @@ __global__ void k_moments(const T* __restrict__ f, double* __restrict__ m, doubl
 
 // Start of a physical step: h_q from the accepted moment histories (Eq. bdf2) and the trial
 // populations from the population-history extrapolation (Section 3.1) into the working slot.
-template <class L, typename T>
-__device__ __forceinline__ void step_begin_range(const DevState* __restrict__ st, T* __restrict__ fbase,
+template <class L, typename T, typename S = T>
+__device__ __forceinline__ void step_begin_range(const DevState* __restrict__ st, S* __restrict__ fbase,
                                                  size_t fstride, const double* __restrict__ mbuf,
                                                  T* __restrict__ h, size_t sites, size_t i0, size_t istride) {
     const volatile DevState* vs = st;
@@ -84,12 +131,13 @@ __device__ __forceinline__ void step_begin_range(const DevState* __restrict__ st
     const size_t mstride = (size_t)(L::D + 1) * sites;
     const double* mn = mbuf + (size_t)vs->m_cur * mstride;
     const double* mnm1 = mbuf + (size_t)vs->m_prev * mstride;
-    const T* f0 = fbase + (size_t)vs->slot_fn[0] * fstride;
-    const T* f1 = fbase + (size_t)vs->slot_fn[1] * fstride;
-    const T* f2 = fbase + (size_t)vs->slot_fn[2] * fstride;
-    T* ft = fbase + (size_t)vs->slot_cur * fstride;
+    const S* f0 = fbase + (size_t)vs->slot_fn[0] * fstride;
+    const S* f1 = fbase + (size_t)vs->slot_fn[1] * fstride;
+    const S* f2 = fbase + (size_t)vs->slot_fn[2] * fstride;
+    S* ft = fbase + (size_t)vs->slot_cur * fstride;
     const double c1 = q == 1 ? 1.0 / dt : 4.0 / (2.0 * dt);
     const double c2 = q == 1 ? 0.0 : 1.0 / (2.0 * dt);
+    const T sig = (T)vs->fscale, isig = T(1) / sig;
     for (size_t i = i0; i < sites; i += istride) {
 #pragma unroll
         for (int c = 0; c <= L::D; ++c) {
@@ -103,22 +151,23 @@ __device__ __forceinline__ void step_begin_range(const DevState* __restrict__ st
 #pragma unroll
             for (int k = 0; k < L::Q; ++k) {
                 const size_t o = k * sites + i;
-                ft[o] = T(2) * f0[o] - f1[o];
+                st_pop<T, S>(ft, o, T(2) * ld_pop<T, S>(f0, o, sig) - ld_pop<T, S>(f1, o, sig), isig);
             }
         } else {
 #pragma unroll
             for (int k = 0; k < L::Q; ++k) {
                 const size_t o = k * sites + i;
-                ft[o] = T(3) * (f0[o] - f1[o]) + f2[o];
+                st_pop<T, S>(ft, o, T(3) * (ld_pop<T, S>(f0, o, sig) - ld_pop<T, S>(f1, o, sig)) +
+                                        ld_pop<T, S>(f2, o, sig), isig);
             }
         }
     }
 }
 
-template <class L, typename T>
-__global__ void k_step_begin(const DevState* __restrict__ st, T* __restrict__ fbase, size_t fstride,
+template <class L, typename T, typename S = T>
+__global__ void k_step_begin(const DevState* __restrict__ st, S* __restrict__ fbase, size_t fstride,
                              const double* __restrict__ mbuf, T* __restrict__ h, size_t sites) {
-    step_begin_range<L, T>(st, fbase, fstride, mbuf, h, sites, blockIdx.x * (size_t)blockDim.x + threadIdx.x,
+    step_begin_range<L, T, S>(st, fbase, fstride, mbuf, h, sites, blockIdx.x * (size_t)blockDim.x + threadIdx.x,
                            (size_t)gridDim.x * blockDim.x);
 }
 
@@ -128,8 +177,8 @@ __global__ void k_step_begin(const DevState* __restrict__ st, T* __restrict__ fb
 // that step's BDF2 history term h = (4 m^{n+1} - m^n)/(2 dt) and its population warm start
 // (2 f^{n+1} - f^n, or 3 f^{n+1} - 3 f^n + f^{n-1}; Section 3.1) into the free working slot, so
 // that the next k_step_begin has nothing to do.
-template <class L, typename T>
-__device__ __forceinline__ void step_end_range(const DevState* __restrict__ st, T* __restrict__ fbase,
+template <class L, typename T, typename S = T>
+__device__ __forceinline__ void step_end_range(const DevState* __restrict__ st, S* __restrict__ fbase,
                                                size_t fstride, double* __restrict__ mbuf, T* __restrict__ h,
                                                size_t sites, size_t i0, size_t istride) {
     const volatile DevState* vs = st;
@@ -141,15 +190,16 @@ __device__ __forceinline__ void step_end_range(const DevState* __restrict__ st, 
     const size_t mstride = (size_t)(L::D + 1) * sites;
     const double* mn = mbuf + (size_t)vs->m_cur * mstride;
     double* mnm1 = mbuf + (size_t)vs->m_prev * mstride;
-    const T* ft = fbase + (size_t)vs->slot_cur * fstride;
+    const S* ft = fbase + (size_t)vs->slot_cur * fstride;
     const double c1 = q == 1 ? 1.0 / dt : 4.0 / (2.0 * dt);
     const double c2 = q == 1 ? 0.0 : 1.0 / (2.0 * dt);
     const bool next = vs->status == MSC_OK && vs->steps_target > 1;
     int nav = vs->n_avail + 1 < 3 ? vs->n_avail + 1 : 3;  // accepted states after rotation
     if (nav > vs->warm_order) nav = vs->warm_order;
-    const T* f0 = fbase + (size_t)vs->slot_fn[0] * fstride;
-    const T* f1 = fbase + (size_t)vs->slot_fn[1] * fstride;
-    T* trial = fbase + (size_t)vs->slot_nxt * fstride;
+    const S* f0 = fbase + (size_t)vs->slot_fn[0] * fstride;
+    const S* f1 = fbase + (size_t)vs->slot_fn[1] * fstride;
+    S* trial = fbase + (size_t)vs->slot_nxt * fstride;
+    const T sig = (T)vs->fscale, isig = T(1) / sig;
     const double n1 = 4.0 / (2.0 * dt), n2 = 1.0 / (2.0 * dt);  // BDF2 for the next step
     const double k1 = 0.5 * c1 * inv, k2 = 0.5 * c2 * inv;
 #pragma unroll 2
@@ -158,7 +208,7 @@ __device__ __forceinline__ void step_end_range(const DevState* __restrict__ st, 
         T mom[4] = {T(0), T(0), T(0), T(0)};
 #pragma unroll
         for (int k = 0; k < L::Q; ++k) {
-            const T v = ft[k * sites + i];
+            const T v = ld_pop<T, S>(ft, k * sites + i, sig);
             fv[k] = v;
             mom[0] += v;
             if (L::cx(k)) mom[1] += T(L::cx(k)) * v;
@@ -177,26 +227,29 @@ __device__ __forceinline__ void step_end_range(const DevState* __restrict__ st, 
         if (next) {
             if (nav == 1) {
 #pragma unroll
-                for (int k = 0; k < L::Q; ++k) trial[k * sites + i] = fv[k];
+                for (int k = 0; k < L::Q; ++k) st_pop<T, S>(trial, k * sites + i, fv[k], isig);
             } else if (nav == 2) {
 #pragma unroll
-                for (int k = 0; k < L::Q; ++k) trial[k * sites + i] = T(2) * fv[k] - f0[k * sites + i];
+                for (int k = 0; k < L::Q; ++k) {
+                    const size_t o = k * sites + i;
+                    st_pop<T, S>(trial, o, T(2) * fv[k] - ld_pop<T, S>(f0, o, sig), isig);
+                }
             } else {
 #pragma unroll
                 for (int k = 0; k < L::Q; ++k) {
                     const size_t o = k * sites + i;
-                    trial[o] = T(3) * (fv[k] - f0[o]) + f1[o];
+                    st_pop<T, S>(trial, o, T(3) * (fv[k] - ld_pop<T, S>(f0, o, sig)) + ld_pop<T, S>(f1, o, sig), isig);
                 }
             }
         }
     }
 }
 
-template <class L, typename T>
-__global__ void __launch_bounds__(kFieldThreads) k_step_end(const DevState* __restrict__ st, T* __restrict__ fbase,
+template <class L, typename T, typename S = T>
+__global__ void __launch_bounds__(kFieldThreads) k_step_end(const DevState* __restrict__ st, S* __restrict__ fbase,
                                                             size_t fstride, double* __restrict__ mbuf, T* __restrict__ h,
                                                             size_t sites) {
-    step_end_range<L, T>(st, fbase, fstride, mbuf, h, sites, blockIdx.x * (size_t)blockDim.x + threadIdx.x,
+    step_end_range<L, T, S>(st, fbase, fstride, mbuf, h, sites, blockIdx.x * (size_t)blockDim.x + threadIdx.x,
                          (size_t)gridDim.x * blockDim.x);
 }
 
@@ -272,6 +325,8 @@ __global__ void k_reset_history(DevState* st) {
     st->last_q = 0;
     st->R_last = 0.0;
     st->prepared = 0;
+    st->fscale = 1.0;
+    st->fmax_bits = 0ull;
 }
 
 __device__ inline void set_target(DevState* st, int n_steps) {
@@ -375,20 +430,21 @@ __global__ void k_step_finish(DevState* st, int* iters_out, int max_steps,
 }
 
 // m^n = P f^n of the accepted slot into both moment slots (after an explicit march)
-template <class L, typename T>
-__device__ __forceinline__ void moments_state_range(const DevState* __restrict__ st, const T* __restrict__ fbase,
+template <class L, typename T, typename S = T>
+__device__ __forceinline__ void moments_state_range(const DevState* __restrict__ st, const S* __restrict__ fbase,
                                                     size_t fstride, double* __restrict__ mbuf, size_t sites,
                                                     size_t i0, size_t istride) {
     const volatile DevState* vs = st;
-    const T* f = fbase + (size_t)vs->slot_fn[0] * fstride;
+    const S* f = fbase + (size_t)vs->slot_fn[0] * fstride;
     const size_t mstride = (size_t)(L::D + 1) * sites;
+    const double sig = vs->fscale;
     double* m0 = mbuf + (size_t)vs->m_cur * mstride;
     double* m1 = mbuf + (size_t)vs->m_prev * mstride;
     for (size_t i = i0; i < sites; i += istride) {
         double mom[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
         for (int k = 0; k < L::Q; ++k) {
-            const double v = (double)f[k * sites + i];
+            const double v = ld_pop<double, S>(f, k * sites + i, sig);
             mom[0] += v;
             if (L::cx(k)) mom[1] += L::cx(k) * v;
             if (L::cy(k)) mom[2] += L::cy(k) * v;
@@ -402,10 +458,10 @@ __device__ __forceinline__ void moments_state_range(const DevState* __restrict__
     }
 }
 
-template <class L, typename T>
-__global__ void k_moments_state(const DevState* __restrict__ st, const T* __restrict__ fbase, size_t fstride,
+template <class L, typename T, typename S = T>
+__global__ void k_moments_state(const DevState* __restrict__ st, const S* __restrict__ fbase, size_t fstride,
                                 double* __restrict__ mbuf, size_t sites) {
-    moments_state_range<L, T>(st, fbase, fstride, mbuf, sites, blockIdx.x * (size_t)blockDim.x + threadIdx.x,
+    moments_state_range<L, T, S>(st, fbase, fstride, mbuf, sites, blockIdx.x * (size_t)blockDim.x + threadIdx.x,
                               (size_t)gridDim.x * blockDim.x);
 }
 

@@ -69,7 +69,8 @@ bool compute_layout(const msc_lattice_desc* d, Layout* L) {
     const size_t sites = d->dim == 2 ? n * n : n * n * n;
     const size_t Q = lattice_q(d->dim);
     const size_t F = d->dim + 1;
-    const size_t e = d->precision == MSC_FP64 ? 8 : 4;
+    const size_t e = field_elem(d->precision);
+    const size_t ep = pop_elem(d->precision);
     size_t o = 0;
     auto take = [&](size_t bytes) {
         const size_t r = o;
@@ -77,7 +78,7 @@ bool compute_layout(const msc_lattice_desc* d, Layout* L) {
         return r;
     };
     L->state = take(sizeof(DevState));
-    L->fstride = Q * sites * e;
+    L->fstride = Q * sites * ep;
     L->fbuf = take(kNumFBuf * L->fstride);
     L->mbuf = take(2 * F * sites * 8);
     L->h = take(F * sites * e);
@@ -104,9 +105,9 @@ int grid_for(size_t sites) {
 
 // ---- typed helpers ------------------------------------------------------------------------------
 
-template <typename T>
-Sweep2Args<T> sweep2_args_graph(msc_ctx* c) {
-    Sweep2Args<T> A;
+template <typename T, typename FS = T>
+Sweep2Args<T, FS> sweep2_args_graph(msc_ctx* c) {
+    Sweep2Args<T, FS> A;
     memset(&A, 0, sizeof(A));
     const Sweep2Geom g = sweep2_geometry(c->desc.n);
     A.dm = at<T>(c, c->lay.dm);
@@ -119,8 +120,9 @@ Sweep2Args<T> sweep2_args_graph(msc_ctx* c) {
     A.hb = g.hb;
     A.nrowblk = g.nrowblk;
     A.st = at<DevState>(c, c->lay.state);
-    A.fbase = at<T>(c, c->lay.fbuf);
-    A.fstride = c->lay.fstride / sizeof(T);
+    A.fbase = at<FS>(c, c->lay.fbuf);
+    A.fstride = c->lay.fstride / sizeof(FS);
+    A.fscale = 1.0;
     A.hist = at<double>(c, c->lay.hist);
     A.hist_cap = c->desc.hist_cap;
     A.replay_counts = at<int>(c, c->lay.replay);
@@ -238,7 +240,7 @@ int set_smem_limits(int dim, int n) {
     return MSC_OK;
 }
 
-template <class L, typename T>
+template <class L, typename T, typename FS>
 int build_march_graph(msc_ctx* c) {
     cudaError_t err = cudaSuccess;
     int rc = set_smem_limits<T>(c->desc.dim, c->desc.n);
@@ -246,8 +248,8 @@ int build_march_graph(msc_ctx* c) {
     cudaGraph_t g;
     CK(cudaGraphCreate(&g, 0));
     DevState* st = at<DevState>(c, c->lay.state);
-    T* fbase = at<T>(c, c->lay.fbuf);
-    const size_t fstride = c->lay.fstride / sizeof(T);
+    FS* fbase = at<FS>(c, c->lay.fbuf);
+    const size_t fstride = c->lay.fstride / sizeof(FS);
     double* mbuf = at<double>(c, c->lay.mbuf);
     T* h = at<T>(c, c->lay.h);
     int* iters = at<int>(c, c->lay.iters);
@@ -268,13 +270,13 @@ int build_march_graph(msc_ctx* c) {
     void* a_setup[] = {&st, &h_iter, &cond1};
     cudaGraphNode_t setup = add_kernel(body_step, {}, (const void*)k_step_setup, dim3(1), dim3(1), 0, a_setup, &err);
     void* a_begin[] = {&st, &fbase, (void*)&fstride, &mbuf, &h, &sites};
-    cudaGraphNode_t begin = add_kernel(body_step, {setup}, (const void*)k_step_begin<L, T>, dim3(fgrid),
+    cudaGraphNode_t begin = add_kernel(body_step, {setup}, (const void*)k_step_begin<L, T, FS>, dim3(fgrid),
                                        dim3(kFieldThreads), 0, a_begin, &err);
     cudaGraph_t body_iter;
     cudaGraphNode_t wit = add_cond(body_step, {begin}, h_iter, cudaGraphCondTypeWhile, &body_iter, &err);
     if (err != cudaSuccess) { cudaGraphDestroy(g); return MSC_ERR_CUDA; }
     void* a_end[] = {&st, &fbase, (void*)&fstride, &mbuf, &h, &sites};
-    cudaGraphNode_t end = add_kernel(body_step, {wit}, (const void*)k_step_end<L, T>, dim3(fgrid),
+    cudaGraphNode_t end = add_kernel(body_step, {wit}, (const void*)k_step_end<L, T, FS>, dim3(fgrid),
                                      dim3(kFieldThreads), 0, a_end, &err);
     void* a_fin[] = {&st, &iters, &max_steps, &h_step, &cond1};
     add_kernel(body_step, {end}, (const void*)k_step_finish, dim3(1), dim3(1), 0, a_fin, &err);
@@ -282,12 +284,12 @@ int build_march_graph(msc_ctx* c) {
     CK(cudaGraphConditionalHandleCreate(&h_corr, body_iter, 0, 0));
     cudaGraphNode_t sw;
     if (L::D == 2) {
-        Sweep2Args<T> A = sweep2_args_graph<T>(c);
+        Sweep2Args<T, FS> A = sweep2_args_graph<T, FS>(c);
         A.h_iter = h_iter;
         A.h_corr = h_corr;
         A.cond = 1;
         void* a_sw[] = {&A};
-        sw = add_kernel(body_iter, {}, (const void*)k_sweep2<T, false, true>, dim3(sweep2_geometry(c->desc.n).blocks),
+        sw = add_kernel(body_iter, {}, (const void*)k_sweep2<T, FS, false, true>, dim3(sweep2_geometry(c->desc.n).blocks),
                         dim3(kSweepWarps * 32), 0, a_sw, &err);
     } else {
         Sweep3Args<T> A = sweep3_args_graph<T>(c);
@@ -311,7 +313,7 @@ int build_march_graph(msc_ctx* c) {
     return MSC_OK;
 }
 
-template <class L, typename T>
+template <class L, typename T, typename FS>
 int build_explicit_graph(msc_ctx* c) {
     cudaError_t err = cudaSuccess;
     int rc = set_smem_limits<T>(c->desc.dim, c->desc.n);
@@ -332,12 +334,12 @@ int build_explicit_graph(msc_ctx* c) {
         std::vector<cudaGraphNode_t> deps;
         if (prev) deps.push_back(prev);
         if (L::D == 2) {
-            Sweep2Args<T> A = sweep2_args_graph<T>(c);
+            Sweep2Args<T, FS> A = sweep2_args_graph<T, FS>(c);
             A.ex_dir = i & 1;
             A.ex_count = i == kExplicitUnroll - 1;
             A.h_ex = h_ex;
             void* aa[] = {&A};
-            prev = add_kernel(body, deps, (const void*)k_sweep2<T, true, true>, dim3(sweep2_geometry(c->desc.n).blocks),
+            prev = add_kernel(body, deps, (const void*)k_sweep2<T, FS, true, true>, dim3(sweep2_geometry(c->desc.n).blocks),
                               dim3(kSweepWarps * 32), 0, aa, &err);
         } else {
             Sweep3Args<T> A = sweep3_args_graph<T>(c);
@@ -357,10 +359,10 @@ int build_explicit_graph(msc_ctx* c) {
     return MSC_OK;
 }
 
-template <class L, typename T>
+template <class L, typename T, typename FS>
 int run_explicit(msc_ctx* c, int n_steps) {
     if (!c->x_ex) {
-        int rc = build_explicit_graph<L, T>(c);
+        int rc = build_explicit_graph<L, T, FS>(c);
         if (rc) return rc;
     }
     DevState* st = at<DevState>(c, c->lay.state);
@@ -372,9 +374,9 @@ int run_explicit(msc_ctx* c, int n_steps) {
     if (blocks > 0) CK(cudaGraphLaunch(c->x_ex, c->stream));
     for (int i = 0; i < rem; ++i) {  // the remainder alternates a->b, b->a, ... as in the loop body
         if (L::D == 2) {
-            Sweep2Args<T> A = sweep2_args_graph<T>(c);
+            Sweep2Args<T, FS> A = sweep2_args_graph<T, FS>(c);
             A.ex_dir = i & 1;
-            k_sweep2<T, true, true><<<sweep2_geometry(c->desc.n).blocks, kSweepWarps * 32, 0, c->stream>>>(A);
+            k_sweep2<T, FS, true, true><<<sweep2_geometry(c->desc.n).blocks, kSweepWarps * 32, 0, c->stream>>>(A);
         } else {
             Sweep3Args<T> A = sweep3_args_graph<T>(c);
             A.ex_dir = i & 1;
@@ -385,13 +387,13 @@ int run_explicit(msc_ctx* c, int n_steps) {
     k_ex_finish<<<1, 1, 0, c->stream>>>(st, odd);
     CK(cudaGetLastError());
     // m^n = P f^n, m^{n-1} = m^n: read the new slot from the state on the device
-    k_moments_state<L, T><<<grid_for(c->sites), kFieldThreads, 0, c->stream>>>(
-        st, at<T>(c, c->lay.fbuf), c->lay.fstride / sizeof(T), at<double>(c, c->lay.mbuf), c->sites);
+    k_moments_state<L, T, FS><<<grid_for(c->sites), kFieldThreads, 0, c->stream>>>(
+        st, at<FS>(c, c->lay.fbuf), c->lay.fstride / sizeof(FS), at<double>(c, c->lay.mbuf), c->sites);
     CK(cudaGetLastError());
     return MSC_OK;
 }
 
-template <class L, typename T>
+template <class L, typename T, typename FS>
 int run_init(msc_ctx* c, const double* p, const double* u, int on_device) {
     DevState* st = at<DevState>(c, c->lay.state);
     double* m0 = at<double>(c, c->lay.mbuf);
@@ -403,10 +405,16 @@ int run_init(msc_ctx* c, const double* p, const double* u, int on_device) {
     CK(cudaMemcpyAsync(m1 + c->sites, u, fb * L::D, kind, c->stream));
     k_reset_history<<<1, 1, 0, c->stream>>>(st);
     CK(cudaGetLastError());
-    T* f0 = at<T>(c, c->lay.fbuf);
-    k_equilibrium<L, T><<<grid_for(c->sites), kFieldThreads, 0, c->stream>>>(m1, m1 + c->sites, f0, c->sites);
+    FS* f0 = at<FS>(c, c->lay.fbuf);
+    if (std::is_same<FS, __half>::value) {  // storage scale sigma from max |f^0|
+        k_feq_absmax<L><<<grid_for(c->sites), kFieldThreads, 0, c->stream>>>(m1, m1 + c->sites, c->sites, st);
+        CK(cudaGetLastError());
+        k_set_scale<<<1, 1, 0, c->stream>>>(st);
+        CK(cudaGetLastError());
+    }
+    k_equilibrium<L, FS><<<grid_for(c->sites), kFieldThreads, 0, c->stream>>>(m1, m1 + c->sites, f0, c->sites, st);
     CK(cudaGetLastError());
-    k_moments<L, T><<<grid_for(c->sites), kFieldThreads, 0, c->stream>>>(f0, m0, m1, c->sites);
+    k_moments<L, FS><<<grid_for(c->sites), kFieldThreads, 0, c->stream>>>(f0, m0, m1, c->sites, st);
     CK(cudaGetLastError());
     return MSC_OK;
 }
@@ -425,17 +433,31 @@ int refresh_tables(msc_ctx* c) {
 
 int read_state(msc_ctx* c, DevState* hs);
 
+// Call fn(L{}, T{}, FS{}) for the context's lattice, arithmetic/field type T and population
+// storage type FS (FP16 storage exists for D2Q9 only).
+template <typename Fn>
+int dispatch(const msc_ctx* c, Fn&& fn) {
+    if (c->desc.dim == 2) {
+        if (c->desc.precision == MSC_FP64) return fn(D2Q9{}, double{}, double{});
+        if (c->desc.precision == MSC_FP32) return fn(D2Q9{}, float{}, float{});
+        return fn(D2Q9{}, float{}, __half{});
+    }
+    if (c->desc.precision == MSC_FP64) return fn(D3Q19{}, double{}, double{});
+    return fn(D3Q19{}, float{}, float{});
+}
+#define MSC_TYPES(l, t, s) decltype(l), decltype(t), decltype(s)
+
 // The march of msc_march driven from the host: the same kernels launched one by one, with the
 // acceptance decision read back after every sweep.  For profilers that do not descend into
 // conditional graph nodes, and for debugging.
-template <class L, typename T>
+template <class L, typename T, typename FS>
 int run_stepwise(msc_ctx* c, int n_steps) {
     using C = typename Cplx<T>::type;
     int rc = set_smem_limits<T>(c->desc.dim, c->desc.n);
     if (rc) return rc;
     DevState* st = at<DevState>(c, c->lay.state);
-    T* fbase = at<T>(c, c->lay.fbuf);
-    const size_t fstride = c->lay.fstride / sizeof(T);
+    FS* fbase = at<FS>(c, c->lay.fbuf);
+    const size_t fstride = c->lay.fstride / sizeof(FS);
     double* mbuf = at<double>(c, c->lay.mbuf);
     T* h = at<T>(c, c->lay.h);
     const int fgrid = grid_for(c->sites);
@@ -463,11 +485,11 @@ int run_stepwise(msc_ctx* c, int n_steps) {
     DevState hs;
     for (int step = 0; step < n_steps; ++step) {
         k_step_setup<<<1, 1, 0, c->stream>>>(st, none, 0);
-        k_step_begin<L, T><<<fgrid, kFieldThreads, 0, c->stream>>>(st, fbase, fstride, mbuf, h, c->sites);
+        k_step_begin<L, T, FS><<<fgrid, kFieldThreads, 0, c->stream>>>(st, fbase, fstride, mbuf, h, c->sites);
         for (;;) {
             if (L::D == 2) {
-                Sweep2Args<T> A = sweep2_args_graph<T>(c);
-                k_sweep2<T, false, true><<<sweep2_geometry(c->desc.n).blocks, kSweepWarps * 32, 0, c->stream>>>(A);
+                Sweep2Args<T, FS> A = sweep2_args_graph<T, FS>(c);
+                k_sweep2<T, FS, false, true><<<sweep2_geometry(c->desc.n).blocks, kSweepWarps * 32, 0, c->stream>>>(A);
             } else {
                 Sweep3Args<T> A = sweep3_args_graph<T>(c);
                 k_sweep3<T, false, true><<<A.g.blocks, A.g.threads, A.g.smem, c->stream>>>(A);
@@ -482,7 +504,7 @@ int run_stepwise(msc_ctx* c, int n_steps) {
                 }
             if (hs.accepted || hs.status != MSC_OK) break;
         }
-        k_step_end<L, T><<<fgrid, kFieldThreads, 0, c->stream>>>(st, fbase, fstride, mbuf, h, c->sites);
+        k_step_end<L, T, FS><<<fgrid, kFieldThreads, 0, c->stream>>>(st, fbase, fstride, mbuf, h, c->sites);
         k_step_finish<<<1, 1, 0, c->stream>>>(st, at<int>(c, c->lay.iters), c->desc.max_steps, none, 0);
         CK(cudaGetLastError());
         rc = read_state(c, &hs);
@@ -534,7 +556,7 @@ int msc_create(msc_ctx** out, const msc_lattice_desc* desc, void* ws, size_t byt
     c->Q = lattice_q(desc->dim);
     c->logn = ilog2(desc->n);
     c->sites = desc->dim == 2 ? (size_t)desc->n * desc->n : (size_t)desc->n * desc->n * desc->n;
-    c->elem = desc->precision == MSC_FP64 ? 8 : 4;
+    c->elem = field_elem(desc->precision);
     c->lay = L;
     c->ws = (unsigned char*)ws;
     c->stream = (cudaStream_t)stream;
@@ -545,6 +567,7 @@ int msc_create(msc_ctx** out, const msc_lattice_desc* desc, void* ws, size_t byt
         free(c);
         return MSC_ERR_CUDA;
     }
+    k_reset_history<<<1, 1, 0, c->stream>>>(at<DevState>(c, L.state));  // sigma = 1 until init
     const int n = desc->n;
     if (desc->precision == MSC_FP64)
         k_twiddles<double2><<<(n + 255) / 256, 256, 0, c->stream>>>((double2*)(c->ws + L.tw), n);
@@ -585,7 +608,7 @@ int msc_set_params(msc_ctx* c, const msc_params* p) {
     if (c->params.warm_order == 0)  // FP32 storage: the cubic rule grows rounding in weakly damped modes
         c->params.warm_order = c->desc.precision == MSC_FP64 ? 3 : (c->desc.dim == 2 ? 2 : 1);
     if (c->params.count_multiple == 0)  // FP32 D2Q9: keep the staggered modes' per-step factor positive
-        c->params.count_multiple = c->desc.precision == MSC_FP32 && c->desc.dim == 2 ? 2 : 1;
+        c->params.count_multiple = c->desc.precision != MSC_FP64 && c->desc.dim == 2 ? 2 : 1;
     c->params_set = true;
     k_set_params<<<1, 1, 0, c->stream>>>(at<DevState>(c, c->lay.state), c->params);
     CK(cudaGetLastError());
@@ -594,13 +617,7 @@ int msc_set_params(msc_ctx* c, const msc_params* p) {
 
 int msc_init_fields(msc_ctx* c, const double* p, const double* u, int on_device) {
     if (!c || !p || !u) return MSC_ERR_ARG;
-    int rc;
-    if (c->desc.dim == 2)
-        rc = c->desc.precision == MSC_FP64 ? run_init<D2Q9, double>(c, p, u, on_device)
-                                           : run_init<D2Q9, float>(c, p, u, on_device);
-    else
-        rc = c->desc.precision == MSC_FP64 ? run_init<D3Q19, double>(c, p, u, on_device)
-                                           : run_init<D3Q19, float>(c, p, u, on_device);
+    int rc = dispatch(c, [&](auto l, auto t, auto s) { return run_init<MSC_TYPES(l, t, s)>(c, p, u, on_device); });
     if (rc == MSC_OK) c->fields_set = true;
     return rc;
 }
@@ -609,13 +626,7 @@ int msc_march(msc_ctx* c, int n_steps) {
     if (!c || n_steps < 0) return MSC_ERR_ARG;
     if (!c->params_set || !c->fields_set) return MSC_ERR_STATE;
     if (!c->x_march) {
-        int rc;
-        if (c->desc.dim == 2)
-            rc = c->desc.precision == MSC_FP64 ? build_march_graph<D2Q9, double>(c)
-                                               : build_march_graph<D2Q9, float>(c);
-        else
-            rc = c->desc.precision == MSC_FP64 ? build_march_graph<D3Q19, double>(c)
-                                               : build_march_graph<D3Q19, float>(c);
+        int rc = dispatch(c, [&](auto l, auto t, auto s) { return build_march_graph<MSC_TYPES(l, t, s)>(c); });
         if (rc) return rc;
     }
     if (c->params.replay && n_steps > c->desc.max_steps) return MSC_ERR_ARG;
@@ -633,22 +644,14 @@ int msc_march_stepwise(msc_ctx* c, int n_steps) {
     if (c->params.replay && n_steps > c->desc.max_steps) return MSC_ERR_ARG;
     int rc = refresh_tables(c);
     if (rc) return rc;
-    if (c->desc.dim == 2)
-        return c->desc.precision == MSC_FP64 ? run_stepwise<D2Q9, double>(c, n_steps)
-                                             : run_stepwise<D2Q9, float>(c, n_steps);
-    return c->desc.precision == MSC_FP64 ? run_stepwise<D3Q19, double>(c, n_steps)
-                                         : run_stepwise<D3Q19, float>(c, n_steps);
+    return dispatch(c, [&](auto l, auto t, auto s) { return run_stepwise<MSC_TYPES(l, t, s)>(c, n_steps); });
 }
 
 int msc_explicit_march(msc_ctx* c, int n_steps) {
     if (!c || n_steps < 0) return MSC_ERR_ARG;
     if (!c->fields_set) return MSC_ERR_STATE;
     if (n_steps == 0) return MSC_OK;
-    if (c->desc.dim == 2)
-        return c->desc.precision == MSC_FP64 ? run_explicit<D2Q9, double>(c, n_steps)
-                                             : run_explicit<D2Q9, float>(c, n_steps);
-    return c->desc.precision == MSC_FP64 ? run_explicit<D3Q19, double>(c, n_steps)
-                                         : run_explicit<D3Q19, float>(c, n_steps);
+    return dispatch(c, [&](auto l, auto t, auto s) { return run_explicit<MSC_TYPES(l, t, s)>(c, n_steps); });
 }
 
 int msc_get_stats(msc_ctx* c, msc_stats* out) {
@@ -693,15 +696,20 @@ int msc_read_populations(msc_ctx* c, double* f, int on_device) {
         CK(cudaStreamSynchronize(c->stream));
         return MSC_OK;
     }
-    if (on_device) return MSC_ERR_ARG;  // FP32 storage: host read-back only
-    float* tmp = (float*)malloc(cnt * 4);
+    if (on_device) return MSC_ERR_ARG;  // FP32 / FP16 storage: host read-back only
+    const size_t ep = pop_elem(c->desc.precision);
+    void* tmp = malloc(cnt * ep);
     if (!tmp) return MSC_ERR_ARG;
-    if (cudaMemcpyAsync(tmp, src, cnt * 4, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+    if (cudaMemcpyAsync(tmp, src, cnt * ep, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
         cudaStreamSynchronize(c->stream) != cudaSuccess) {
         free(tmp);
         return MSC_ERR_CUDA;
     }
-    for (size_t i = 0; i < cnt; ++i) f[i] = (double)tmp[i];
+    if (c->desc.precision == MSC_FP32) {
+        for (size_t i = 0; i < cnt; ++i) f[i] = (double)((const float*)tmp)[i];
+    } else {  // FP16: stored f / sigma
+        for (size_t i = 0; i < cnt; ++i) f[i] = s.fscale * (double)__half2float(((const __half*)tmp)[i]);
+    }
     free(tmp);
     return MSC_OK;
 }
@@ -744,8 +752,8 @@ int msc_set_replay_counts(msc_ctx* c, const int* counts, int n) {
     return MSC_OK;
 }
 
-// blob: [magic, dim, n, precision, n_avail, pad] int32 x6, steps_done int64, then n_avail population
-// arrays (storage type, newest first), then m^n and m^{n-1} (double)
+// blob: [magic, dim, n, precision, n_avail, e] int32 x6 (population scale sigma = 2^e), steps_done
+// int64, then n_avail population arrays (storage type, newest first), then m^n and m^{n-1} (double)
 int msc_save_state(msc_ctx* c, void* blob, size_t* bytes) {
     if (!c || !bytes) return MSC_ERR_ARG;
     DevState s;
@@ -759,7 +767,9 @@ int msc_save_state(msc_ctx* c, void* blob, size_t* bytes) {
     }
     if (*bytes < need) return MSC_ERR_ARG;
     unsigned char* b = (unsigned char*)blob;
-    int32_t hdr[6] = {0x4d53434c, c->desc.dim, c->desc.n, c->desc.precision, s.n_avail, 0};
+    int sig_exp = 0;
+    frexp(s.fscale > 0.0 ? s.fscale : 1.0, &sig_exp);
+    int32_t hdr[6] = {0x4d53434c, c->desc.dim, c->desc.n, c->desc.precision, s.n_avail, sig_exp - 1};
     memcpy(b, hdr, 24);
     int64_t sd = s.steps_done;
     memcpy(b + 24, &sd, 8);
@@ -783,7 +793,7 @@ int msc_load_state(msc_ctx* c, const void* blob, size_t bytes) {
     int32_t hdr[6];
     memcpy(hdr, b, 24);
     if (hdr[0] != 0x4d53434c || hdr[1] != c->desc.dim || hdr[2] != c->desc.n || hdr[3] != c->desc.precision ||
-        hdr[4] < 1 || hdr[4] > 3)
+        hdr[4] < 1 || hdr[4] > 3 || hdr[5] < -1000 || hdr[5] > 1000)
         return MSC_ERR_ARG;
     int64_t sd;
     memcpy(&sd, b + 24, 8);
@@ -813,6 +823,7 @@ int msc_load_state(msc_ctx* c, const void* blob, size_t bytes) {
     s.steps_done = sd;
     s.status = MSC_OK;
     s.prepared = 0;
+    s.fscale = ldexp(1.0, hdr[5]);
     CK(cudaMemcpy(c->ws + c->lay.state, &s, sizeof(DevState), cudaMemcpyHostToDevice));
     c->fields_set = true;
     return MSC_OK;
@@ -853,21 +864,22 @@ StageScratch stage_scratch(int dim, int n, int precision, void* base) {
     return s;
 }
 
-template <typename T>
+template <typename T, typename FS = T>
 int stage_sweep(int dim, int n, double a, const void* fin, const void* dm, const void* h, void* fout,
                 void* pr, double* sumsq, void* scratch, cudaStream_t stream) {
     StageScratch S = stage_scratch(dim, n, sizeof(T) == 8 ? MSC_FP64 : MSC_FP32, scratch);
     CK(cudaMemsetAsync(S.counter, 0, 4, stream));
     if (dim == 2) {
-        Sweep2Args<T> A;
+        Sweep2Args<T, FS> A;
         memset(&A, 0, sizeof(A));
         const Sweep2Geom g = sweep2_geometry(n);
-        A.fin = (const T*)fin;
+        A.fin = (const FS*)fin;
         A.dm = (const T*)dm;
         A.h = (const T*)h;
-        A.fout = (T*)fout;
+        A.fout = (FS*)fout;
         A.pr = (T*)pr;
         A.a = a;
+        A.fscale = 1.0;
         A.lift = dm != nullptr;
         A.sumsq_out = sumsq;
         A.partial = S.partial;
@@ -876,8 +888,8 @@ int stage_sweep(int dim, int n, double a, const void* fin, const void* dm, const
         A.nstrips = g.nstrips;
         A.hb = g.hb;
         A.nrowblk = g.nrowblk;
-        k_sweep2<T, false, false><<<g.blocks, kSweepWarps * 32, 0, stream>>>(A);
-    } else {
+        k_sweep2<T, FS, false, false><<<g.blocks, kSweepWarps * 32, 0, stream>>>(A);
+    } else if constexpr (std::is_same<T, FS>::value) {
         if (set_sweep3_smem_limits<T>(n) != 0) return MSC_ERR_CUDA;
         Sweep3Args<T> A;
         memset(&A, 0, sizeof(A));
@@ -944,6 +956,9 @@ int msc_sweep(int dim, int n, int precision, double a, const void* f_in, const v
         return MSC_ERR_ARG;
     if (precision == MSC_FP64)
         return stage_sweep<double>(dim, n, a, f_in, dm, h, f_out, pr_out, sumsq_out, scratch, (cudaStream_t)stream);
+    if (precision == MSC_FP16)
+        return stage_sweep<float, __half>(dim, n, a, f_in, dm, h, f_out, pr_out, sumsq_out, scratch,
+                                          (cudaStream_t)stream);
     return stage_sweep<float>(dim, n, a, f_in, dm, h, f_out, pr_out, sumsq_out, scratch, (cudaStream_t)stream);
 }
 
@@ -965,6 +980,8 @@ int msc_equilibrium(int dim, int n, int precision, const double* p, const double
     if (dim == 2) {
         if (precision == MSC_FP64)
             k_equilibrium<D2Q9, double><<<grid_for(sites), kFieldThreads, 0, s>>>(p, u, (double*)f_out, sites);
+        else if (precision == MSC_FP16)
+            k_equilibrium<D2Q9, __half><<<grid_for(sites), kFieldThreads, 0, s>>>(p, u, (__half*)f_out, sites);
         else
             k_equilibrium<D2Q9, float><<<grid_for(sites), kFieldThreads, 0, s>>>(p, u, (float*)f_out, sites);
     } else {

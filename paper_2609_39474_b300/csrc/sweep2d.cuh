@@ -20,15 +20,16 @@ namespace msc {
 constexpr int kSweepWarps = 4;          // warps (strips) per block
 constexpr int kStripOut = 30;           // output columns per warp strip
 
-template <typename T>
+template <typename T, typename S = T>  // T: arithmetic and field type, S: population storage
 struct Sweep2Args {
     // stateless mode: explicit pointers; graph mode: pointers resolved from the device state
-    const T* fin;
+    const S* fin;
     const T* dm;
     const T* h;
-    T* fout;
+    S* fout;
     T* pr;
     double a;
+    double fscale;  // stateless mode: population storage scale (FP16 storage holds f / fscale)
     int lift;
     double* sumsq_out;
     // reduction scratch
@@ -38,7 +39,7 @@ struct Sweep2Args {
     int n, nstrips, hb, nrowblk;
     // graph mode
     DevState* st;
-    T* fbase;
+    S* fbase;
     size_t fstride;  // elements
     double* hist;
     int hist_cap;
@@ -94,9 +95,10 @@ __device__ inline void march_after_sweep(DevState* st, double total, double qsit
 
 // One warp unit of the sweep: output columns [strip*30, strip*30 + 30) of rows [rb*hb, rb*hb + hb).
 // Returns this lane's share of sum r^2 (zero in EXPLICIT mode).  Called by all 32 lanes.
-template <typename T, bool EXPLICIT>
-__device__ __forceinline__ double sweep2_unit(const T* fin, const T* dm, const T* hh, T* fout, T* pr, T a, T inv,
-                                              int lift, int n, int hb, int strip, int rb, int lane) {
+template <typename T, typename S, bool EXPLICIT>
+__device__ __forceinline__ double sweep2_unit(const S* fin, const T* dm, const T* hh, S* fout, T* pr, T a, T inv,
+                                              int lift, int n, int hb, int strip, int rb, int lane,
+                                              T sig = T(1), T isig = T(1)) {
     using L = D2Q9;
     const int nmask = n - 1;
     const size_t NN = (size_t)n * n;
@@ -116,7 +118,7 @@ __device__ __forceinline__ double sweep2_unit(const T* fin, const T* dm, const T
     auto load_row = [&](int jr) {
         const size_t id = (size_t)(jr & nmask) * n + x;
 #pragma unroll
-        for (int k = 0; k < 9; ++k) nf[k] = fin[k * NN + id];
+        for (int k = 0; k < 9; ++k) nf[k] = ld_pop<T, S>(fin, k * NN + id, sig);
         if (!EXPLICIT) {
             if (lift) { ndp = dm[id]; ndx = dm[NN + id]; ndy = dm[2 * NN + id]; }
             nh0 = hh[id]; nh1 = hh[NN + id]; nh2 = hh[2 * NN + id];
@@ -175,7 +177,7 @@ __device__ __forceinline__ double sweep2_unit(const T* fin, const T* dm, const T
         if (j - 1 >= y0 && out_lane) {
             const size_t oidx = (size_t)((j - 1) & nmask) * n + x;
 #pragma unroll
-            for (int k = 0; k < 9; ++k) fout[k * NN + oidx] = Ar[k];
+            for (int k = 0; k < 9; ++k) st_pop<T, S>(fout, k * NN + oidx, Ar[k], isig);
             if (!EXPLICIT) {
                 T r0 = T(0), r1 = T(0), r2 = T(0), rr = T(0);
 #pragma unroll
@@ -205,23 +207,25 @@ __device__ __forceinline__ double sweep2_unit(const T* fin, const T* dm, const T
     return ssq;
 }
 
-template <typename T, bool EXPLICIT, bool GRAPH>
-__global__ void __launch_bounds__(kSweepWarps * 32) k_sweep2(Sweep2Args<T> A) {
+template <typename T, typename S, bool EXPLICIT, bool GRAPH>
+__global__ void __launch_bounds__(kSweepWarps * 32) k_sweep2(Sweep2Args<T, S> A) {
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int n = A.n;
     const size_t NN = (size_t)n * n;
 
-    const T* fin = A.fin;
+    const S* fin = A.fin;
     const T* dm = A.dm;
     const T* hh = A.h;
-    T* fout = A.fout;
+    S* fout = A.fout;
     T* pr = A.pr;
     T a = (T)A.a;
     T inv = (T)(1.0 / (1.0 + A.a / 2.0));
     int lift = A.lift;
+    double fs = A.fscale;
     if (GRAPH) {
         const volatile DevState* vs = A.st;
+        if constexpr (!std::is_same<S, T>::value) fs = vs->fscale;
         if (EXPLICIT) {
             const int sa = vs->ex_a, sb = vs->ex_b;
             fin = A.fbase + (size_t)(A.ex_dir ? sb : sa) * A.fstride;
@@ -245,8 +249,8 @@ __global__ void __launch_bounds__(kSweepWarps * 32) k_sweep2(Sweep2Args<T> A) {
     const int unit = blockIdx.x * kSweepWarps + warp;
     double ssq = 0.0;
     if (unit < A.nstrips * A.nrowblk)  // warp-uniform
-        ssq = sweep2_unit<T, EXPLICIT>(fin, dm, hh, fout, pr, a, inv, lift, n, A.hb, unit % A.nstrips,
-                                       unit / A.nstrips, lane);
+        ssq = sweep2_unit<T, S, EXPLICIT>(fin, dm, hh, fout, pr, a, inv, lift, n, A.hb, unit % A.nstrips,
+                                          unit / A.nstrips, lane, (T)fs, (T)(1.0 / fs));
     if (EXPLICIT) return;
 
     // ---- residual norm: block partials, last block reduces in a fixed order ----

@@ -66,6 +66,7 @@ int sweep2_noalloc(int n, double a, const void* fin, const void* dm, const void*
     A.fout = (T*)fout;
     A.pr = (T*)pr;
     A.a = a;
+    A.fscale = 1.0;
     A.lift = dm != nullptr;
     A.sumsq_out = sumsq;
     A.partial = reinterpret_cast<double*>(static_cast<unsigned char*>(base) + 256);
@@ -74,7 +75,7 @@ int sweep2_noalloc(int n, double a, const void* fin, const void* dm, const void*
     A.nstrips = g.nstrips;
     A.hb = g.hb;
     A.nrowblk = g.nrowblk;
-    k_sweep2<T, false, false><<<g.blocks, kSweepWarps * 32, 0, stream>>>(A);
+    k_sweep2<T, T, false, false><<<g.blocks, kSweepWarps * 32, 0, stream>>>(A);
     return cudaGetLastError() == cudaSuccess ? MSC_OK : MSC_ERR_CUDA;
 }
 
@@ -83,8 +84,8 @@ int sweep2_noalloc(int n, double a, const void* fin, const void* dm, const void*
 extern "C" int msc_sweep_d2q9_noalloc(int n, int precision, double a, const void* f_in, const void* dm,
                                       const void* h, void* f_out, void* pr_out, double* sumsq_out,
                                       void* stream) {
-    if (!msc::valid_lattice(2, n, precision) || !f_in || !h || !f_out || !pr_out || !sumsq_out ||
-        f_in == f_out || !(a >= 0.0))
+    if (!msc::valid_lattice(2, n, precision) || precision == MSC_FP16 || !f_in || !h || !f_out || !pr_out ||
+        !sumsq_out || f_in == f_out || !(a >= 0.0))
         return MSC_ERR_ARG;
     if (precision == MSC_FP64)
         return msc::sweep2_noalloc<double>(n, a, f_in, dm, h, f_out, pr_out, sumsq_out, (cudaStream_t)stream);

@@ -11,7 +11,9 @@ import torch
 
 from . import _lib as L
 
-_DT = {"fp64": (L.MSC_FP64, torch.float64), "fp32": (L.MSC_FP32, torch.float32)}
+# precision -> (code, population storage dtype, working-field dtype)
+_DT = {"fp64": (L.MSC_FP64, torch.float64, torch.float64), "fp32": (L.MSC_FP32, torch.float32, torch.float32),
+       "fp16": (L.MSC_FP16, torch.float16, torch.float32)}
 
 
 def _ptr(t: torch.Tensor) -> int:
@@ -28,7 +30,13 @@ def precision_code(precision: str) -> int:
 
 
 def storage_dtype(precision: str) -> torch.dtype:
+    """dtype of stored populations (FP16 storage: float16)."""
     return _DT[precision][1]
+
+
+def field_dtype(precision: str) -> torch.dtype:
+    """dtype of the working fields h, P r, dm (float32 for FP16 population storage)."""
+    return _DT[precision][2]
 
 
 class MscLattice:
@@ -234,13 +242,13 @@ class StageScratch:
 def sweep(dim: int, n: int, precision: str, a: float, f_in: torch.Tensor, h: torch.Tensor,
           dm: torch.Tensor = None, scratch: StageScratch = None, stream=None):
     """One fused sweep through msc_sweep: returns (f_out, P r, sum r^2 as a device double)."""
-    dt = storage_dtype(precision)
-    for t in (f_in, h) + ((dm,) if dm is not None else ()):
-        if t.dtype != dt or not t.is_cuda or not t.is_contiguous():
-            raise ValueError("stage inputs must be contiguous device tensors of the storage type")
+    dt, ft = storage_dtype(precision), field_dtype(precision)
+    for t, want in ((f_in, dt), (h, ft)) + (((dm, ft),) if dm is not None else ()):
+        if t.dtype != want or not t.is_cuda or not t.is_contiguous():
+            raise ValueError("stage inputs must be contiguous device tensors of the storage / field type")
     scratch = scratch or StageScratch(dim, n, precision, f_in.device)
     f_out = torch.empty_like(f_in)
-    pr = torch.empty((dim + 1,) + (n,) * dim, dtype=dt, device=f_in.device)
+    pr = torch.empty((dim + 1,) + (n,) * dim, dtype=ft, device=f_in.device)
     ssq = torch.empty((), dtype=torch.float64, device=f_in.device)
     L.check(L.lib.msc_sweep(dim, n, precision_code(precision), float(a), _ptr(f_in),
                             _ptr(dm) if dm is not None else None, _ptr(h), _ptr(f_out), _ptr(pr), _ptr(ssq),

@@ -43,6 +43,7 @@ KMAX = 300
 # candidate the reference arm uses (the matched-gate winner of the GPU candidate search at N = 1024)
 DEFAULT_CANDIDATE = {1024: (64, 1e-8), 256: (32, 1e-8)}
 SWEEP_BYTES_PER_SITE_FP32 = 2 * 9 * 4 + 3 * 4 + 3 * 4 + 3 * 4  # f in/out, h, lifted dm, P r
+SWEEP_BYTES_PER_SITE_FP16 = 2 * 9 * 2 + 3 * 4 + 3 * 4 + 3 * 4  # binary16 f in/out, FP32 h, dm, P r
 ROOF_N = 4096  # out-of-L2 size for the sweep roofline (16.7 M sites, 1.8 GB per sweep)
 
 
@@ -120,8 +121,12 @@ class ClockSampler:
 # our arm: the CUDA library through its Python binding
 # ---------------------------------------------------------------------------------------------------
 
-def measure_workload(torch, PL, dev, dim, n, steps, warmup, dist=None, full=False):
-    """Explicit baseline, candidate search, timed MSC marches (and, for the headline, e2e)."""
+def measure_workload(torch, PL, dev, dim, n, steps, warmup, dist=None, full=False, precision="fp32",
+                     explicit_ref=None):
+    """Explicit baseline, candidate search, timed MSC marches (and, for the headline, e2e).
+
+    explicit_ref: (t_explicit_ms, e_explicit) of another storage precision's explicit run to use as
+    the baseline (FP16 storage is compared with the FP32 explicit LBM, whose accuracy it must match)."""
     w = WORKLOADS[(dim, n)]
     p, u, t_end, u_ref = workload(n, dim)
     p_d = torch.as_tensor(p, device=dev).contiguous()
@@ -132,7 +137,7 @@ def measure_workload(torch, PL, dev, dim, n, steps, warmup, dist=None, full=Fals
     def ev():
         return torch.cuda.Event(enable_timing=True)
 
-    L = PL.MscLattice(dim, n, "fp32", max_steps=4096, hist_cap=1 << 16, device=str(dev))
+    L = PL.MscLattice(dim, n, precision, max_steps=4096, hist_cap=1 << 16, device=str(dev))
 
     # -- explicit LBM baseline: graph-captured, same kernels with no source (Section 4.1) --------
     def explicit_once():
@@ -150,6 +155,9 @@ def measure_workload(torch, PL, dev, dim, n, steps, warmup, dist=None, full=Fals
     t_ex = min(explicit_once() for _ in range(2))
     u_ex = L.fields()[1].cpu().numpy()
     e_ex = velocity_error(u_ex, u_ref)
+    t_ex_own, e_ex_own = t_ex, e_ex
+    if explicit_ref is not None:
+        t_ex, e_ex = explicit_ref
 
     # -- candidate matrix (Table protocol), untimed selection ------------------------------------
     def msc_once(S, eps):
@@ -221,7 +229,9 @@ def measure_workload(torch, PL, dev, dim, n, steps, warmup, dist=None, full=Fals
             "rho_obs_steps": len(rho), "final_residual": per_step[-1][-1] if per_step else None}
     s_1pct = t_ex / min(msc_once(best1["S"], best1["eps"])[0] for _ in range(3)) if best1 else None
     res = {
-        "workload": f"{'D2Q9' if dim == 2 else 'D3Q19'} periodic N={n} Re=1 random-phase seed {w['seed']} FP32",
+        "workload": f"{'D2Q9' if dim == 2 else 'D3Q19'} periodic N={n} Re=1 random-phase seed {w['seed']} "
+                    f"{precision.upper()} storage",
+        "t_explicit_own_ms": t_ex_own, "e_explicit_own": e_ex_own,
         "s_wall_matched": t_ex / ms_step, "s_wall_1pct": s_1pct, "t_explicit_ms": t_ex, "ms_per_step": ms_step,
         "inner_mlups": n ** dim * statistics.mean(inner) / (ms_step * 1e3),
         "inner_iters_per_step": statistics.mean(inner) / S, "candidate": best, "candidate_1pct": best1,
@@ -285,7 +295,7 @@ def start_batch_references():
     """NS references of the batch instances in a spawn pool (CPU), overlapping the GPU work."""
     import multiprocessing
     ctx = multiprocessing.get_context("spawn")
-    pool = ctx.Pool(max(1, min(16, (os.cpu_count() or 2) - 1)))
+    pool = ctx.Pool(max(1, min(12, (os.cpu_count() or 4) - 2)))
     jobs = [(d["n"], d["Re"], d["seed"], d["t_end"]) for d in batch_instances()]
     return pool, pool.map_async(_batch_reference, jobs)
 
@@ -427,6 +437,28 @@ def measure_batch(torch, PL, dev, refs_async=None, reps=3):
     return res
 
 
+def batch_stage(torch, PL, dev, args):
+    """The batched kernels of the 48-instance sweep, one family at a time (msc_batch_time_stage)."""
+    lats = []
+    for d in batch_instances():
+        p, u = random_phase(d["n"], 2, d["Re"], seed=d["seed"], kmax=8)
+        L = PL.MscLattice(2, d["n"], "fp32", max_steps=64, hist_cap=64, device=str(dev))
+        L.set_params(dt=d["t_end"] / 16, eps=1e-6)
+        L.init_fields(p, u)
+        lats.append(L)
+    B = PL.MscBatch(lats)
+    if args.tuning:
+        B.set_tuning(json.loads(args.tuning))
+    else:
+        B.autotune(reps=5)
+    sites = sum(d["n"] ** 2 for d in batch_instances())
+    out = {"tuning": B.tuning, "sites": sites}
+    for which in ("sweep", "rowfft", "colsolve"):
+        out[which + "_us"] = B.time_stage(which, reps=max(1, args.steps))
+    out["sweep_gbs"] = SWEEP_BYTES_PER_SITE_FP32 * sites / (out["sweep_us"] * 1e3)
+    return out
+
+
 def run_ours(args, rank, world, dist):
     import torch
     from paper_2609_39474_b300 import lattice as PL
@@ -435,13 +467,24 @@ def run_ours(args, rank, world, dist):
     torch.cuda.set_device(dev)
     batch_refs = None
     if not args.no_batch:
-        batch_refs = start_batch_references()
+        # the continuum references of the batch run on the host cores before any timed region, so that
+        # they do not compete with the host side of the timed (and end-to-end) measurements
+        pool, refs = start_batch_references()
+        refs.wait()
+        batch_refs = (pool, refs)
     res = measure_workload(torch, PL, dev, 2, args.n, args.steps, args.warmup, dist, full=True)
     # roofline of the dominant kernel (the fused sweep) at an out-of-L2 size, and at the bench size
     res["roofline"] = sweep_roofline(torch, PL, dev)
     res["sweep_at_n"] = sweep_time(torch, PL, dev, args.n, reps=50)
     res["secondary"] = []
+    res["fp16"] = None
     if not args.no_secondary:
+        # FP16 population storage on the headline workload, against the FP32 explicit baseline
+        f16 = measure_workload(torch, PL, dev, 2, args.n, max(3, min(args.steps, 10)), 3, dist, full=False,
+                               precision="fp16", explicit_ref=(res["t_explicit_ms"], res["e_explicit"]))
+        f16.pop("clocks", None)
+        f16["sweep_roofline_n4096"] = sweep_time(torch, PL, dev, ROOF_N, reps=20, precision="fp16")
+        res["fp16"] = f16
         for dim, n in ((2, 256), (3, 128)):
             if (dim, n) != (2, args.n):
                 sec = measure_workload(torch, PL, dev, dim, n, max(3, min(args.steps, 10)), 3, dist, full=False)
@@ -461,7 +504,9 @@ def run_phase(args):
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     if args.phase == "sweep":
-        return {"phase": "sweep", **sweep_time(torch, PL, dev, ROOF_N, reps=args.steps)}
+        return {"phase": "sweep", **sweep_time(torch, PL, dev, ROOF_N, reps=args.steps, precision=args.precision)}
+    if args.phase == "batch-stage":
+        return {"phase": "batch-stage", **batch_stage(torch, PL, dev, args)}
     if args.phase == "batch":
         return {"phase": "batch", **measure_batch(torch, PL, dev)}
     n = args.n
@@ -490,24 +535,27 @@ def run_phase(args):
             "status": st["status"]}
 
 
-def sweep_time(torch, PL, dev, n, reps=20):
-    """Mean duration (ms) of the fused FP32 sweep with the lift, CUDA events on its stream."""
+def sweep_time(torch, PL, dev, n, reps=20, precision="fp32"):
+    """Mean duration (ms) of the fused sweep with the lift, CUDA events on its stream."""
     sites = n * n
-    f = torch.randn((9, n, n), device=dev, dtype=torch.float32) * 1e-3
-    h = torch.randn((3, n, n), device=dev, dtype=torch.float32) * 1e-4
-    dm = torch.randn((3, n, n), device=dev, dtype=torch.float32) * 1e-5
-    sc = PL.StageScratch(2, n, "fp32", dev)
+    pt, ft = PL.storage_dtype(precision), PL.field_dtype(precision)
+    scale = 0.5 if precision == "fp16" else 1e-3  # FP16 storage holds O(1) scaled values
+    f = (torch.randn((9, n, n), device=dev, dtype=torch.float32) * scale).to(pt)
+    h = torch.randn((3, n, n), device=dev, dtype=ft) * 1e-4
+    dm = torch.randn((3, n, n), device=dev, dtype=ft) * 1e-5
+    sc = PL.StageScratch(2, n, precision, dev)
     for _ in range(3):
-        PL.sweep(2, n, "fp32", 0.01, f, h, dm, sc)
+        PL.sweep(2, n, precision, 0.01, f, h, dm, sc)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(reps):
-        PL.sweep(2, n, "fp32", 0.01, f, h, dm, sc)
+        PL.sweep(2, n, precision, 0.01, f, h, dm, sc)
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / reps
-    return {"n": n, "ms": ms, "gbs": SWEEP_BYTES_PER_SITE_FP32 * sites / (ms * 1e6)}
+    bps = SWEEP_BYTES_PER_SITE_FP16 if precision == "fp16" else SWEEP_BYTES_PER_SITE_FP32
+    return {"n": n, "ms": ms, "gbs": bps * sites / (ms * 1e6), "bytes_per_site": bps, "precision": precision}
 
 
 def sweep_roofline(torch, PL, dev):
@@ -600,18 +648,24 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-secondary", action="store_true", help="skip the N=256 and D3Q19 N=128 workloads")
     ap.add_argument("--no-batch", action="store_true", help="skip the 48-instance batched sweep")
-    ap.add_argument("--phase", default="all", choices=["all", "msc", "msc-stepwise", "sweep", "batch"],
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16"], help="storage of --phase sweep")
+    ap.add_argument("--tuning", default=None,
+                    help="--phase batch-stage: a batch tiling as JSON (keys sweep_rows, fft_rows, col_lines, "
+                         "sweep_ctas_per_sm) instead of autotuning, so that only the timed launches run")
+    ap.add_argument("--phase", default="all",
+                    choices=["all", "msc", "msc-stepwise", "sweep", "batch", "batch-stage"],
                     help="profiling aids: 'msc' runs only the timed MSC marches of the default candidate, "
                          "'msc-stepwise' the same marches driven from the host (one launch per kernel, "
                          "visible to ncu), 'sweep' only the fused-sweep roofline loop, 'batch' only the "
-                         "48-instance batched parameter sweep")
+                         "48-instance batched parameter sweep, 'batch-stage' the batch's kernels timed one "
+                         "family at a time (stateless, visible to ncu)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
 
@@ -681,6 +735,7 @@ def main():
         "candidates": res["candidates"],
         "secondary": res["secondary"],
         "batch": res["batch"],
+        "fp16": res["fp16"],
     }
     print(json.dumps(line))
     if dist is not None:

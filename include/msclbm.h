@@ -301,6 +301,12 @@ int msc_batch_autotune(msc_batch* b, int reps, msc_batch_tuning* out);
 int msc_batch_get_tuning(msc_batch* b, msc_batch_tuning* out);
 /* Install a tiling (validated as described above; MSC_ERR_ARG otherwise, batch unchanged). */
 int msc_batch_set_tuning(msc_batch* b, const msc_batch_tuning* t);
+/* Time one batched kernel family with the current tiling, as the autotuner does (stateless: reads
+   each instance's accepted populations, writes only working arrays that a march rewrites before
+   reading): which = 0 the persistent sweep over every instance, 1 the forward + inverse row
+   transforms, 2 the column solve.  Best of `reps` launches after one warm-up launch, in
+   microseconds, into *us.  Synchronises the stream. */
+int msc_batch_time_stage(msc_batch* b, int which, int reps, float* us);
 
 #ifdef __cplusplus
 }

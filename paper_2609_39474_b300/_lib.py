@@ -98,6 +98,7 @@ _SIG = {
     "msc_batch_autotune": (_i, [_vp, _i, ctypes.POINTER(BatchTuning)]),
     "msc_batch_get_tuning": (_i, [_vp, ctypes.POINTER(BatchTuning)]),
     "msc_batch_set_tuning": (_i, [_vp, ctypes.POINTER(BatchTuning)]),
+    "msc_batch_time_stage": (_i, [_vp, _i, _i, ctypes.POINTER(ctypes.c_float)]),
 }
 for _name, (_res, _args) in _SIG.items():
     _fn = getattr(lib, _name)

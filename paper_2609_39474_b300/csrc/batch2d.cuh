@@ -125,30 +125,31 @@ __global__ void __launch_bounds__(kSweepWarps * 32) k_bsweep2(const BInst<T>* __
         }
         double ssq = sweep2_unit<T, T, MODE == 2>(fin, A.dm, A.h, fout, A.pr, a, inv, lift, A.n, A.hb,
                                                lu % A.nstrips, lu / A.nstrips, lane);
-        if (MODE == 2) continue;
+        if constexpr (MODE != 2) {  // residual norm of the instance (not for the explicit step)
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) ssq += __shfl_xor_sync(0xffffffffu, ssq, off);
-        unsigned int last = 0;
-        if (lane == 0) {
-            B.upart[lu] = ssq;
+            for (int off = 16; off > 0; off >>= 1) ssq += __shfl_xor_sync(0xffffffffu, ssq, off);
+            unsigned int last = 0;
+            if (lane == 0) {
+                B.upart[lu] = ssq;
+                __threadfence();
+                last = atomicAdd(B.ucount, 1u) == (unsigned int)(B.units - 1);
+            }
+            last = __shfl_sync(0xffffffffu, last, 0);
+            if (!last) continue;
+            // the last unit of instance i: every partial of the sweep is visible, sum in a fixed order
             __threadfence();
-            last = atomicAdd(B.ucount, 1u) == (unsigned int)(B.units - 1);
-        }
-        last = __shfl_sync(0xffffffffu, last, 0);
-        if (!last) continue;
-        // the last unit of instance i: every partial of the sweep is visible, sum in a fixed order
-        __threadfence();
-        double s = 0.0;
-        for (int k = lane; k < B.units; k += 32) s += __ldcg(B.upart + k);
+            double s = 0.0;
+            for (int k = lane; k < B.units; k += 32) s += __ldcg(B.upart + k);
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-        if (lane == 0) {
-            *B.ucount = 0u;
-            if (MODE == 0)
-                march_after_sweep(B.st, s, 9.0 * (double)B.sites, A.hist, A.hist_cap, A.replay_counts, A.max_steps,
-                                  0, 0, 0);
-            else
-                *B.t_sumsq = s;
+            for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+            if (lane == 0) {
+                *B.ucount = 0u;
+                if (MODE == 0)
+                    march_after_sweep(B.st, s, 9.0 * (double)B.sites, A.hist, A.hist_cap, A.replay_counts, A.max_steps,
+                                      0, 0, 0);
+                else
+                    *B.t_sumsq = s;
+            }
         }
     }
 }

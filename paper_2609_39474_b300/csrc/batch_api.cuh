@@ -333,10 +333,9 @@ float time_batch_kernel(msc_batch* b, BatchTimer& tm, int which, int reps) {
     return best;
 }
 
-template <typename T>
-int autotune_batch(msc_batch* b, int reps) {
-    // tuning sweeps read each instance's accepted populations and write a free ring slot
-    int slots[kBatchMax][2];
+// per instance the (input, output) ring slots of a stateless sweep: the accepted populations and
+// a slot outside the history
+int tuning_slots(msc_batch* b, int (*slots)[2]) {
     for (int i = 0; i < b->n_inst; ++i) {
         DevState hs;
         int rc = read_state(b->ctx[i], &hs);
@@ -350,6 +349,15 @@ int autotune_batch(msc_batch* b, int reps) {
         }
         if (slots[i][0] < 0 || slots[i][0] >= kNumFBuf || slots[i][1] < 0) return MSC_ERR_STATE;
     }
+    return MSC_OK;
+}
+
+template <typename T>
+int autotune_batch(msc_batch* b, int reps) {
+    // tuning sweeps read each instance's accepted populations and write a free ring slot
+    int slots[kBatchMax][2];
+    int rc0 = tuning_slots(b, slots);
+    if (rc0) return rc0;
     BatchTimer tm;
     if (!tm.ok) return MSC_ERR_CUDA;
     msc_batch_tuning& t = b->tun;
@@ -377,11 +385,9 @@ int autotune_batch(msc_batch* b, int reps) {
         int occ = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bsweep2<T, 0>, kSweepWarps * 32, 0) != cudaSuccess)
             return MSC_ERR_CUDA;
-        const int cands[] = {1, 2, 3, 4, 6, 8, 12, 16};
         int best_k = t.sweep_ctas_per_sm;
         float best = 1e30f;
-        for (int k : cands) {
-            if (k > occ) continue;
+        for (int k = 1; k <= occ && k <= 16; ++k) {
             t.sweep_ctas_per_sm = k;
             if ((rc = measure(0, &cur))) return rc;
             if (cur < best) { best = cur; best_k = k; }
@@ -555,6 +561,20 @@ int msc_batch_set_tuning(msc_batch* b, const msc_batch_tuning* t) {
     b->tun = *t;
     drop_batch_graphs(b);
     return batch_upload(b);
+}
+
+int msc_batch_time_stage(msc_batch* b, int which, int reps, float* us) {
+    if (!b || !us || reps < 1 || which < 0 || which > 2) return MSC_ERR_ARG;
+    int slots[kBatchMax][2];
+    int rc = tuning_slots(b, slots);
+    if (rc) return rc;
+    rc = batch_upload(b, slots);
+    if (rc) return rc;
+    BatchTimer tm;
+    if (!tm.ok) return MSC_ERR_CUDA;
+    *us = b->precision == MSC_FP64 ? time_batch_kernel<double>(b, tm, which, reps)
+                                   : time_batch_kernel<float>(b, tm, which, reps);
+    return *us < 0.f ? MSC_ERR_CUDA : MSC_OK;
 }
 
 int msc_batch_autotune(msc_batch* b, int reps, msc_batch_tuning* out) {

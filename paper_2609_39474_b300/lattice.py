@@ -221,6 +221,13 @@ class MscBatch:
         L.check(L.lib.msc_batch_get_tuning(self._b, ctypes.byref(t)), "msc_batch_get_tuning")
         return self._tuning_dict(t)
 
+    def time_stage(self, which: str, reps: int = 10) -> float:
+        """Best-of-reps microseconds of one batched kernel family ('sweep', 'rowfft', 'colsolve')."""
+        us = ctypes.c_float()
+        code = {"sweep": 0, "rowfft": 1, "colsolve": 2}[which]
+        L.check(L.lib.msc_batch_time_stage(self._b, code, int(reps), ctypes.byref(us)), "msc_batch_time_stage")
+        return us.value
+
     def set_tuning(self, tun: dict):
         t = L.BatchTuning()
         L.check(L.lib.msc_batch_get_tuning(self._b, ctypes.byref(t)), "msc_batch_get_tuning")

@@ -50,6 +50,9 @@ class MarchParams:
                               # 1 (f^n) and 2 (2f^n - f^{n-1}) truncate it
     count_multiple: int = 1   # accept only at inner counts that are multiples of this (1: Algorithm 1;
                               # 2: sweeps in pairs, for reduced-precision storage)
+    force: Optional[tuple] = None  # uniform body force F (d components); the paper has none.  Read as
+                              # an addition to the momentum source, s_u = h_u - a u + F, which is the
+                              # same as adding (0, F) to h in both the reconstruction and the source
 
 
 @dataclass
@@ -101,11 +104,22 @@ def warm_start(f_hist: list, order: int = 3) -> np.ndarray:
     return 3.0 * f_hist[0] - 3.0 * f_hist[1] + f_hist[2]
 
 
+def forced_history(lat: Lattice, h: np.ndarray, force) -> np.ndarray:
+    """h + (0, F): the body force enters wherever the BDF history term does."""
+    if force is None:
+        return h
+    h = h.copy()
+    for al in range(lat.d):
+        h[1 + al] += force[al]
+    return h
+
+
 def physical_step(st: DualTimeState, prm: MarchParams, replay_count: Optional[int] = None) -> StepRecord:
     """One physical step of Algorithm 1 (corrector on) or plain Picard (corrector off)."""
     lat = st.lat
     q = 1 if st.steps_done == 0 else 2
     a, h = bdf_coefficients(q, prm.dt, st.m_n, st.m_nm1)
+    h = forced_history(lat, h, prm.force)
     f = warm_start(st.f_hist, prm.warm_order)
     res = []
     for ell in range(1, prm.kmax + 1):

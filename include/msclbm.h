@@ -98,6 +98,10 @@ typedef struct {
                        so an odd count leaves them with a negative per-step factor that a warm
                        start extrapolation amplifies; even counts keep the factor positive.
                        0 = default: 2 for FP32 storage on D2Q9, else 1. */
+    double force[3]; /* uniform body force F (d components used; the paper has none): added to the
+                       momentum source, s_u = h_u - a u + F, i.e. (0, F) joins h_q in both the
+                       reconstruction (Eq. macro-reconstruct) and the source (Eq. source-moments).
+                       Zero reproduces the paper's march. */
 } msc_params;
 
 typedef struct {
@@ -232,6 +236,44 @@ int msc_equilibrium(int dim, int n, int precision, const double* p_hat, const do
    serialise them. */
 int msc_sweep_d2q9_noalloc(int n, int precision, double a, const void* f_in, const void* dm,
                            const void* h, void* f_out, void* pr_out, double* sumsq_out, void* stream);
+
+/* ---------------------------------------------------------------------------------------------
+ * Discrete adjoint (D2Q9).  The accepted state of each physical step is the fixed point
+ * f^{n+1} = T(f^{n+1}; h^n) (Eqs. fixed-point-problem, sweep) with h^n = h_q(m^n, m^{n-1}) +
+ * (0, F) (Eq. bdf2 plus the body force of msc_params) and m^{n+1} = R(f^{n+1}; h^n)
+ * (Eq. macro-reconstruct); the warm start only picks the first iterate.  A loss of the final fields
+ * is differentiated step by step, last step first, by implicit differentiation of each fixed
+ * point: (I - dT/df)^T lambda = P^T mu / (1 + a/2) with mu = dL/dm^{n+1}, then
+ * dL/dh^n = (dT/dh)^T lambda + mu / (2 (1 + a/2)), passed to m^n, m^{n-1} through h^n and to F.
+ * At the operating point lambda = P^T theta with a three-field unknown theta, iterated with the
+ * transposed shadow correction (the per-wavevector factor (H(k)^H)^{-1} inside the mask).
+ * Since m^0 = P f_eq(p_hat_0, u_0) = (p_hat_0, u_0), dL/dm^0 is the gradient with respect to the
+ * initial fields.
+ * ------------------------------------------------------------------------------------------- */
+typedef struct {
+    int iters;       /* transposed iterations run */
+    int status;      /* MSC_OK, MSC_ERR_NONCONVERGED or MSC_ERR_NONFINITE */
+    double residual; /* final RMS of the reduced adjoint residual relative to RMS(mu / (1 + a/2)) */
+} msc_adjoint_stats;
+
+/* Adjoint of physical step n -> n+1 (q = 1 for the first step of a march, else 2), with the
+   context's dt, nu and force.  All arrays are device double, (d+1) x sites each, layout of
+   msc_read_fields (p_hat first): m_new = m^{n+1}, m_cur = m^n, m_prev = m^{n-1} (unused, may be
+   NULL, when q = 1) are the forward moments; abar_new = dL/dm^{n+1} (complete: every later step
+   already processed); abar_cur += c1 dL/dh^n and abar_prev -= c2 dL/dh^n (abar_prev unused when
+   q = 1); dforce[0..d-1] += the velocity parts of dL/dh^n summed over sites.  Stops when the
+   relative residual falls below eps (> 0) or after kmax iterations (MSC_ERR_NONCONVERGED: the
+   accumulators are then left untouched).  Uses the context's working arrays as scratch: the forward
+   state is undefined afterwards, so load a state (msc_load_state / msc_load_state_device) before
+   the next march.  Synchronises the stream once per iteration.  `out` may be NULL. */
+int msc_adjoint_step(msc_ctx* ctx, int q, const double* m_new, const double* m_cur, const double* m_prev,
+                     const double* abar_new, double* abar_cur, double* abar_prev, double* dforce, double eps,
+                     int kmax, msc_adjoint_stats* out);
+
+/* msc_save_state / msc_load_state with the blob in device memory (same layout; checkpoints of a
+   reverse pass stay on the device).  Synchronise the stream. */
+int msc_save_state_device(msc_ctx* ctx, void* dev_blob, size_t* bytes);
+int msc_load_state_device(msc_ctx* ctx, const void* dev_blob, size_t bytes);
 
 /* ---------------------------------------------------------------------------------------------
  * Batched march (a parameter sweep, Section 4.6 "Operating envelope": the same method over a range

@@ -29,7 +29,8 @@ class LatticeDesc(ctypes.Structure):
 class Params(ctypes.Structure):
     _fields_ = [("nu", ctypes.c_double), ("dt", ctypes.c_double), ("eps", ctypes.c_double),
                 ("kmax", ctypes.c_int), ("nmin", ctypes.c_int), ("corrector", ctypes.c_int),
-                ("replay", ctypes.c_int), ("warm_order", ctypes.c_int), ("count_multiple", ctypes.c_int)]
+                ("replay", ctypes.c_int), ("warm_order", ctypes.c_int), ("count_multiple", ctypes.c_int),
+                ("force", ctypes.c_double * 3)]
 
 
 class Stats(ctypes.Structure):
@@ -47,6 +48,10 @@ class BatchTuning(ctypes.Structure):
                 ("sweep_rows", ctypes.c_int * MSC_BATCH_CLASSES), ("fft_rows", ctypes.c_int * MSC_BATCH_CLASSES),
                 ("col_lines", ctypes.c_int * MSC_BATCH_CLASSES), ("sweep_ctas_per_sm", ctypes.c_int),
                 ("sweep_us", ctypes.c_float), ("rowfft_us", ctypes.c_float), ("colsolve_us", ctypes.c_float)]
+
+
+class AdjointStats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("status", ctypes.c_int), ("residual", ctypes.c_double)]
 
 
 class MscError(RuntimeError):
@@ -90,6 +95,9 @@ _SIG = {
     "msc_shadow_solve": (_i, [_i, _i, _i, _d, _d, _vp, _vp, _vp, _sz, _vp]),
     "msc_equilibrium": (_i, [_i, _i, _i, _vp, _vp, _vp, _vp]),
     "msc_sweep_d2q9_noalloc": (_i, [_i, _i, _d, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "msc_adjoint_step": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _d, _i, ctypes.POINTER(AdjointStats)]),
+    "msc_save_state_device": (_i, [_vp, _vp, ctypes.POINTER(_sz)]),
+    "msc_load_state_device": (_i, [_vp, _vp, _sz]),
     "msc_batch_workspace_bytes": (_sz, [ctypes.POINTER(_vp), _i]),
     "msc_batch_create": (_i, [ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i, _vp, _sz, _vp]),
     "msc_batch_destroy": (None, [_vp]),

@@ -58,6 +58,7 @@ struct DevState {
     int kmax, nmin, corrector, replay;
     int warm_order;         // accepted states used by the warm start (1..3)
     int count_multiple;     // accepted inner counts are multiples of this (1 or 2)
+    double force[3];        // uniform body force, added to the momentum part of h_q
     int params_ok;
     // physical-step bookkeeping
     int64_t steps_done;     // accepted steps since init

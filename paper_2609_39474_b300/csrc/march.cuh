@@ -138,11 +138,12 @@ __device__ __forceinline__ void step_begin_range(const DevState* __restrict__ st
     const double c1 = q == 1 ? 1.0 / dt : 4.0 / (2.0 * dt);
     const double c2 = q == 1 ? 0.0 : 1.0 / (2.0 * dt);
     const T sig = (T)vs->fscale, isig = T(1) / sig;
+    const double fc[4] = {0.0, vs->force[0], vs->force[1], vs->force[2]};
     for (size_t i = i0; i < sites; i += istride) {
 #pragma unroll
-        for (int c = 0; c <= L::D; ++c) {
+        for (int c = 0; c <= L::D; ++c) {  // h = c1 m^n - c2 m^{n-1} + (0, F), as k_step_end forms it
             const size_t o = c * sites + i;
-            h[o] = (T)(c1 * mn[o] - c2 * mnm1[o]);
+            h[o] = (T)fma(c1, mn[o], fma(-c2, mnm1[o], fc[c]));
         }
         if (nav == 1) {
 #pragma unroll
@@ -202,6 +203,9 @@ __device__ __forceinline__ void step_end_range(const DevState* __restrict__ st, 
     const T sig = (T)vs->fscale, isig = T(1) / sig;
     const double n1 = 4.0 / (2.0 * dt), n2 = 1.0 / (2.0 * dt);  // BDF2 for the next step
     const double k1 = 0.5 * c1 * inv, k2 = 0.5 * c2 * inv;
+    // body force: (0, F) joins h in the reconstruction and in the next step's h
+    const double fc[4] = {0.0, vs->force[0], vs->force[1], vs->force[2]};
+    const double kf[4] = {0.0, 0.5 * inv * fc[1], 0.5 * inv * fc[2], 0.5 * inv * fc[3]};
 #pragma unroll 2
     for (size_t i = i0; i < sites; i += istride) {
         T fv[L::Q];
@@ -217,12 +221,12 @@ __device__ __forceinline__ void step_end_range(const DevState* __restrict__ st, 
         }
 #pragma unroll
         for (int c = 0; c <= L::D; ++c) {
-            // m^{n+1} = (P f + h/2) inv with h = c1 m^n - c2 m^{n-1}, constants folded (FP64)
+            // m^{n+1} = (P f + h/2) inv with h = c1 m^n - c2 m^{n-1} + (0, F), constants folded (FP64)
             const size_t o = c * sites + i;
             const double mc = mn[o];
-            const double mnew = fma(k1, mc, fma(-k2, mnm1[o], inv * (double)mom[c]));
+            const double mnew = fma(k1, mc, fma(-k2, mnm1[o], fma(inv, (double)mom[c], kf[c])));
             mnm1[o] = mnew;
-            if (next) h[o] = (T)fma(n1, mnew, -n2 * mc);
+            if (next) h[o] = (T)fma(n1, mnew, fma(-n2, mc, fc[c]));
         }
         if (next) {
             if (nav == 1) {
@@ -304,6 +308,9 @@ __global__ void k_set_params(DevState* st, msc_params p) {
     st->replay = p.replay;
     st->warm_order = p.warm_order;
     st->count_multiple = p.count_multiple;
+    st->force[0] = p.force[0];
+    st->force[1] = p.force[1];
+    st->force[2] = p.force[2];
     st->params_ok = 1;
 }
 

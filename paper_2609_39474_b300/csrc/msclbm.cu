@@ -1,6 +1,7 @@
 // C ABI of the MSC-LBM library: contexts, the device-resident march (CUDA graph with nested
 // conditional WHILE/IF nodes, so that the acceptance test of Algorithm 1 never leaves the
 // device), the explicit LBM baseline and the stage entry points.  See include/msclbm.h.
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -594,7 +595,8 @@ int msc_set_params(msc_ctx* c, const msc_params* p) {
     if (!c || !p) return MSC_ERR_ARG;
     if (!(p->dt > 0.0) || !(p->eps >= 0.0) || !(p->nu > 0.0) || p->kmax < 1 || p->nmin < 1 ||
         (p->corrector != 0 && p->corrector != 1) || (p->replay != 0 && p->replay != 1) || p->warm_order < 0 ||
-        p->warm_order > 3 || p->count_multiple < 0 || p->count_multiple > 2)
+        p->warm_order > 3 || p->count_multiple < 0 || p->count_multiple > 2 || !std::isfinite(p->force[0]) ||
+        !std::isfinite(p->force[1]) || !std::isfinite(p->force[2]))
         return MSC_ERR_ARG;
     // the shadow solve bakes nu into the graph: rebuild if it changes
     if (c->params_set && p->nu != c->params.nu && c->x_march) {
@@ -998,3 +1000,4 @@ int msc_equilibrium(int dim, int n, int precision, const double* p, const double
 
 #include "sweep_noalloc.cuh"
 #include "batch_api.cuh"
+#include "adjoint_api.cuh"

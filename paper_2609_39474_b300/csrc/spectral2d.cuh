@@ -192,9 +192,34 @@ __device__ __forceinline__ void schur_apply(C* v[D + 1], const double* kv, const
     }
 }
 
+// Transposed solve x = (H(k)^H)^{-1} y, the per-wavevector factor of the adjoint shadow correction
+// (the transpose of F^{-1} chi H^{-1} F for the real inner product): with the same table,
+//   dp = A y_p + i cs^2 B (k.y_m),   du = Dv y_m + i (Cc / cs^2) k dp.
+template <typename C, int D>
+__device__ __forceinline__ void schur_apply_adjoint(C* v[D + 1], const double* kv, const double* cf) {
+    using T = decltype(v[0]->x);
+    double rx[D + 1], ry[D + 1];
+#pragma unroll
+    for (int i = 0; i <= D; ++i) { rx[i] = (double)v[i]->x; ry[i] = (double)v[i]->y; }
+    double krx = 0.0, kry = 0.0;
+#pragma unroll
+    for (int al = 0; al < D; ++al) { krx += kv[al] * rx[al + 1]; kry += kv[al] * ry[al + 1]; }
+    const double bt = kCs2 * cf[1], ct = cf[2] / kCs2;
+    const double dpx = cf[0] * rx[0] - bt * kry;
+    const double dpy = cf[0] * ry[0] + bt * krx;
+    v[0]->x = (T)dpx;
+    v[0]->y = (T)dpy;
+#pragma unroll
+    for (int al = 0; al < D; ++al) {
+        const double ck = ct * kv[al];
+        v[al + 1]->x = (T)(cf[3] * rx[al + 1] - ck * dpy);
+        v[al + 1]->y = (T)(cf[3] * ry[al + 1] + ck * dpx);
+    }
+}
+
 // 2D: G consecutive kept j_x columns per block (G a power of two; the last block of a lattice may
 // hold fewer), all three fields of each.  Line (c, g) of the block sits at (c G + g) plen in shared memory.
-template <typename T>
+template <typename T, bool ADJ = false>
 __device__ __forceinline__ void colsolve_block(const Spec2Args<T>& A, int bid, int G) {
     using C = typename Cplx<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -243,7 +268,8 @@ __device__ __forceinline__ void colsolve_block(const Spec2Args<T>& A, int bid, i
         } else {
             solve_coefficients(a, A.nu, kv[0] * kv[0] + kv[1] * kv[1], scale, cf);
         }
-        schur_apply<C, 2>(v, kv, cf);
+        if (ADJ) schur_apply_adjoint<C, 2>(v, kv, cf);
+        else schur_apply<C, 2>(v, kv, cf);
     }
     __syncthreads();
     fft_stockham<C, true>(s, n, logn, 3 * G, A.tw);
@@ -257,6 +283,12 @@ __device__ __forceinline__ void colsolve_block(const Spec2Args<T>& A, int bid, i
 template <typename T>
 __global__ void __launch_bounds__(sizeof(T) == 8 ? 384 : 768) k_colsolve(Spec2Args<T> A) {
     colsolve_block<T>(A, blockIdx.x, 1);
+}
+
+// the transposed column solve of the adjoint shadow correction
+template <typename T>
+__global__ void __launch_bounds__(sizeof(T) == 8 ? 384 : 768) k_colsolve_adjoint(Spec2Args<T> A) {
+    colsolve_block<T, true>(A, blockIdx.x, 1);
 }
 
 inline int spec2_col_threads(int n) {

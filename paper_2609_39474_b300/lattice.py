@@ -76,13 +76,18 @@ class MscLattice:
 
     def set_params(self, dt: float, eps: float = 1e-8, nu: float = 1.0 / 6.0, kmax: int = 300,
                    nmin=None, corrector: bool = True, replay: bool = False, warm_order: int = 0,
-                   count_multiple: int = 0):
+                   count_multiple: int = 0, force=None):
         """warm_order: 3 cubic (Section 3.1), 2 linear, 1 none; 0 = 3 for FP64, FP32: 2 (D2Q9) / 1 (D3Q19).
         count_multiple: accepted inner counts are multiples of it (1 = Algorithm 1, 2 = sweeps in pairs);
-        0 = 2 for FP32 D2Q9, else 1."""
+        0 = 2 for FP32 D2Q9, else 1.  force: uniform body force (d components, default zero)."""
         if nmin is None:
             nmin = 2 if self.dim == 2 else 1
-        p = L.Params(nu, dt, eps, kmax, nmin, int(corrector), int(replay), int(warm_order), int(count_multiple))
+        fv = [0.0, 0.0, 0.0]
+        if force is not None:
+            for al, v in enumerate(force):
+                fv[al] = float(v)
+        p = L.Params(nu, dt, eps, kmax, nmin, int(corrector), int(replay), int(warm_order), int(count_multiple),
+                     (ctypes.c_double * 3)(*fv))
         L.check(L.lib.msc_set_params(self._ctx, ctypes.byref(p)), "msc_set_params")
 
     def init_fields(self, p_hat, u):
@@ -154,8 +159,45 @@ class MscLattice:
     def load_state(self, blob: bytes):
         L.check(L.lib.msc_load_state(self._ctx, blob, len(blob)), "msc_load_state")
 
+    def save_state_device(self) -> torch.Tensor:
+        """The msc_save_state blob, kept in device memory (uint8 tensor)."""
+        n = ctypes.c_size_t()
+        L.check(L.lib.msc_save_state_device(self._ctx, None, ctypes.byref(n)), "msc_save_state_device")
+        blob = torch.empty(n.value, dtype=torch.uint8, device=self.device)
+        L.check(L.lib.msc_save_state_device(self._ctx, _ptr(blob), ctypes.byref(n)), "msc_save_state_device")
+        return blob
+
+    def load_state_device(self, blob: torch.Tensor):
+        L.check(L.lib.msc_load_state_device(self._ctx, _ptr(blob), blob.numel()), "msc_load_state_device")
+
+    def moments_into(self, out: torch.Tensor):
+        """Copy m^n = (p_hat, u) of the last accepted step into a (d+1, n, ...) float64 device tensor."""
+        _check_moments(out)
+        L.check(L.lib.msc_read_fields(self._ctx, _ptr(out[0]), _ptr(out[1]), 1), "msc_read_fields")
+
+    def adjoint_step(self, q: int, m_new, m_cur, m_prev, abar_new, abar_cur, abar_prev, dforce,
+                     eps: float = 1e-10, kmax: int = 1000) -> dict:
+        """msc_adjoint_step: dL/dm^{n+1} -> accumulate into dL/dm^n, dL/dm^{n-1}, dL/dF (device float64)."""
+        _check_moments(m_new, m_cur, m_prev, abar_new, abar_cur, abar_prev)
+        st = L.AdjointStats()
+        rc = L.lib.msc_adjoint_step(self._ctx, int(q), _ptr(m_new), _ptr(m_cur), _dptr(m_prev), _ptr(abar_new),
+                                    _ptr(abar_cur), _dptr(abar_prev), _ptr(dforce), float(eps), int(kmax),
+                                    ctypes.byref(st))
+        L.check(rc, "msc_adjoint_step")
+        return {"iters": st.iters, "residual": st.residual}
+
 
 # ---- stage calls ---------------------------------------------------------------------------------
+
+def _dptr(t):
+    return None if t is None else t.data_ptr()
+
+
+def _check_moments(*ts):
+    for t in ts:
+        if t is not None and (t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous()):
+            raise ValueError("moment arrays must be contiguous float64 device tensors of shape (d+1, n, n)")
+
 
 class MscBatch:
     """Several D2Q9 lattices (one precision, one stream, any mix of n and parameters) marched by one

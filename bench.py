@@ -459,6 +459,71 @@ def batch_stage(torch, PL, dev, args):
     return out
 
 
+def measure_adjoint(torch, PL, dev, n=256, dt_target=32.0, fd_dirs=1):
+    """Config 5: L = 1/2 sum |u^S - u*|^2 at t = 0.1 N^2 / nu, u* from a seeded target field run
+    under a force; gradients with respect to u0 (guess seed 3) and the force (at F = 0) by the
+    discrete adjoint with checkpoints every 8 steps, checked against central differences."""
+    from paper_2609_39474_b300.adjoint import MarchRunner
+    t_end = nint(0.6 * n * n)
+    S = nint(t_end / dt_target)
+    dt = t_end / S
+    U = NU / n
+    eps = 1e-5 * U  # acceptance tolerance: 1e-5 of the amplitude
+    F_star = (0.5 * U / t_end, 0.25 * U / t_end)
+    pt, ut = random_phase(n, 2, 1.0, seed=2, kmax=8)
+    p0, u0 = random_phase(n, 2, 1.0, seed=3, kmax=8)
+    p0_d, u0_d = torch.as_tensor(p0, device=dev), torch.as_tensor(u0, device=dev)
+
+    def runner():
+        return MarchRunner(PL.MscLattice(2, n, "fp32", max_steps=64, hist_cap=1 << 12, device=str(dev)), dt=dt,
+                           steps=S, eps=eps, checkpoint_every=8, eps_adjoint=1e-5, kmax_adjoint=2000)
+
+    target = runner().forward(torch.as_tensor(pt, device=dev), torch.as_tensor(ut, device=dev), F_star)
+    R = runner()
+
+    def ev():
+        return torch.cuda.Event(enable_timing=True)
+
+    R.forward(p0_d, u0_d)  # warm-up (graph build)
+    torch.cuda.synchronize()
+    e0, e1, e2 = ev(), ev(), ev()
+    e0.record()
+    uS = R.forward(p0_d, u0_d)
+    e1.record()
+    gp, gu, gF = R.backward(uS - target)
+    e2.record()
+    torch.cuda.synchronize()
+    t_fwd, t_bwd = e0.elapsed_time(e1), e1.elapsed_time(e2)
+    loss0 = 0.5 * float(((uS - target) ** 2).sum())
+
+    def loss(u0_, F_):
+        uu = R.forward(p0_d, u0_, F_)
+        return 0.5 * float(((uu - target) ** 2).sum())
+
+    rng = np.random.default_rng(11)
+    checks = []
+    for _ in range(fd_dirs):
+        v = torch.as_tensor(rng.standard_normal(u0.shape) * np.abs(u0).max(), device=dev)
+        d = 1e-2
+        fd = (loss(u0_d + d * v, (0.0, 0.0)) - loss(u0_d - d * v, (0.0, 0.0))) / (2 * d)
+        checks.append({"wrt": "u0 (random direction)", "adjoint": float((gu * v).sum()), "central_fd": fd})
+    for al in range(2):
+        dF = 0.2 * abs(F_star[0])
+        e = [0.0, 0.0]
+        e[al] = dF
+        fd = (loss(u0_d, tuple(e)) - loss(u0_d, tuple(-x for x in e))) / (2 * dF)
+        checks.append({"wrt": f"F[{al}]", "adjoint": float(gF[al]), "central_fd": fd})
+    for c in checks:
+        c["rel_diff"] = abs(c["adjoint"] / c["central_fd"] - 1)
+    it = R.adjoint_iters
+    return {"workload": f"D2Q9 periodic N={n} Re=1 FP32, T_end={t_end} (0.1 N^2/nu), S={S}, dt={dt:.3f}, "
+                        "target seed 2 under F*, guess seed 3 at F = 0, checkpoints every 8 steps",
+            "loss": loss0, "t_forward_ms": t_fwd, "t_backward_ms": t_bwd, "backward_over_forward": t_bwd / t_fwd,
+            "adjoint_iters_per_step": float(np.mean(it)), "adjoint_iters_max": int(max(it)),
+            "grad_norms": {"u0": float(gu.norm()), "F": [float(x) for x in gF]}, "fd_checks": checks,
+            "checkpoint_bytes": int(sum(b.numel() for b in R.checkpoints))}
+
+
 def run_ours(args, rank, world, dist):
     import torch
     from paper_2609_39474_b300 import lattice as PL
@@ -490,6 +555,7 @@ def run_ours(args, rank, world, dist):
                 sec = measure_workload(torch, PL, dev, dim, n, max(3, min(args.steps, 10)), 3, dist, full=False)
                 sec.pop("clocks", None)
                 res["secondary"].append(sec)
+    res["adjoint"] = None if args.no_secondary else measure_adjoint(torch, PL, dev)
     res["batch"] = None
     if batch_refs is not None:
         pool, refs = batch_refs
@@ -509,6 +575,8 @@ def run_phase(args):
         return {"phase": "batch-stage", **batch_stage(torch, PL, dev, args)}
     if args.phase == "batch":
         return {"phase": "batch", **measure_batch(torch, PL, dev)}
+    if args.phase == "adjoint":
+        return {"phase": "adjoint", **measure_adjoint(torch, PL, dev)}
     n = args.n
     S, eps = DEFAULT_CANDIDATE.get(n, (64, 1e-8))
     p, u = random_phase(n, 2, 1.0, seed=1, kmax=8)
@@ -660,7 +728,7 @@ def main():
                     help="--phase batch-stage: a batch tiling as JSON (keys sweep_rows, fft_rows, col_lines, "
                          "sweep_ctas_per_sm) instead of autotuning, so that only the timed launches run")
     ap.add_argument("--phase", default="all",
-                    choices=["all", "msc", "msc-stepwise", "sweep", "batch", "batch-stage"],
+                    choices=["all", "msc", "msc-stepwise", "sweep", "batch", "batch-stage", "adjoint"],
                     help="profiling aids: 'msc' runs only the timed MSC marches of the default candidate, "
                          "'msc-stepwise' the same marches driven from the host (one launch per kernel, "
                          "visible to ncu), 'sweep' only the fused-sweep roofline loop, 'batch' only the "
@@ -736,6 +804,7 @@ def main():
         "secondary": res["secondary"],
         "batch": res["batch"],
         "fp16": res["fp16"],
+        "adjoint": res["adjoint"],
     }
     print(json.dumps(line))
     if dist is not None:

@@ -102,6 +102,11 @@ typedef struct {
                        momentum source, s_u = h_u - a u + F, i.e. (0, F) joins h_q in both the
                        reconstruction (Eq. macro-reconstruct) and the source (Eq. source-moments).
                        Zero reproduces the paper's march. */
+    double omega[2]; /* TRT relaxation rates (omega+, omega-) of the general collision (Eq. collision)
+                       for off-design runs, 0 < omega < 2; 0, 0 (or 1, 1) = the operating point
+                       Lambda = 1/4, nu = 1/6 (Eq. collision-operating).  The viscosity of the shadow
+                       solve stays `nu`: set nu = (1/omega+ - 1/2)/3 for a consistent corrector.
+                       D2Q9 only; the batch and the adjoint run at the operating point only. */
 } msc_params;
 
 typedef struct {
@@ -220,6 +225,13 @@ int msc_shadow_solve(int dim, int n, int precision, double a, double nu, const v
 /* f_out = f_eq(p_hat, u) (Eq. feq) from double device fields; f_out in the storage type. */
 int msc_equilibrium(int dim, int n, int precision, const double* p_hat, const double* u,
                     void* f_out, void* stream);
+
+/* msc_sweep for D2Q9 with the general TRT collision (Eq. collision) at relaxation rates
+   omega_p = 1/tau+, omega_m = 1/tau- (each in (0, 2)); with omega_p = omega_m = 1 it equals the
+   operating-point sweep up to rounding.  Arguments otherwise as msc_sweep (dim = 2). */
+int msc_sweep_trt(int n, int precision, double a, double omega_p, double omega_m, const void* f_in, const void* dm,
+                  const void* h, void* f_out, void* pr_out, double* sumsq_out, void* scratch, size_t scratch_bytes,
+                  void* stream);
 
 /* Allocation-free variant of msc_sweep for D2Q9 (dim 2).  The paper has no counterpart: this is
    an interface convenience for callers that cannot allocate device memory, such as host

@@ -19,6 +19,9 @@ written to be checked against the paper by eye:
                 explicit LBM, population/moment histories (Section 3.1).
 * ``linear``    the linearised Fourier symbol of one sweep and of one corrected
                 iteration (Eqs. local-linear-response, symbol).
+* ``fullsymbol``  the full-symbol reference operator of off-design runs
+                (Eq. full-symbol) and the TRT rate / ghost-survival relations
+                (Eqs. trt, eta).
 * ``adjoint``   the discrete adjoint of the converged march (implicit
                 differentiation of every accepted fixed point; exact sparse
                 solves, complex-step collision Jacobians) and the body force.

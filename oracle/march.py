@@ -50,6 +50,8 @@ class MarchParams:
                               # 1 (f^n) and 2 (2f^n - f^{n-1}) truncate it
     count_multiple: int = 1   # accept only at inner counts that are multiples of this (1: Algorithm 1;
                               # 2: sweeps in pairs, for reduced-precision storage)
+    full_symbol: bool = False  # corrector: the full-symbol reference operator (Eq. full-symbol) instead of
+                              # the shadow correction: f <- f + F^{-1}[(I - Z J)^{-1} F r]
     force: Optional[tuple] = None  # uniform body force F (d components); the paper has none.  Read as
                               # an addition to the momentum source, s_u = h_u - a u + F, which is the
                               # same as adding (0, F) to h in both the reconstruction and the source
@@ -122,6 +124,10 @@ def physical_step(st: DualTimeState, prm: MarchParams, replay_count: Optional[in
     h = forced_history(lat, h, prm.force)
     f = warm_start(st.f_hist, prm.warm_order)
     res = []
+    Minv = None
+    if prm.full_symbol and prm.corrector:
+        from .fullsymbol import correction_matrices, rest_jacobian
+        Minv = correction_matrices(lat, rest_jacobian(lat, a, prm.omega or (1.0, 1.0)), f.shape[1:])
     for ell in range(1, prm.kmax + 1):
         f_T = sweep(lat, f, a, h, prm.omega)
         r, R = residual(f_T, f)
@@ -139,7 +145,10 @@ def physical_step(st: DualTimeState, prm: MarchParams, replay_count: Optional[in
             rec = StepRecord(q, ell, res, True)
             st.records.append(rec)
             return rec
-        if prm.corrector:
+        if Minv is not None:
+            from .fullsymbol import full_symbol_correction
+            f = f + full_symbol_correction(lat, r, Minv)
+        elif prm.corrector:
             _, df = shadow_correction(lat, r, a, prm.nu)
             f = f_T + df
         else:
@@ -161,10 +170,10 @@ def march(st: DualTimeState, prm: MarchParams, n_steps: int, replay_counts=None)
     return out
 
 
-def explicit_march(lat: Lattice, f: np.ndarray, n_steps: int) -> np.ndarray:
-    """n_steps explicit LBM steps f <- S f_eq(P f) (same collision and streaming, no source)."""
+def explicit_march(lat: Lattice, f: np.ndarray, n_steps: int, omega=None) -> np.ndarray:
+    """n_steps explicit LBM steps f <- S C(f) (same collision and streaming, no source)."""
     for _ in range(n_steps):
-        f = explicit_step(lat, f)
+        f = explicit_step(lat, f, omega)
     return f
 
 

@@ -54,7 +54,7 @@ def residual(f_T: np.ndarray, f: np.ndarray):
     return r, float(np.sqrt(np.sum(r * r) / r.size))
 
 
-def explicit_step(lat: Lattice, f: np.ndarray) -> np.ndarray:
+def explicit_step(lat: Lattice, f: np.ndarray, omega=None) -> np.ndarray:
     """Explicit LBM step: the same collision and streaming with no BDF source (a = h = 0)."""
     zero = np.zeros((lat.d + 1,) + f.shape[1:])
-    return sweep(lat, f, 0.0, zero)
+    return sweep(lat, f, 0.0, zero, omega)

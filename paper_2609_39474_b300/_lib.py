@@ -30,7 +30,7 @@ class Params(ctypes.Structure):
     _fields_ = [("nu", ctypes.c_double), ("dt", ctypes.c_double), ("eps", ctypes.c_double),
                 ("kmax", ctypes.c_int), ("nmin", ctypes.c_int), ("corrector", ctypes.c_int),
                 ("replay", ctypes.c_int), ("warm_order", ctypes.c_int), ("count_multiple", ctypes.c_int),
-                ("force", ctypes.c_double * 3)]
+                ("force", ctypes.c_double * 3), ("omega", ctypes.c_double * 2)]
 
 
 class Stats(ctypes.Structure):
@@ -95,6 +95,7 @@ _SIG = {
     "msc_shadow_solve": (_i, [_i, _i, _i, _d, _d, _vp, _vp, _vp, _sz, _vp]),
     "msc_equilibrium": (_i, [_i, _i, _i, _vp, _vp, _vp, _vp]),
     "msc_sweep_d2q9_noalloc": (_i, [_i, _i, _d, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "msc_sweep_trt": (_i, [_i, _i, _d, _d, _d, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "msc_adjoint_step": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _d, _i, ctypes.POINTER(AdjointStats)]),
     "msc_save_state_device": (_i, [_vp, _vp, ctypes.POINTER(_sz)]),
     "msc_load_state_device": (_i, [_vp, _vp, _sz]),

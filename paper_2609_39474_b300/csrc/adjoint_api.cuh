@@ -111,6 +111,7 @@ int msc_adjoint_step(msc_ctx* c, int q, const double* m_new, const double* m_cur
     if (q == 2 && (!m_prev || !abar_prev)) return MSC_ERR_ARG;
     if (c->desc.dim != 2) return MSC_ERR_ARG;
     if (!c->params_set) return MSC_ERR_STATE;
+    if (ctx_trt(c)) return MSC_ERR_ARG;  // the adjoint differentiates the operating-point collision
     if (c->desc.precision == MSC_FP64)
         return run_adjoint_step<double>(c, q, m_new, m_cur, m_prev, abar_new, abar_cur, abar_prev, dforce, eps,
                                         kmax, out);

@@ -497,6 +497,7 @@ int msc_batch_march(msc_batch* b, const int* n_steps) {
         msc_ctx* c = b->ctx[i];
         if (k < 0) return MSC_ERR_ARG;
         if (k > 0 && (!c->params_set || !c->fields_set)) return MSC_ERR_STATE;
+        if (k > 0 && ctx_trt(c)) return MSC_ERR_ARG;  // the batched sweep is the operating-point kernel
         if (k > 0 && c->params.replay && k > c->desc.max_steps) return MSC_ERR_ARG;
         s.n[i] = k;
     }

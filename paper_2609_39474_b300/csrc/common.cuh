@@ -27,6 +27,10 @@ struct D2Q9 {
     __host__ __device__ static constexpr double w(int k) {
         return k == 0 ? 4.0 / 9.0 : (k < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
     }
+    // the direction with c = -c_k (TRT even/odd pairs, Eq. trt)
+    __host__ __device__ static constexpr int opp(int k) {
+        return k == 0 ? 0 : (k < 5 ? (k + 1) % 4 + 1 : (k - 3) % 4 + 5);
+    }
 };
 
 struct D3Q19 {
@@ -59,6 +63,7 @@ struct DevState {
     int warm_order;         // accepted states used by the warm start (1..3)
     int count_multiple;     // accepted inner counts are multiples of this (1 or 2)
     double force[3];        // uniform body force, added to the momentum part of h_q
+    double omega_p, omega_m;  // TRT relaxation rates (1, 1 at the operating point)
     int params_ok;
     // physical-step bookkeeping
     int64_t steps_done;     // accepted steps since init

@@ -311,6 +311,8 @@ __global__ void k_set_params(DevState* st, msc_params p) {
     st->force[0] = p.force[0];
     st->force[1] = p.force[1];
     st->force[2] = p.force[2];
+    st->omega_p = p.omega[0] > 0.0 ? p.omega[0] : 1.0;
+    st->omega_m = p.omega[1] > 0.0 ? p.omega[1] : 1.0;
     st->params_ok = 1;
 }
 

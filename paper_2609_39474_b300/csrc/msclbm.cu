@@ -57,6 +57,20 @@ int sweep_blocks_for(int dim, int n, int precision) {
     return sweep3_geometry(n, precision == MSC_FP64 ? 8 : 4).blocks;
 }
 
+// off-design TRT rates in effect (0 means the operating point)
+bool params_trt(const msc_params& p) {
+    const double wp = p.omega[0] > 0.0 ? p.omega[0] : 1.0, wm = p.omega[1] > 0.0 ? p.omega[1] : 1.0;
+    return wp != 1.0 || wm != 1.0;
+}
+bool ctx_trt(const msc_ctx* c) { return c->params_set && params_trt(c->params); }
+
+// the 2D sweep kernel of a context: operating point or general TRT collision
+template <typename T, typename FS, bool EXPLICIT, bool GRAPH>
+const void* sweep2_kernel(const msc_ctx* c) {
+    return ctx_trt(c) ? (const void*)k_sweep2<T, FS, EXPLICIT, GRAPH, true>
+                      : (const void*)k_sweep2<T, FS, EXPLICIT, GRAPH, false>;
+}
+
 size_t spec_bytes(int dim, int n, int precision) {
     const size_t celem = precision == MSC_FP64 ? 16 : 8;
     if (dim == 2) return (size_t)3 * n * (n / 4 + 1) * celem;
@@ -290,7 +304,7 @@ int build_march_graph(msc_ctx* c) {
         A.h_corr = h_corr;
         A.cond = 1;
         void* a_sw[] = {&A};
-        sw = add_kernel(body_iter, {}, (const void*)k_sweep2<T, FS, false, true>, dim3(sweep2_geometry(c->desc.n).blocks),
+        sw = add_kernel(body_iter, {}, sweep2_kernel<T, FS, false, true>(c), dim3(sweep2_geometry(c->desc.n).blocks),
                         dim3(kSweepWarps * 32), 0, a_sw, &err);
     } else {
         Sweep3Args<T> A = sweep3_args_graph<T>(c);
@@ -340,7 +354,7 @@ int build_explicit_graph(msc_ctx* c) {
             A.ex_count = i == kExplicitUnroll - 1;
             A.h_ex = h_ex;
             void* aa[] = {&A};
-            prev = add_kernel(body, deps, (const void*)k_sweep2<T, FS, true, true>, dim3(sweep2_geometry(c->desc.n).blocks),
+            prev = add_kernel(body, deps, sweep2_kernel<T, FS, true, true>(c), dim3(sweep2_geometry(c->desc.n).blocks),
                               dim3(kSweepWarps * 32), 0, aa, &err);
         } else {
             Sweep3Args<T> A = sweep3_args_graph<T>(c);
@@ -377,7 +391,9 @@ int run_explicit(msc_ctx* c, int n_steps) {
         if (L::D == 2) {
             Sweep2Args<T, FS> A = sweep2_args_graph<T, FS>(c);
             A.ex_dir = i & 1;
-            k_sweep2<T, FS, true, true><<<sweep2_geometry(c->desc.n).blocks, kSweepWarps * 32, 0, c->stream>>>(A);
+            void* aa[] = {&A};
+            CK(cudaLaunchKernel(sweep2_kernel<T, FS, true, true>(c), dim3(sweep2_geometry(c->desc.n).blocks),
+                                dim3(kSweepWarps * 32), aa, 0, c->stream));
         } else {
             Sweep3Args<T> A = sweep3_args_graph<T>(c);
             A.ex_dir = i & 1;
@@ -490,7 +506,9 @@ int run_stepwise(msc_ctx* c, int n_steps) {
         for (;;) {
             if (L::D == 2) {
                 Sweep2Args<T, FS> A = sweep2_args_graph<T, FS>(c);
-                k_sweep2<T, FS, false, true><<<sweep2_geometry(c->desc.n).blocks, kSweepWarps * 32, 0, c->stream>>>(A);
+                void* aa[] = {&A};
+                CK(cudaLaunchKernel(sweep2_kernel<T, FS, false, true>(c), dim3(sweep2_geometry(c->desc.n).blocks),
+                                    dim3(kSweepWarps * 32), aa, 0, c->stream));
             } else {
                 Sweep3Args<T> A = sweep3_args_graph<T>(c);
                 k_sweep3<T, false, true><<<A.g.blocks, A.g.threads, A.g.smem, c->stream>>>(A);
@@ -596,14 +614,23 @@ int msc_set_params(msc_ctx* c, const msc_params* p) {
     if (!(p->dt > 0.0) || !(p->eps >= 0.0) || !(p->nu > 0.0) || p->kmax < 1 || p->nmin < 1 ||
         (p->corrector != 0 && p->corrector != 1) || (p->replay != 0 && p->replay != 1) || p->warm_order < 0 ||
         p->warm_order > 3 || p->count_multiple < 0 || p->count_multiple > 2 || !std::isfinite(p->force[0]) ||
-        !std::isfinite(p->force[1]) || !std::isfinite(p->force[2]))
+        !std::isfinite(p->force[1]) || !std::isfinite(p->force[2]) || !(p->omega[0] >= 0.0 && p->omega[0] < 2.0) ||
+        !(p->omega[1] >= 0.0 && p->omega[1] < 2.0))
         return MSC_ERR_ARG;
-    // the shadow solve bakes nu into the graph: rebuild if it changes
-    if (c->params_set && p->nu != c->params.nu && c->x_march) {
+    if (params_trt(*p) && c->desc.dim != 2) return MSC_ERR_ARG;  // the general TRT sweep exists for D2Q9
+    // the shadow solve bakes nu into the graph, the collision kind picks the sweep kernel: rebuild
+    const bool kind_changes = c->params_set && params_trt(*p) != params_trt(c->params);
+    if (c->params_set && (p->nu != c->params.nu || kind_changes) && c->x_march) {
         cudaGraphExecDestroy(c->x_march);
         cudaGraphDestroy(c->g_march);
         c->x_march = nullptr;
         c->g_march = nullptr;
+    }
+    if (kind_changes && c->x_ex) {
+        cudaGraphExecDestroy(c->x_ex);
+        cudaGraphDestroy(c->g_ex);
+        c->x_ex = nullptr;
+        c->g_ex = nullptr;
     }
     if (!c->params_set || p->dt != c->params.dt || p->nu != c->params.nu) c->coef_dirty = true;
     c->params = *p;
@@ -868,7 +895,7 @@ StageScratch stage_scratch(int dim, int n, int precision, void* base) {
 
 template <typename T, typename FS = T>
 int stage_sweep(int dim, int n, double a, const void* fin, const void* dm, const void* h, void* fout,
-                void* pr, double* sumsq, void* scratch, cudaStream_t stream) {
+                void* pr, double* sumsq, void* scratch, cudaStream_t stream, double wp = 0.0, double wm = 0.0) {
     StageScratch S = stage_scratch(dim, n, sizeof(T) == 8 ? MSC_FP64 : MSC_FP32, scratch);
     CK(cudaMemsetAsync(S.counter, 0, 4, stream));
     if (dim == 2) {
@@ -882,6 +909,8 @@ int stage_sweep(int dim, int n, double a, const void* fin, const void* dm, const
         A.pr = (T*)pr;
         A.a = a;
         A.fscale = 1.0;
+        A.omega_p = wp;
+        A.omega_m = wm;
         A.lift = dm != nullptr;
         A.sumsq_out = sumsq;
         A.partial = S.partial;
@@ -890,7 +919,10 @@ int stage_sweep(int dim, int n, double a, const void* fin, const void* dm, const
         A.nstrips = g.nstrips;
         A.hb = g.hb;
         A.nrowblk = g.nrowblk;
-        k_sweep2<T, FS, false, false><<<g.blocks, kSweepWarps * 32, 0, stream>>>(A);
+        if (wp > 0.0)
+            k_sweep2<T, FS, false, false, true><<<g.blocks, kSweepWarps * 32, 0, stream>>>(A);
+        else
+            k_sweep2<T, FS, false, false><<<g.blocks, kSweepWarps * 32, 0, stream>>>(A);
     } else if constexpr (std::is_same<T, FS>::value) {
         if (set_sweep3_smem_limits<T>(n) != 0) return MSC_ERR_CUDA;
         Sweep3Args<T> A;
@@ -962,6 +994,22 @@ int msc_sweep(int dim, int n, int precision, double a, const void* f_in, const v
         return stage_sweep<float, __half>(dim, n, a, f_in, dm, h, f_out, pr_out, sumsq_out, scratch,
                                           (cudaStream_t)stream);
     return stage_sweep<float>(dim, n, a, f_in, dm, h, f_out, pr_out, sumsq_out, scratch, (cudaStream_t)stream);
+}
+
+int msc_sweep_trt(int n, int precision, double a, double omega_p, double omega_m, const void* f_in, const void* dm,
+                  const void* h, void* f_out, void* pr_out, double* sumsq_out, void* scratch, size_t scratch_bytes,
+                  void* stream) {
+    if (!valid_lattice(2, n, precision) || !f_in || !h || !f_out || !pr_out || !sumsq_out || !scratch ||
+        f_in == f_out || scratch_bytes < msc_stage_scratch_bytes(2, n, precision) || !(a >= 0.0) ||
+        !(omega_p > 0.0 && omega_p < 2.0) || !(omega_m > 0.0 && omega_m < 2.0))
+        return MSC_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (precision == MSC_FP64)
+        return stage_sweep<double>(2, n, a, f_in, dm, h, f_out, pr_out, sumsq_out, scratch, st, omega_p, omega_m);
+    if (precision == MSC_FP16)
+        return stage_sweep<float, __half>(2, n, a, f_in, dm, h, f_out, pr_out, sumsq_out, scratch, st, omega_p,
+                                          omega_m);
+    return stage_sweep<float>(2, n, a, f_in, dm, h, f_out, pr_out, sumsq_out, scratch, st, omega_p, omega_m);
 }
 
 int msc_shadow_solve(int dim, int n, int precision, double a, double nu, const void* pr, void* dm,

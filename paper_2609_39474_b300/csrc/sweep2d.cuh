@@ -30,6 +30,7 @@ struct Sweep2Args {
     T* pr;
     double a;
     double fscale;  // stateless mode: population storage scale (FP16 storage holds f / fscale)
+    double omega_p, omega_m;  // stateless mode: TRT rates of the general collision (TRT kernels only)
     int lift;
     double* sumsq_out;
     // reduction scratch
@@ -95,10 +96,10 @@ __device__ inline void march_after_sweep(DevState* st, double total, double qsit
 
 // One warp unit of the sweep: output columns [strip*30, strip*30 + 30) of rows [rb*hb, rb*hb + hb).
 // Returns this lane's share of sum r^2 (zero in EXPLICIT mode).  Called by all 32 lanes.
-template <typename T, typename S, bool EXPLICIT>
+template <typename T, typename S, bool EXPLICIT, bool TRT = false>
 __device__ __forceinline__ double sweep2_unit(const S* fin, const T* dm, const T* hh, S* fout, T* pr, T a, T inv,
                                               int lift, int n, int hb, int strip, int rb, int lane,
-                                              T sig = T(1), T isig = T(1)) {
+                                              T sig = T(1), T isig = T(1), T wp = T(1), T wm = T(1)) {
     using L = D2Q9;
     const int nmask = n - 1;
     const size_t NN = (size_t)n * n;
@@ -155,14 +156,38 @@ __device__ __forceinline__ double sweep2_unit(const S* fin, const T* dm, const T
             sx = h1 - a * ux;
             sy = h2 - a * uy;
         }
-        // operating-point collision C = f_eq + Phi/2 (Eq. collision-operating)
-        const T A0 = p + T(0.5) * s0 - T(1.5) * (ux * ux + uy * uy) - T(1.5) * (ux * sx + uy * sy);
         T C[9];
+        if constexpr (!TRT) {
+            // operating-point collision C = f_eq + Phi/2 (Eq. collision-operating)
+            const T A0 = p + T(0.5) * s0 - T(1.5) * (ux * ux + uy * uy) - T(1.5) * (ux * sx + uy * sy);
 #pragma unroll
-        for (int k = 0; k < 9; ++k) {
-            const T cu = T(L::cx(k)) * ux + T(L::cy(k)) * uy;
-            const T cs = T(L::cx(k)) * sx + T(L::cy(k)) * sy;
-            C[k] = (T)L::w(k) * (A0 + T(3) * cu + T(1.5) * cs + T(4.5) * cu * (cu + cs));
+            for (int k = 0; k < 9; ++k) {
+                const T cu = T(L::cx(k)) * ux + T(L::cy(k)) * uy;
+                const T cs = T(L::cx(k)) * sx + T(L::cy(k)) * sy;
+                C[k] = (T)L::w(k) * (A0 + T(3) * cu + T(1.5) * cs + T(4.5) * cu * (cu + cs));
+            }
+        } else {
+            // general TRT collision (Eq. collision): even / odd parts of f, f_eq (Eq. feq) and the
+            // source distribution Phi (Eq. source-distribution) relax at omega+ / omega-
+            const T B0 = p - T(1.5) * (ux * ux + uy * uy);
+            const T us = ux * sx + uy * sy;
+            T E[9], Ph[9];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) {
+                const T cu = T(L::cx(k)) * ux + T(L::cy(k)) * uy;
+                const T cs = T(L::cx(k)) * sx + T(L::cy(k)) * sy;
+                E[k] = (T)L::w(k) * (B0 + T(3) * cu + T(4.5) * cu * cu);
+                Ph[k] = (T)L::w(k) * (s0 + T(3) * (cs - us) + T(9) * cu * cs);
+            }
+            const T hp = T(1) - T(0.5) * wp, hm = T(1) - T(0.5) * wm;
+#pragma unroll
+            for (int k = 0; k < 9; ++k) {
+                const int o = L::opp(k);
+                const T fp = T(0.5) * (f[k] + f[o]), fm = T(0.5) * (f[k] - f[o]);
+                const T ep = T(0.5) * (E[k] + E[o]), em = T(0.5) * (E[k] - E[o]);
+                const T pp = T(0.5) * (Ph[k] + Ph[o]), pm = T(0.5) * (Ph[k] - Ph[o]);
+                C[k] = f[k] - wp * (fp - ep) - wm * (fm - em) + hp * pp + hm * pm;
+            }
         }
         // push streaming in x: value for column x comes from column x - c_kx
 #pragma unroll
@@ -207,7 +232,7 @@ __device__ __forceinline__ double sweep2_unit(const S* fin, const T* dm, const T
     return ssq;
 }
 
-template <typename T, typename S, bool EXPLICIT, bool GRAPH>
+template <typename T, typename S, bool EXPLICIT, bool GRAPH, bool TRT = false>
 __global__ void __launch_bounds__(kSweepWarps * 32) k_sweep2(Sweep2Args<T, S> A) {
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -223,9 +248,11 @@ __global__ void __launch_bounds__(kSweepWarps * 32) k_sweep2(Sweep2Args<T, S> A)
     T inv = (T)(1.0 / (1.0 + A.a / 2.0));
     int lift = A.lift;
     double fs = A.fscale;
+    double wpd = A.omega_p, wmd = A.omega_m;
     if (GRAPH) {
         const volatile DevState* vs = A.st;
         if constexpr (!std::is_same<S, T>::value) fs = vs->fscale;
+        if constexpr (TRT) { wpd = vs->omega_p; wmd = vs->omega_m; }
         if (EXPLICIT) {
             const int sa = vs->ex_a, sb = vs->ex_b;
             fin = A.fbase + (size_t)(A.ex_dir ? sb : sa) * A.fstride;
@@ -249,8 +276,8 @@ __global__ void __launch_bounds__(kSweepWarps * 32) k_sweep2(Sweep2Args<T, S> A)
     const int unit = blockIdx.x * kSweepWarps + warp;
     double ssq = 0.0;
     if (unit < A.nstrips * A.nrowblk)  // warp-uniform
-        ssq = sweep2_unit<T, S, EXPLICIT>(fin, dm, hh, fout, pr, a, inv, lift, n, A.hb, unit % A.nstrips,
-                                          unit / A.nstrips, lane, (T)fs, (T)(1.0 / fs));
+        ssq = sweep2_unit<T, S, EXPLICIT, TRT>(fin, dm, hh, fout, pr, a, inv, lift, n, A.hb, unit % A.nstrips,
+                                               unit / A.nstrips, lane, (T)fs, (T)(1.0 / fs), (T)wpd, (T)wmd);
     if (EXPLICIT) return;
 
     // ---- residual norm: block partials, last block reduces in a fixed order ----

@@ -76,18 +76,20 @@ class MscLattice:
 
     def set_params(self, dt: float, eps: float = 1e-8, nu: float = 1.0 / 6.0, kmax: int = 300,
                    nmin=None, corrector: bool = True, replay: bool = False, warm_order: int = 0,
-                   count_multiple: int = 0, force=None):
+                   count_multiple: int = 0, force=None, omega=None):
         """warm_order: 3 cubic (Section 3.1), 2 linear, 1 none; 0 = 3 for FP64, FP32: 2 (D2Q9) / 1 (D3Q19).
         count_multiple: accepted inner counts are multiples of it (1 = Algorithm 1, 2 = sweeps in pairs);
-        0 = 2 for FP32 D2Q9, else 1.  force: uniform body force (d components, default zero)."""
+        0 = 2 for FP32 D2Q9, else 1.  force: uniform body force (d components, default zero).
+        omega: (omega+, omega-) of the general TRT collision (D2Q9; default the operating point)."""
         if nmin is None:
             nmin = 2 if self.dim == 2 else 1
         fv = [0.0, 0.0, 0.0]
         if force is not None:
             for al, v in enumerate(force):
                 fv[al] = float(v)
+        om = [0.0, 0.0] if omega is None else [float(omega[0]), float(omega[1])]
         p = L.Params(nu, dt, eps, kmax, nmin, int(corrector), int(replay), int(warm_order), int(count_multiple),
-                     (ctypes.c_double * 3)(*fv))
+                     (ctypes.c_double * 3)(*fv), (ctypes.c_double * 2)(*om))
         L.check(L.lib.msc_set_params(self._ctx, ctypes.byref(p)), "msc_set_params")
 
     def init_fields(self, p_hat, u):
@@ -302,6 +304,23 @@ def sweep(dim: int, n: int, precision: str, a: float, f_in: torch.Tensor, h: tor
     L.check(L.lib.msc_sweep(dim, n, precision_code(precision), float(a), _ptr(f_in),
                             _ptr(dm) if dm is not None else None, _ptr(h), _ptr(f_out), _ptr(pr), _ptr(ssq),
                             _ptr(scratch.buf), scratch.nbytes, _stream(stream)), "msc_sweep")
+    return f_out, pr, ssq
+
+
+def sweep_trt(n: int, precision: str, a: float, omega_p: float, omega_m: float, f_in: torch.Tensor, h: torch.Tensor,
+              dm: torch.Tensor = None, scratch: StageScratch = None, stream=None):
+    """One D2Q9 sweep with the general TRT collision through msc_sweep_trt: (f_out, P r, sum r^2)."""
+    dt, ft = storage_dtype(precision), field_dtype(precision)
+    for t, want in ((f_in, dt), (h, ft)) + (((dm, ft),) if dm is not None else ()):
+        if t.dtype != want or not t.is_cuda or not t.is_contiguous():
+            raise ValueError("stage inputs must be contiguous device tensors of the storage / field type")
+    scratch = scratch or StageScratch(2, n, precision, f_in.device)
+    f_out = torch.empty_like(f_in)
+    pr = torch.empty((3, n, n), dtype=ft, device=f_in.device)
+    ssq = torch.empty((), dtype=torch.float64, device=f_in.device)
+    L.check(L.lib.msc_sweep_trt(n, precision_code(precision), float(a), float(omega_p), float(omega_m), _ptr(f_in),
+                                _dptr(dm), _ptr(h), _ptr(f_out), _ptr(pr), _ptr(ssq), _ptr(scratch.buf),
+                                scratch.nbytes, _stream(stream)), "msc_sweep_trt")
     return f_out, pr, ssq
 
 

@@ -524,6 +524,35 @@ def measure_adjoint(torch, PL, dev, n=256, dt_target=32.0, fd_dirs=1):
             "checkpoint_bytes": int(sum(b.numel() for b in R.checkpoints))}
 
 
+def measure_offdesign(torch, PL, dev, n=128):
+    """Observed contraction (Eq. rho-observed, m = 10) of the shadow-corrected iteration on one interior
+    BDF2 step of the D2Q9 Taylor-Green field, away from the collision operating point: Lambda scanned
+    at nu = 1/6 and nu scanned at Lambda = 1/4 (Section 4.6), general TRT sweep, FP64, eps = 1e-10."""
+    from workloads.fields import tgv2d
+    t_end = nint(0.15 * n * n)
+    dt = t_end / 64
+    p, u = tgv2d(n, 1.0)
+    p_d, u_d = torch.as_tensor(p, device=dev), torch.as_tensor(u, device=dev)
+    L = PL.MscLattice(2, n, "fp64", max_steps=8, hist_cap=1024, device=str(dev))
+    pts = [(1.0 / 6.0, lam) for lam in (1 / 64, 1 / 16, 0.05, 0.1, 0.25, 0.5, 1.0, 2.0, 4.0)]
+    pts += [(nu, 0.25) for nu in (0.3, 0.25, 0.2, 0.14, 0.12, 0.11, 0.1, 0.09, 0.08)]
+    out = []
+    for nu, lam in pts:
+        tp = 3.0 * nu + 0.5
+        wp, wm = 1.0 / tp, 1.0 / (lam / (tp - 0.5) + 0.5)
+        L.set_params(dt=dt, eps=1e-10, nu=nu, kmax=300, omega=(wp, wm))
+        L.init_fields(p_d, u_d)
+        L.march(1)   # BDF1 starter
+        L.march(1)   # the interior BDF2 step
+        st = L.stats()
+        rho = DG.rho_observed(L.residual_history(), 10)
+        out.append({"nu": nu, "Lambda": lam, "omega": [wp, wm], "status": st["status"],
+                    "iters": int(st["inner_total"]), "rho_obs": rho})
+    L.close()
+    return {"workload": f"D2Q9 Taylor-Green N={n} Re=1, dt={dt:.3f} (T_end/64), one interior BDF2 step, "
+                        "shadow correction with the general TRT sweep, FP64", "points": out}
+
+
 def run_ours(args, rank, world, dist):
     import torch
     from paper_2609_39474_b300 import lattice as PL
@@ -556,6 +585,7 @@ def run_ours(args, rank, world, dist):
                 sec.pop("clocks", None)
                 res["secondary"].append(sec)
     res["adjoint"] = None if args.no_secondary else measure_adjoint(torch, PL, dev)
+    res["offdesign"] = None if args.no_secondary else measure_offdesign(torch, PL, dev)
     res["batch"] = None
     if batch_refs is not None:
         pool, refs = batch_refs
@@ -577,6 +607,8 @@ def run_phase(args):
         return {"phase": "batch", **measure_batch(torch, PL, dev)}
     if args.phase == "adjoint":
         return {"phase": "adjoint", **measure_adjoint(torch, PL, dev)}
+    if args.phase == "offdesign":
+        return {"phase": "offdesign", **measure_offdesign(torch, PL, dev)}
     n = args.n
     S, eps = DEFAULT_CANDIDATE.get(n, (64, 1e-8))
     p, u = random_phase(n, 2, 1.0, seed=1, kmax=8)
@@ -728,7 +760,7 @@ def main():
                     help="--phase batch-stage: a batch tiling as JSON (keys sweep_rows, fft_rows, col_lines, "
                          "sweep_ctas_per_sm) instead of autotuning, so that only the timed launches run")
     ap.add_argument("--phase", default="all",
-                    choices=["all", "msc", "msc-stepwise", "sweep", "batch", "batch-stage", "adjoint"],
+                    choices=["all", "msc", "msc-stepwise", "sweep", "batch", "batch-stage", "adjoint", "offdesign"],
                     help="profiling aids: 'msc' runs only the timed MSC marches of the default candidate, "
                          "'msc-stepwise' the same marches driven from the host (one launch per kernel, "
                          "visible to ncu), 'sweep' only the fused-sweep roofline loop, 'batch' only the "
@@ -805,6 +837,7 @@ def main():
         "batch": res["batch"],
         "fp16": res["fp16"],
         "adjoint": res["adjoint"],
+        "offdesign": res["offdesign"],
     }
     print(json.dumps(line))
     if dist is not None:

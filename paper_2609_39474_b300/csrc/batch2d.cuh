@@ -208,14 +208,14 @@ __global__ void __launch_bounds__(kFieldThreads) k_bstep_begin(const BInst<T>* _
     step_begin_range<D2Q9, T>(B.st, B.fbase, B.fstride, B.mbuf, B.h, B.sites, i0, is);
 }
 
-template <typename T>
+template <typename T, bool FORCE>
 __global__ void __launch_bounds__(kFieldThreads) k_bstep_end(const BInst<T>* __restrict__ I,
                                                              const BMap* __restrict__ M) {
     int i;
     size_t i0, is;
     fld_range<T>(M, &i, &i0, &is);
     const BInst<T>& B = I[i];
-    step_end_range<D2Q9, T>(B.st, B.fbase, B.fstride, B.mbuf, B.h, B.sites, i0, is);  // accepted only
+    step_end_range<D2Q9, T, T, FORCE>(B.st, B.fbase, B.fstride, B.mbuf, B.h, B.sites, i0, is);  // accepted only
 }
 
 // m^n = P f^n after a batched explicit march, for the instances that took steps

@@ -20,6 +20,7 @@ struct msc_batch {
     int sweep_grid, row_blocks, row_threads, col_blocks, col_threads, fld_blocks;
     size_t row_smem, col_smem;
     BMap map;  // host copy of the uploaded prefix tables
+    bool graph_force;  // the march graph's step end carries the body-force terms
     cudaGraph_t g_march;
     cudaGraphExec_t x_march;
     cudaGraph_t g_ex;
@@ -244,7 +245,8 @@ int build_batch_march_graph(msc_batch* b) {
                                     dim3(b->col_threads), b->col_smem, a_sp, &err);
     cudaGraphNode_t r2 = add_kernel(body, {cs}, (const void*)k_browfft<T, true, 0>, dim3(b->row_blocks),
                                     dim3(b->row_threads), b->row_smem, a_sp, &err);
-    cudaGraphNode_t en = add_kernel(body, {r2}, (const void*)k_bstep_end<T>, dim3(b->fld_blocks),
+    const void* fn_end = b->graph_force ? (const void*)k_bstep_end<T, true> : (const void*)k_bstep_end<T, false>;
+    cudaGraphNode_t en = add_kernel(body, {r2}, fn_end, dim3(b->fld_blocks),
                                     dim3(kFieldThreads), 0, a_fld, &err);
     void* a_fin[] = {&M, &h_round};
     add_kernel(body, {en}, (const void*)k_bfinish, dim3(1), dim3(kBatchMax), 0, a_fin, &err);
@@ -501,11 +503,20 @@ int msc_batch_march(msc_batch* b, const int* n_steps) {
         if (k > 0 && c->params.replay && k > c->desc.max_steps) return MSC_ERR_ARG;
         s.n[i] = k;
     }
+    bool force = false;
     for (int i = 0; i < b->n_inst; ++i) {
         if (s.n[i] == 0) continue;
         int rc = refresh_tables(b->ctx[i]);
         if (rc) return rc;
+        force |= params_force(b->ctx[i]->params);
     }
+    if (b->x_march && force != b->graph_force) {  // the step-end kernel depends on whether a force acts
+        cudaGraphExecDestroy(b->x_march);
+        cudaGraphDestroy(b->g_march);
+        b->x_march = nullptr;
+        b->g_march = nullptr;
+    }
+    b->graph_force = force;
     if (!b->x_march) {
         int rc = b->precision == MSC_FP64 ? build_batch_march_graph<double>(b) : build_batch_march_graph<float>(b);
         if (rc) return rc;

@@ -178,7 +178,7 @@ __global__ void k_step_begin(const DevState* __restrict__ st, S* __restrict__ fb
 // that step's BDF2 history term h = (4 m^{n+1} - m^n)/(2 dt) and its population warm start
 // (2 f^{n+1} - f^n, or 3 f^{n+1} - 3 f^n + f^{n-1}; Section 3.1) into the free working slot, so
 // that the next k_step_begin has nothing to do.
-template <class L, typename T, typename S = T>
+template <class L, typename T, typename S = T, bool FORCE = true>
 __device__ __forceinline__ void step_end_range(const DevState* __restrict__ st, S* __restrict__ fbase,
                                                size_t fstride, double* __restrict__ mbuf, T* __restrict__ h,
                                                size_t sites, size_t i0, size_t istride) {
@@ -203,8 +203,8 @@ __device__ __forceinline__ void step_end_range(const DevState* __restrict__ st, 
     const T sig = (T)vs->fscale, isig = T(1) / sig;
     const double n1 = 4.0 / (2.0 * dt), n2 = 1.0 / (2.0 * dt);  // BDF2 for the next step
     const double k1 = 0.5 * c1 * inv, k2 = 0.5 * c2 * inv;
-    // body force: (0, F) joins h in the reconstruction and in the next step's h
-    const double fc[4] = {0.0, vs->force[0], vs->force[1], vs->force[2]};
+    // body force: (0, F) joins h in the reconstruction and in the next step's h (FORCE = false: F = 0)
+    const double fc[4] = {0.0, FORCE ? vs->force[0] : 0.0, FORCE ? vs->force[1] : 0.0, FORCE ? vs->force[2] : 0.0};
     const double kf[4] = {0.0, 0.5 * inv * fc[1], 0.5 * inv * fc[2], 0.5 * inv * fc[3]};
 #pragma unroll 2
     for (size_t i = i0; i < sites; i += istride) {
@@ -224,9 +224,10 @@ __device__ __forceinline__ void step_end_range(const DevState* __restrict__ st, 
             // m^{n+1} = (P f + h/2) inv with h = c1 m^n - c2 m^{n-1} + (0, F), constants folded (FP64)
             const size_t o = c * sites + i;
             const double mc = mn[o];
-            const double mnew = fma(k1, mc, fma(-k2, mnm1[o], fma(inv, (double)mom[c], kf[c])));
+            const double mnew = FORCE ? fma(k1, mc, fma(-k2, mnm1[o], fma(inv, (double)mom[c], kf[c])))
+                                      : fma(k1, mc, fma(-k2, mnm1[o], inv * (double)mom[c]));
             mnm1[o] = mnew;
-            if (next) h[o] = (T)fma(n1, mnew, fma(-n2, mc, fc[c]));
+            if (next) h[o] = FORCE ? (T)fma(n1, mnew, fma(-n2, mc, fc[c])) : (T)fma(n1, mnew, -n2 * mc);
         }
         if (next) {
             if (nav == 1) {
@@ -249,11 +250,14 @@ __device__ __forceinline__ void step_end_range(const DevState* __restrict__ st, 
     }
 }
 
-template <class L, typename T, typename S = T>
-__global__ void __launch_bounds__(kFieldThreads) k_step_end(const DevState* __restrict__ st, S* __restrict__ fbase,
+// FP32 storage: six blocks per SM (the FP64 history update keeps the FP64 pipe busy only with
+// enough warps resident)
+template <class L, typename T, typename S = T, bool FORCE = true>
+__global__ void __launch_bounds__(kFieldThreads)
+    k_step_end(const DevState* __restrict__ st, S* __restrict__ fbase,
                                                             size_t fstride, double* __restrict__ mbuf, T* __restrict__ h,
                                                             size_t sites) {
-    step_end_range<L, T, S>(st, fbase, fstride, mbuf, h, sites, blockIdx.x * (size_t)blockDim.x + threadIdx.x,
+    step_end_range<L, T, S, FORCE>(st, fbase, fstride, mbuf, h, sites, blockIdx.x * (size_t)blockDim.x + threadIdx.x,
                          (size_t)gridDim.x * blockDim.x);
 }
 

@@ -63,6 +63,14 @@ bool params_trt(const msc_params& p) {
     return wp != 1.0 || wm != 1.0;
 }
 bool ctx_trt(const msc_ctx* c) { return c->params_set && params_trt(c->params); }
+bool params_force(const msc_params& p) { return p.force[0] != 0.0 || p.force[1] != 0.0 || p.force[2] != 0.0; }
+
+// the step-end kernel of a context: with or without the body-force terms
+template <class L, typename T, typename FS>
+const void* step_end_kernel(const msc_ctx* c) {
+    return c->params_set && params_force(c->params) ? (const void*)k_step_end<L, T, FS, true>
+                                                    : (const void*)k_step_end<L, T, FS, false>;
+}
 
 // the 2D sweep kernel of a context: operating point or general TRT collision
 template <typename T, typename FS, bool EXPLICIT, bool GRAPH>
@@ -291,7 +299,7 @@ int build_march_graph(msc_ctx* c) {
     cudaGraphNode_t wit = add_cond(body_step, {begin}, h_iter, cudaGraphCondTypeWhile, &body_iter, &err);
     if (err != cudaSuccess) { cudaGraphDestroy(g); return MSC_ERR_CUDA; }
     void* a_end[] = {&st, &fbase, (void*)&fstride, &mbuf, &h, &sites};
-    cudaGraphNode_t end = add_kernel(body_step, {wit}, (const void*)k_step_end<L, T, FS>, dim3(fgrid),
+    cudaGraphNode_t end = add_kernel(body_step, {wit}, step_end_kernel<L, T, FS>(c), dim3(fgrid),
                                      dim3(kFieldThreads), 0, a_end, &err);
     void* a_fin[] = {&st, &iters, &max_steps, &h_step, &cond1};
     add_kernel(body_step, {end}, (const void*)k_step_finish, dim3(1), dim3(1), 0, a_fin, &err);
@@ -523,7 +531,10 @@ int run_stepwise(msc_ctx* c, int n_steps) {
                 }
             if (hs.accepted || hs.status != MSC_OK) break;
         }
-        k_step_end<L, T, FS><<<fgrid, kFieldThreads, 0, c->stream>>>(st, fbase, fstride, mbuf, h, c->sites);
+        {
+            void* ea[] = {&st, &fbase, (void*)&fstride, &mbuf, &h, (void*)&c->sites};
+            CK(cudaLaunchKernel(step_end_kernel<L, T, FS>(c), dim3(fgrid), dim3(kFieldThreads), ea, 0, c->stream));
+        }
         k_step_finish<<<1, 1, 0, c->stream>>>(st, at<int>(c, c->lay.iters), c->desc.max_steps, none, 0);
         CK(cudaGetLastError());
         rc = read_state(c, &hs);
@@ -619,7 +630,8 @@ int msc_set_params(msc_ctx* c, const msc_params* p) {
         return MSC_ERR_ARG;
     if (params_trt(*p) && c->desc.dim != 2) return MSC_ERR_ARG;  // the general TRT sweep exists for D2Q9
     // the shadow solve bakes nu into the graph, the collision kind picks the sweep kernel: rebuild
-    const bool kind_changes = c->params_set && params_trt(*p) != params_trt(c->params);
+    const bool kind_changes = c->params_set && (params_trt(*p) != params_trt(c->params) ||
+                                                params_force(*p) != params_force(c->params));
     if (c->params_set && (p->nu != c->params.nu || kind_changes) && c->x_march) {
         cudaGraphExecDestroy(c->x_march);
         cudaGraphDestroy(c->g_march);

@@ -232,8 +232,9 @@ __device__ __forceinline__ double sweep2_unit(const S* fin, const T* dm, const T
     return ssq;
 }
 
+// FP32 operating-point sweeps keep six blocks (24 warps) per SM: the kernel is bound by load latency
 template <typename T, typename S, bool EXPLICIT, bool GRAPH, bool TRT = false>
-__global__ void __launch_bounds__(kSweepWarps * 32) k_sweep2(Sweep2Args<T, S> A) {
+__global__ void __launch_bounds__(kSweepWarps * 32, sizeof(T) == 4 && !TRT ? 6 : 1) k_sweep2(Sweep2Args<T, S> A) {
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int n = A.n;

@@ -282,6 +282,13 @@ int msc_adjoint_step(msc_ctx* ctx, int q, const double* m_new, const double* m_c
                      const double* abar_new, double* abar_cur, double* abar_prev, double* dforce, double eps,
                      int kmax, msc_adjoint_stats* out);
 
+/* Self-check of the library's binary32 <-> binary64 conversions (integer-pipe implementations of the
+   IEEE 754 widening and round-to-nearest-even narrowing used by the FP32-storage step kernels)
+   against the hardware conversions on blocks x 256 x per_thread random patterns; *mismatches
+   receives the count (0 expected).  Allocates 4 bytes of device memory for the count and
+   synchronises the device. */
+int msc_selftest_conversions(int blocks, int per_thread, unsigned long long seed, int* mismatches);
+
 /* msc_save_state / msc_load_state with the blob in device memory (same layout; checkpoints of a
    reverse pass stay on the device).  Synchronise the stream. */
 int msc_save_state_device(msc_ctx* ctx, void* dev_blob, size_t* bytes);

@@ -98,6 +98,7 @@ _SIG = {
     "msc_sweep_trt": (_i, [_i, _i, _d, _d, _d, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "msc_adjoint_step": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _d, _i, ctypes.POINTER(AdjointStats)]),
     "msc_save_state_device": (_i, [_vp, _vp, ctypes.POINTER(_sz)]),
+    "msc_selftest_conversions": (_i, [_i, _i, ctypes.c_ulonglong, ctypes.POINTER(_i)]),
     "msc_load_state_device": (_i, [_vp, _vp, _sz]),
     "msc_batch_workspace_bytes": (_sz, [ctypes.POINTER(_vp), _i]),
     "msc_batch_create": (_i, [ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i, _vp, _sz, _vp]),

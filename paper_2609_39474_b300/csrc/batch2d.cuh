@@ -76,7 +76,7 @@ __device__ __forceinline__ int find_inst(const int* __restrict__ off, int n_inst
     return lo;
 }
 
-__device__ __forceinline__ bool inst_active(const volatile DevState* vs) {
+__device__ __forceinline__ bool inst_active(const DevState* vs) {
     return vs->params_ok && vs->status == MSC_OK && vs->steps_target > 0;
 }
 
@@ -99,22 +99,21 @@ __global__ void __launch_bounds__(kSweepWarps * 32) k_bsweep2(const BInst<T>* __
         T a, inv;
         int lift;
         if (MODE == 0) {
-            const volatile DevState* vs = B.st;
+            const DevState* vs = B.st;
             if (!inst_active(vs)) continue;
             fin = B.fbase + (size_t)vs->slot_cur * B.fstride;
             fout = B.fbase + (size_t)vs->slot_nxt * B.fstride;
-            const double ad = vs->a;
-            a = (T)ad;
-            inv = (T)(1.0 / (1.0 + ad / 2.0));
+            a = (T)vs->a;
+            inv = (T)vs->inv_a;
             lift = vs->lift;
         } else if (MODE == 1) {
             fin = B.t_fin;
             fout = B.t_fout;
             a = (T)A.a;
-            inv = (T)(1.0 / (1.0 + A.a / 2.0));
+            inv = (T)A.inv;
             lift = 1;
         } else {
-            const volatile DevState* vs = B.st;
+            const DevState* vs = B.st;
             if (vs->ex_loops_left <= ex_node) continue;
             const int sa = vs->ex_a, sb = vs->ex_b;
             fin = B.fbase + (size_t)((ex_node & 1) ? sb : sa) * B.fstride;
@@ -164,7 +163,7 @@ __device__ __forceinline__ bool spec_inst(const BInst<T>& B, Spec2Args<T>* A) {
         A->coef = nullptr;
         return true;
     }
-    const volatile DevState* vs = B.st;
+    const DevState* vs = B.st;
     return inst_active(vs) && vs->lift;
 }
 

@@ -121,11 +121,13 @@ BInst<T> make_inst(msc_batch* b, int i, double* upart, unsigned int* ucount, dou
     B.sw.hb = b->tun.sweep_rows[cl];
     B.sw.nrowblk = n / B.sw.hb;
     B.sw.a = c->params_set ? 3.0 / (2.0 * c->params.dt) : 1.0;
+    B.sw.inv = 1.0 / (1.0 + B.sw.a / 2.0);
     B.sp = spec3_args<T>(n, c->logn, B.sw.a, c->params_set ? c->params.nu : 1.0 / 6.0, at<T>(c, c->lay.pr),
                          at<C>(c, c->lay.spec), at<T>(c, c->lay.dm), at<C>(c, c->lay.tw), at<DevState>(c, c->lay.state),
                          at<double>(c, c->lay.coef));
     B.sp.nf = 3;
     B.sp.rows = n;
+    B.sp.nscale = 1.0 / ((double)n * n);
     B.sp.P = b->tun.fft_rows[cl];
     B.sp.G = b->tun.col_lines[cl];
     B.st = at<DevState>(c, c->lay.state);

@@ -55,7 +55,10 @@ struct D3Q19 {
 
 // ---- device-resident march state -------------------------------------------------------------
 // One instance per context, in the workspace.  Scalars written by single-thread control kernels
-// and by the last block of the sweep; everything else reads them at kernel start.
+// and by the last block of the sweep; everything else reads them at kernel start with ordinary
+// (L1-cached) loads: a kernel that writes the state does so only after every thread of it has
+// read the fields it uses, and the caches start clean at every launch.  (Uncached reads of the
+// same few lines by every thread of a grid queue up on one L2 slice.)
 struct DevState {
     // parameters (set by msc_set_params)
     double nu, dt, eps;
@@ -76,6 +79,12 @@ struct DevState {
     int m_cur, m_prev;      // moment history slots of m^n, m^{n-1}
     int q;                  // BDF order of the current step
     double a;               // a_q
+    // constants of the current step, formed once by the single-thread control kernels (an FP64
+    // division costs ~10 FP64 instructions on a pipe that runs at ~1/58 of the FP32 rate)
+    double inv_a;           // 1 / (1 + a_q / 2)
+    double c1, c2;          // h_q = c1 m^n - c2 m^{n-1}
+    double n1, n2;          // BDF2 coefficients 4 / (2 dt), 1 / (2 dt) of the next step
+    double isig;            // 1 / fscale
     int iter;               // inner iterations done in the current step
     int lift;               // next sweep applies f = f_cur + E dm
     int accepted;           // current step accepted
@@ -119,6 +128,42 @@ inline bool valid_lattice(int dim, int n, int precision) {
     if (dim == 2) return n <= (precision == MSC_FP64 ? 2048 : 4096);
     if (dim == 3) return precision != MSC_FP16 && n <= (precision == MSC_FP64 ? 128 : 256);
     return false;
+}
+
+// binary32 <-> binary64 conversions on the integer pipe (IEEE 754 formats; B300's FP64 pipe, which
+// executes the conversion instructions, runs at ~1/58 of the FP32 rate).  Same results as the
+// hardware conversions; values outside the normal ranges take the hardware path.
+// widen: exact.  The exponent field is re-biased by 1023 - 127 = 896, the mantissa moves up 29 bits.
+__device__ __forceinline__ double widen_f32(float x) {
+    const unsigned int b = __float_as_uint(x);
+    const unsigned int mag = b & 0x7fffffffu;
+    if (mag - 0x00800000u >= 0x7f000000u) return (double)x;  // zero, subnormal, inf, nan
+    const unsigned long long d = ((unsigned long long)(b >> 31) << 63) |
+                                 (((unsigned long long)mag + (896ull << 23)) << 29);
+    return __longlong_as_double((long long)d);
+}
+// narrow: round to nearest, ties to even, for results in the normal binary32 range (double
+// exponents 897 .. 1150); a carry out of the mantissa increments the exponent (to inf at the top).
+__device__ __forceinline__ float narrow_f64(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned long long mag = b & 0x7fffffffffffffffull;
+    const unsigned int e = (unsigned int)(mag >> 52);
+    if (e - 897u > 253u) return (float)x;  // zero, binary32 subnormal or overflow range, inf, nan
+    const unsigned long long t = mag - (896ull << 52);
+    unsigned int r = (unsigned int)(t >> 29);
+    const unsigned int rem = (unsigned int)t & 0x1fffffffu;
+    r += (rem > 0x10000000u) | ((rem == 0x10000000u) & (r & 1u));
+    return __uint_as_float(((unsigned int)(b >> 63) << 31) | r);
+}
+template <typename T>
+__device__ __forceinline__ double to_f64(T x) {
+    if constexpr (std::is_same<T, float>::value) return widen_f32(x);
+    else return (double)x;
+}
+template <typename T>
+__device__ __forceinline__ T from_f64(double x) {
+    if constexpr (std::is_same<T, float>::value) return narrow_f64(x);
+    else return (T)x;
 }
 
 // bytes of one stored population value and of one working-field value (h, P r, dm)

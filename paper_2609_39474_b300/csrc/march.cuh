@@ -20,16 +20,29 @@ __device__ __forceinline__ double cdotu(int k, const double* u) {
     return s;
 }
 
+// The BDF history term h = c1 m_a - c2 m_b + f_c (Eq. bdf2 plus the body force) in the working-field
+// type: FP64 storage evaluates it in FP64; FP32 / FP16 storage (h is stored in FP32) evaluates it in
+// FP32 from the history rounded to FP32, which keeps FP64 instructions (~1/58 of the FP32 rate on
+// B300) to the history update itself.  Both step kernels use this one formula, so a march resumed
+// from a saved state repeats the uninterrupted march bit for bit.
+template <typename T>
+__device__ __forceinline__ T bdf_history(double c1, double ma, double c2, double mb, double fc) {
+    if constexpr (std::is_same<T, float>::value)
+        return fmaf((float)c1, narrow_f64(ma), fmaf(-(float)c2, narrow_f64(mb), (float)fc));
+    else
+        return (T)fma(c1, ma, fma(-c2, mb, fc));
+}
+
 // storage scale of the populations: from the state when there is one, else 1
 __device__ __forceinline__ double pop_scale(const DevState* st) {
-    return st ? ((const volatile DevState*)st)->fscale : 1.0;
+    return st ? st->fscale : 1.0;
 }
 
 // f = f_eq(p_hat, u)   (Eq. feq); p and u are double fields, f in the storage type S
 template <class L, typename S>
 __global__ void k_equilibrium(const double* __restrict__ p, const double* __restrict__ u,
                               S* __restrict__ f, size_t sites, const DevState* st = nullptr) {
-    const double isig = 1.0 / pop_scale(st);
+    const double isig = st ? st->isig : 1.0;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < sites;
          i += (size_t)gridDim.x * blockDim.x) {
         double uv[3] = {0.0, 0.0, 0.0};
@@ -86,6 +99,7 @@ __global__ void k_set_scale(DevState* st) {
         sig = ldexp(1.0, e);
     }
     st->fscale = sig;
+    st->isig = 1.0 / sig;
 }
 
 // m = P f in double (Eq. moments); optionally a second copy
@@ -123,7 +137,7 @@ template <class L, typename T, typename S = T>
 __device__ __forceinline__ void step_begin_range(const DevState* __restrict__ st, S* __restrict__ fbase,
                                                  size_t fstride, const double* __restrict__ mbuf,
                                                  T* __restrict__ h, size_t sites, size_t i0, size_t istride) {
-    const volatile DevState* vs = st;
+    const DevState* vs = st;
     if (vs->prepared) return;  // formed by the previous step's k_step_end
     const int q = vs->q;
     const double dt = vs->dt;
@@ -135,15 +149,16 @@ __device__ __forceinline__ void step_begin_range(const DevState* __restrict__ st
     const S* f1 = fbase + (size_t)vs->slot_fn[1] * fstride;
     const S* f2 = fbase + (size_t)vs->slot_fn[2] * fstride;
     S* ft = fbase + (size_t)vs->slot_cur * fstride;
-    const double c1 = q == 1 ? 1.0 / dt : 4.0 / (2.0 * dt);
-    const double c2 = q == 1 ? 0.0 : 1.0 / (2.0 * dt);
-    const T sig = (T)vs->fscale, isig = T(1) / sig;
+    const double c1 = vs->c1, c2 = vs->c2;
+    (void)q;
+    (void)dt;
+    const T sig = (T)vs->fscale, isig = (T)vs->isig;
     const double fc[4] = {0.0, vs->force[0], vs->force[1], vs->force[2]};
     for (size_t i = i0; i < sites; i += istride) {
 #pragma unroll
         for (int c = 0; c <= L::D; ++c) {  // h = c1 m^n - c2 m^{n-1} + (0, F), as k_step_end forms it
             const size_t o = c * sites + i;
-            h[o] = (T)fma(c1, mn[o], fma(-c2, mnm1[o], fc[c]));
+            h[o] = bdf_history<T>(c1, mn[o], c2, mnm1[o], fc[c]);
         }
         if (nav == 1) {
 #pragma unroll
@@ -182,38 +197,52 @@ template <class L, typename T, typename S = T, bool FORCE = true>
 __device__ __forceinline__ void step_end_range(const DevState* __restrict__ st, S* __restrict__ fbase,
                                                size_t fstride, double* __restrict__ mbuf, T* __restrict__ h,
                                                size_t sites, size_t i0, size_t istride) {
-    const volatile DevState* vs = st;
+    const DevState* vs = st;
     if (!vs->accepted) return;
-    const int q = vs->q;
-    const double dt = vs->dt;
-    const double a = vs->a;
-    const double inv = 1.0 / (1.0 + a / 2.0);
+    const double inv = vs->inv_a;
     const size_t mstride = (size_t)(L::D + 1) * sites;
-    const double* mn = mbuf + (size_t)vs->m_cur * mstride;
-    double* mnm1 = mbuf + (size_t)vs->m_prev * mstride;
-    const S* ft = fbase + (size_t)vs->slot_cur * fstride;
-    const double c1 = q == 1 ? 1.0 / dt : 4.0 / (2.0 * dt);
-    const double c2 = q == 1 ? 0.0 : 1.0 / (2.0 * dt);
+    const double c1 = vs->c1, c2 = vs->c2;
     const bool next = vs->status == MSC_OK && vs->steps_target > 1;
     int nav = vs->n_avail + 1 < 3 ? vs->n_avail + 1 : 3;  // accepted states after rotation
     if (nav > vs->warm_order) nav = vs->warm_order;
-    const S* f0 = fbase + (size_t)vs->slot_fn[0] * fstride;
-    const S* f1 = fbase + (size_t)vs->slot_fn[1] * fstride;
-    S* trial = fbase + (size_t)vs->slot_nxt * fstride;
-    const T sig = (T)vs->fscale, isig = T(1) / sig;
-    const double n1 = 4.0 / (2.0 * dt), n2 = 1.0 / (2.0 * dt);  // BDF2 for the next step
+    if (!next) nav = 0;
+    // the ring slots, the moment slots and h never overlap: no store below aliases a load
+    const double* __restrict__ mn = mbuf + (size_t)vs->m_cur * mstride;
+    double* __restrict__ mnm1 = mbuf + (size_t)vs->m_prev * mstride;
+    const S* __restrict__ ft = fbase + (size_t)vs->slot_cur * fstride;
+    const S* __restrict__ f0 = fbase + (size_t)vs->slot_fn[0] * fstride;
+    const S* __restrict__ f1 = fbase + (size_t)vs->slot_fn[1] * fstride;
+    S* __restrict__ trial = fbase + (size_t)vs->slot_nxt * fstride;
+    const T sig = (T)vs->fscale, isig = (T)vs->isig;
+    const double n1 = vs->n1, n2 = vs->n2;  // BDF2 for the next step
     const double k1 = 0.5 * c1 * inv, k2 = 0.5 * c2 * inv;
     // body force: (0, F) joins h in the reconstruction and in the next step's h (FORCE = false: F = 0)
     const double fc[4] = {0.0, FORCE ? vs->force[0] : 0.0, FORCE ? vs->force[1] : 0.0, FORCE ? vs->force[2] : 0.0};
     const double kf[4] = {0.0, 0.5 * inv * fc[1], 0.5 * inv * fc[2], 0.5 * inv * fc[3]};
 #pragma unroll 2
     for (size_t i = i0; i < sites; i += istride) {
-        T fv[L::Q];
+        // every load of the site is issued before any arithmetic or store (one memory latency per site)
+        T fv[L::Q], g0[L::Q], g1[L::Q];
+        double mcv[L::D + 1], mpv[L::D + 1];
+#pragma unroll
+        for (int k = 0; k < L::Q; ++k) fv[k] = ld_pop<T, S>(ft, k * sites + i, sig);
+        if (nav >= 2) {
+#pragma unroll
+            for (int k = 0; k < L::Q; ++k) g0[k] = ld_pop<T, S>(f0, k * sites + i, sig);
+        }
+        if (nav == 3) {
+#pragma unroll
+            for (int k = 0; k < L::Q; ++k) g1[k] = ld_pop<T, S>(f1, k * sites + i, sig);
+        }
+#pragma unroll
+        for (int c = 0; c <= L::D; ++c) {
+            mcv[c] = mn[c * sites + i];
+            mpv[c] = mnm1[c * sites + i];
+        }
         T mom[4] = {T(0), T(0), T(0), T(0)};
 #pragma unroll
         for (int k = 0; k < L::Q; ++k) {
-            const T v = ld_pop<T, S>(ft, k * sites + i, sig);
-            fv[k] = v;
+            const T v = fv[k];
             mom[0] += v;
             if (L::cx(k)) mom[1] += T(L::cx(k)) * v;
             if (L::cy(k)) mom[2] += T(L::cy(k)) * v;
@@ -223,29 +252,22 @@ __device__ __forceinline__ void step_end_range(const DevState* __restrict__ st, 
         for (int c = 0; c <= L::D; ++c) {
             // m^{n+1} = (P f + h/2) inv with h = c1 m^n - c2 m^{n-1} + (0, F), constants folded (FP64)
             const size_t o = c * sites + i;
-            const double mc = mn[o];
-            const double mnew = FORCE ? fma(k1, mc, fma(-k2, mnm1[o], fma(inv, (double)mom[c], kf[c])))
-                                      : fma(k1, mc, fma(-k2, mnm1[o], inv * (double)mom[c]));
+            const double mc = mcv[c];
+            const double md = to_f64<T>(mom[c]);
+            const double mnew = FORCE ? fma(k1, mc, fma(-k2, mpv[c], fma(inv, md, kf[c])))
+                                      : fma(k1, mc, fma(-k2, mpv[c], inv * md));
             mnm1[o] = mnew;
-            if (next) h[o] = FORCE ? (T)fma(n1, mnew, fma(-n2, mc, fc[c])) : (T)fma(n1, mnew, -n2 * mc);
+            if (next) h[o] = bdf_history<T>(n1, mnew, n2, mc, fc[c]);
         }
-        if (next) {
-            if (nav == 1) {
+        if (nav == 1) {
 #pragma unroll
-                for (int k = 0; k < L::Q; ++k) st_pop<T, S>(trial, k * sites + i, fv[k], isig);
-            } else if (nav == 2) {
+            for (int k = 0; k < L::Q; ++k) st_pop<T, S>(trial, k * sites + i, fv[k], isig);
+        } else if (nav == 2) {
 #pragma unroll
-                for (int k = 0; k < L::Q; ++k) {
-                    const size_t o = k * sites + i;
-                    st_pop<T, S>(trial, o, T(2) * fv[k] - ld_pop<T, S>(f0, o, sig), isig);
-                }
-            } else {
+            for (int k = 0; k < L::Q; ++k) st_pop<T, S>(trial, k * sites + i, T(2) * fv[k] - g0[k], isig);
+        } else if (nav == 3) {
 #pragma unroll
-                for (int k = 0; k < L::Q; ++k) {
-                    const size_t o = k * sites + i;
-                    st_pop<T, S>(trial, o, T(3) * (fv[k] - ld_pop<T, S>(f0, o, sig)) + ld_pop<T, S>(f1, o, sig), isig);
-                }
-            }
+            for (int k = 0; k < L::Q; ++k) st_pop<T, S>(trial, k * sites + i, T(3) * (fv[k] - g0[k]) + g1[k], isig);
         }
     }
 }
@@ -302,9 +324,19 @@ __global__ void k_solve_tables(double* coef, int dim, int n, double dt, double n
 
 // ---- single-thread control kernels ------------------------------------------------------------
 
+__device__ inline void set_step_constants(DevState* st) {
+    const double dt = st->dt;
+    st->a = st->q == 1 ? 1.0 / dt : 3.0 / (2.0 * dt);
+    st->inv_a = 1.0 / (1.0 + st->a / 2.0);
+    st->c1 = st->q == 1 ? 1.0 / dt : 4.0 / (2.0 * dt);
+    st->c2 = st->q == 1 ? 0.0 : 1.0 / (2.0 * dt);
+}
+
 __global__ void k_set_params(DevState* st, msc_params p) {
     st->nu = p.nu;
     st->dt = p.dt;
+    st->n1 = 4.0 / (2.0 * p.dt);
+    st->n2 = 1.0 / (2.0 * p.dt);
     st->eps = p.eps;
     st->kmax = p.kmax;
     st->nmin = p.nmin;
@@ -339,6 +371,7 @@ __global__ void k_reset_history(DevState* st) {
     st->R_last = 0.0;
     st->prepared = 0;
     st->fscale = 1.0;
+    st->isig = 1.0;
     st->fmax_bits = 0ull;
 }
 
@@ -376,7 +409,7 @@ __device__ inline bool slot_in_history(const DevState* st, int s) {
 __device__ inline void step_setup(DevState* st) {
     if (st->prepared) return;
     st->q = st->steps_done == 0 ? 1 : 2;
-    st->a = st->q == 1 ? 1.0 / st->dt : 3.0 / (2.0 * st->dt);
+    set_step_constants(st);
     st->iter = 0;
     st->accepted = 0;
     st->lift = 0;
@@ -419,7 +452,7 @@ __device__ inline unsigned int step_finish(DevState* st, int* iters_out, int max
     const int trial = st->slot_nxt;
     if (go) {
         st->q = 2;
-        st->a = 3.0 / (2.0 * st->dt);
+        set_step_constants(st);
         st->iter = 0;
         st->accepted = 0;
         st->lift = 0;
@@ -447,7 +480,7 @@ template <class L, typename T, typename S = T>
 __device__ __forceinline__ void moments_state_range(const DevState* __restrict__ st, const S* __restrict__ fbase,
                                                     size_t fstride, double* __restrict__ mbuf, size_t sites,
                                                     size_t i0, size_t istride) {
-    const volatile DevState* vs = st;
+    const DevState* vs = st;
     const S* f = fbase + (size_t)vs->slot_fn[0] * fstride;
     const size_t mstride = (size_t)(L::D + 1) * sites;
     const double sig = vs->fscale;

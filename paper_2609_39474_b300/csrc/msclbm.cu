@@ -227,6 +227,7 @@ void add_spectral_nodes(msc_ctx* c, cudaGraph_t g, cudaError_t* err) {
         S.nf = 3;
         S.rows = n;
         S.P = rg.P;
+        S.nscale = 1.0 / ((double)n * n);
         cudaGraphNode_t n1 = add_kernel(g, {}, (const void*)k_rowfft_fwd<T>, dim3(rg.blocks), dim3(rg.threads),
                                         spec_row_smem<T>(n, rg.P), args, err);
         cudaGraphNode_t n2 = add_kernel(g, {n1}, (const void*)k_colsolve<T>, dim3(n / 4 + 1),
@@ -497,6 +498,7 @@ int run_stepwise(msc_ctx* c, int n_steps) {
         S.nf = 3;
         S.rows = n;
         S.P = rg.P;
+        S.nscale = 1.0 / ((double)n * n);
         spec[0] = {(const void*)k_rowfft_fwd<T>, dim3(rg.blocks), dim3(rg.threads), spec_row_smem<T>(n, rg.P)};
         spec[1] = {(const void*)k_colsolve<T>, dim3(n / 4 + 1), dim3(spec2_col_threads(n)), spec2_col_smem<T>(n)};
         spec[2] = {(const void*)k_rowfft_inv<T>, dim3(rg.blocks), dim3(rg.threads), spec_row_smem<T>(n, rg.P)};
@@ -865,6 +867,7 @@ int msc_load_state(msc_ctx* c, const void* blob, size_t bytes) {
     s.status = MSC_OK;
     s.prepared = 0;
     s.fscale = ldexp(1.0, hdr[5]);
+    s.isig = 1.0 / s.fscale;
     CK(cudaMemcpy(c->ws + c->lay.state, &s, sizeof(DevState), cudaMemcpyHostToDevice));
     c->fields_set = true;
     return MSC_OK;
@@ -920,6 +923,7 @@ int stage_sweep(int dim, int n, double a, const void* fin, const void* dm, const
         A.fout = (FS*)fout;
         A.pr = (T*)pr;
         A.a = a;
+        A.inv = 1.0 / (1.0 + a / 2.0);
         A.fscale = 1.0;
         A.omega_p = wp;
         A.omega_m = wm;
@@ -946,6 +950,7 @@ int stage_sweep(int dim, int n, double a, const void* fin, const void* dm, const
         A.fout = (T*)fout;
         A.pr = (T*)pr;
         A.a = a;
+        A.inv = 1.0 / (1.0 + a / 2.0);
         A.lift = dm != nullptr;
         A.sumsq_out = sumsq;
         A.partial = S.partial;
@@ -981,6 +986,8 @@ int stage_shadow(int dim, int n, double a, double nu, const void* pr, void* dm, 
         A.P = rg.P;
         A.a = a;
         A.nu = nu;
+        A.kunit = 6.283185307179586476925286766559 / (double)n;
+        A.nscale = 1.0 / ((double)n * n);
         A.st = nullptr;
         k_rowfft_fwd<T><<<rg.blocks, rg.threads, spec_row_smem<T>(n, rg.P), stream>>>(A);
         k_colsolve<T><<<n / 4 + 1, spec2_col_threads(n), spec2_col_smem<T>(n), stream>>>(A);

@@ -35,6 +35,8 @@ struct Spec2Args {
     int nf;              // number of fields (d + 1)
     int rows;            // lines of length n per field (n in 2D, n^2 in 3D)
     double a, nu;
+    double kunit;        // 2 pi / n (formed on the host)
+    double nscale;       // 1 / N_Omega (formed on the host)
     const DevState* st;  // graph mode: a and q from the state
     const double* coef;  // graph mode: per-mode solve coefficients for q = 1, 2 (k_solve_tables)
 };
@@ -42,7 +44,7 @@ struct Spec2Args {
 // pick the coefficient table of the current BDF order (graph mode) or none (stage calls)
 __device__ inline const double* solve_table(const double* coef, const DevState* st, int dim, int n) {
     if (!coef) return nullptr;
-    const int q = ((const volatile DevState*)st)->q;
+    const int q = st->q;
     return coef + (size_t)(q - 1) * 4 * solve_modes(dim, n);
 }
 
@@ -243,10 +245,10 @@ __device__ __forceinline__ void colsolve_block(const Spec2Args<T>& A, int bid, i
     }
     __syncthreads();
     fft_stockham<C, false>(s, n, logn, 3 * G, A.tw);
-    const double a = A.st ? ((const volatile DevState*)A.st)->a : A.a;
+    const double a = A.st ? A.st->a : A.a;
     const double* tab = solve_table(A.coef, A.st, 2, n);
-    const double two_pi_n = 6.283185307179586476925286766559 / (double)n;
-    const double scale = 1.0 / ((double)n * (double)n);
+    const double two_pi_n = A.kunit;
+    const double scale = A.nscale;
     for (int t = threadIdx.x; t < gn; t += blockDim.x) {
         const int g = t >> logn;
         const int jy = t & (n - 1);

@@ -98,10 +98,10 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 384 : 768) k_zsolve(Spec2Args
     }
     __syncthreads();
     fft_stockham<C, false>(s, n, logn, 4 * G, A.tw);
-    const double a = A.st ? ((const volatile DevState*)A.st)->a : A.a;
+    const double a = A.st ? A.st->a : A.a;
     const double* tab = solve_table(A.coef, A.st, 3, n);
-    const double two_pi_n = 6.283185307179586476925286766559 / (double)n;
-    const double scale = 1.0 / ((double)n * (double)n * (double)n);
+    const double two_pi_n = A.kunit;
+    const double scale = A.nscale;
     for (int t = threadIdx.x; t < G * n; t += blockDim.x) {
         const int g = t >> logn;
         const int jz = t & (n - 1);
@@ -193,6 +193,8 @@ inline Spec2Args<T> spec3_args(int n, int logn, double a, double nu, const T* pr
     A.rows = n * n;
     A.a = a;
     A.nu = nu;
+    A.kunit = 6.283185307179586476925286766559 / (double)n;
+    A.nscale = 1.0 / ((double)n * (double)n * (double)n);  // 3D; the 2D callers replace it
     A.st = st;
     spec3_pass_args<T>(n, &A, 0);
     return A;

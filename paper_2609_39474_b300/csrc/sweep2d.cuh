@@ -29,6 +29,7 @@ struct Sweep2Args {
     S* fout;
     T* pr;
     double a;
+    double inv;     // stateless mode: 1 / (1 + a/2), formed on the host
     double fscale;  // stateless mode: population storage scale (FP16 storage holds f / fscale)
     double omega_p, omega_m;  // stateless mode: TRT rates of the general collision (TRT kernels only)
     int lift;
@@ -246,13 +247,13 @@ __global__ void __launch_bounds__(kSweepWarps * 32, sizeof(T) == 4 && !TRT ? 6 :
     S* fout = A.fout;
     T* pr = A.pr;
     T a = (T)A.a;
-    T inv = (T)(1.0 / (1.0 + A.a / 2.0));
+    T inv = (T)A.inv;
     int lift = A.lift;
-    double fs = A.fscale;
+    double fs = A.fscale, ifs = 1.0;  // stateless FP16 calls use fscale = 1
     double wpd = A.omega_p, wmd = A.omega_m;
     if (GRAPH) {
-        const volatile DevState* vs = A.st;
-        if constexpr (!std::is_same<S, T>::value) fs = vs->fscale;
+        const DevState* vs = A.st;
+        if constexpr (!std::is_same<S, T>::value) { fs = vs->fscale; ifs = vs->isig; }
         if constexpr (TRT) { wpd = vs->omega_p; wmd = vs->omega_m; }
         if (EXPLICIT) {
             const int sa = vs->ex_a, sb = vs->ex_b;
@@ -267,9 +268,8 @@ __global__ void __launch_bounds__(kSweepWarps * 32, sizeof(T) == 4 && !TRT ? 6 :
         } else {
             fin = A.fbase + (size_t)vs->slot_cur * A.fstride;
             fout = A.fbase + (size_t)vs->slot_nxt * A.fstride;
-            const double ad = vs->a;
-            a = (T)ad;
-            inv = (T)(1.0 / (1.0 + ad / 2.0));
+            a = (T)vs->a;
+            inv = (T)vs->inv_a;
             lift = vs->lift;
         }
     }
@@ -278,7 +278,7 @@ __global__ void __launch_bounds__(kSweepWarps * 32, sizeof(T) == 4 && !TRT ? 6 :
     double ssq = 0.0;
     if (unit < A.nstrips * A.nrowblk)  // warp-uniform
         ssq = sweep2_unit<T, S, EXPLICIT, TRT>(fin, dm, hh, fout, pr, a, inv, lift, n, A.hb, unit % A.nstrips,
-                                               unit / A.nstrips, lane, (T)fs, (T)(1.0 / fs), (T)wpd, (T)wmd);
+                                               unit / A.nstrips, lane, (T)fs, (T)ifs, (T)wpd, (T)wmd);
     if (EXPLICIT) return;
 
     // ---- residual norm: block partials, last block reduces in a fixed order ----

@@ -29,6 +29,7 @@ struct Sweep3Args {
     T* fout;
     T* pr;
     double a;
+    double inv;  // stateless mode: 1 / (1 + a/2), formed on the host
     int lift;
     double* sumsq_out;
     double* partial;
@@ -87,10 +88,10 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 512) k_sweep3(Sweep3Arg
     T* fout = A.fout;
     T* pr = A.pr;
     T a = (T)A.a;
-    T inv = (T)(1.0 / (1.0 + A.a / 2.0));
+    T inv = (T)A.inv;
     int lift = A.lift;
     if (GRAPH) {
-        const volatile DevState* vs = A.st;
+        const DevState* vs = A.st;
         if (EXPLICIT) {
             const int sa = vs->ex_a, sb = vs->ex_b;
             fin = A.fbase + (size_t)(A.ex_dir ? sb : sa) * A.fstride;
@@ -104,9 +105,8 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 512) k_sweep3(Sweep3Arg
         } else {
             fin = A.fbase + (size_t)vs->slot_cur * A.fstride;
             fout = A.fbase + (size_t)vs->slot_nxt * A.fstride;
-            const double ad = vs->a;
-            a = (T)ad;
-            inv = (T)(1.0 / (1.0 + ad / 2.0));
+            a = (T)vs->a;
+            inv = (T)vs->inv_a;
             lift = vs->lift;
         }
     }

@@ -66,6 +66,7 @@ int sweep2_noalloc(int n, double a, const void* fin, const void* dm, const void*
     A.fout = (T*)fout;
     A.pr = (T*)pr;
     A.a = a;
+    A.inv = 1.0 / (1.0 + a / 2.0);
     A.fscale = 1.0;
     A.lift = dm != nullptr;
     A.sumsq_out = sumsq;

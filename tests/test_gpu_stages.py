@@ -119,3 +119,13 @@ def test_stage_argument_checks():
         PL.sweep(2, 16, "fp64", -1.0, f, torch.zeros((3, 16, 16), dtype=torch.float64, device="cuda"))
     with pytest.raises(ValueError):
         PL.sweep(2, 16, "fp32", 0.1, f, torch.zeros((3, 16, 16), dtype=torch.float64, device="cuda"))
+
+
+def test_integer_pipe_conversions_match_the_hardware():
+    # the step kernels' binary32 <-> binary64 conversions (widening, round-to-nearest-even
+    # narrowing) against CUDA's conversions on 16 M random patterns each, ties included
+    import ctypes
+    from paper_2609_39474_b300 import _lib as L
+    bad = ctypes.c_int(-1)
+    assert L.lib.msc_selftest_conversions(64, 1024, 12345, ctypes.byref(bad)) == 0
+    assert bad.value == 0

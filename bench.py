@@ -41,7 +41,7 @@ S_LIST = [4, 8, 16, 32, 64, 128, 256]
 EPS_LIST = [1e-6, 1e-8, 1e-10]
 KMAX = 300
 # candidate the reference arm uses (the matched-gate winner of the GPU candidate search at N = 1024)
-DEFAULT_CANDIDATE = {1024: (64, 1e-8), 256: (32, 1e-8)}
+DEFAULT_CANDIDATE = {1024: (16, 1e-6), 256: (128, 1e-6)}
 SWEEP_BYTES_PER_SITE_FP32 = 2 * 9 * 4 + 3 * 4 + 3 * 4 + 3 * 4  # f in/out, h, lifted dm, P r
 SWEEP_BYTES_PER_SITE_FP16 = 2 * 9 * 2 + 3 * 4 + 3 * 4 + 3 * 4  # binary16 f in/out, FP32 h, dm, P r
 ROOF_N = 4096  # out-of-L2 size for the sweep roofline (16.7 M sites, 1.8 GB per sweep)

@@ -115,24 +115,29 @@ __device__ __forceinline__ double sweep2_unit(const S* fin, const T* dm, const T
     for (int k = 0; k < 9; ++k) { Ar[k] = T(0); Br[k] = T(0); ftp[k] = T(0); }
     T ssq_f = T(0);
 
-    // software pipeline: the loads of row j+1 are issued before row j is collided
-    T nf[9], ndp = T(0), ndx = T(0), ndy = T(0), nh0 = T(0), nh1 = T(0), nh2 = T(0);
-    auto load_row = [&](int jr) {
+    // software pipeline, two rows deep: the loads of rows j+1 and j+2 are in flight while row j is
+    // collided (a warp keeps ~2 rows x 15 values of 128 B outstanding; the kernel is bound by load
+    // latency, not by issue)
+    T nf[9], ndp = T(0), ndx = T(0), ndy = T(0), nh0 = T(0), nh1 = T(0), nh2 = T(0);  // row j+1
+    T qf[9], qdp = T(0), qdx = T(0), qdy = T(0), qh0 = T(0), qh1 = T(0), qh2 = T(0);  // row j+2
+    auto load_row = [&](int jr, T* g, T& gdp, T& gdx, T& gdy, T& gh0, T& gh1, T& gh2) {
         const size_t id = (size_t)(jr & nmask) * n + x;
 #pragma unroll
-        for (int k = 0; k < 9; ++k) nf[k] = ld_pop<T, S>(fin, k * NN + id, sig);
+        for (int k = 0; k < 9; ++k) g[k] = ld_pop<T, S>(fin, k * NN + id, sig);
         if (!EXPLICIT) {
-            if (lift) { ndp = dm[id]; ndx = dm[NN + id]; ndy = dm[2 * NN + id]; }
-            nh0 = hh[id]; nh1 = hh[NN + id]; nh2 = hh[2 * NN + id];
+            if (lift) { gdp = dm[id]; gdx = dm[NN + id]; gdy = dm[2 * NN + id]; }
+            gh0 = hh[id]; gh1 = hh[NN + id]; gh2 = hh[2 * NN + id];
         }
     };
-    load_row(y0 - 1);
+    load_row(y0 - 1, nf, ndp, ndx, ndy, nh0, nh1, nh2);
+    load_row(y0, qf, qdp, qdx, qdy, qh0, qh1, qh2);
     for (int j = y0 - 1; j <= y0 + hb; ++j) {
         T f[9];
 #pragma unroll
-        for (int k = 0; k < 9; ++k) f[k] = nf[k];
+        for (int k = 0; k < 9; ++k) { f[k] = nf[k]; nf[k] = qf[k]; }
         const T dp = ndp, dux = ndx, duy = ndy, h0 = nh0, h1 = nh1, h2 = nh2;
-        if (j < y0 + hb) load_row(j + 1);
+        ndp = qdp; ndx = qdx; ndy = qdy; nh0 = qh0; nh1 = qh1; nh2 = qh2;
+        if (j + 2 <= y0 + hb) load_row(j + 2, qf, qdp, qdx, qdy, qh0, qh1, qh2);
         if (!EXPLICIT && lift) {  // trial f = f_T,prev + E dm   (Eq. lift)
 #pragma unroll
             for (int k = 0; k < 9; ++k)
@@ -233,9 +238,9 @@ __device__ __forceinline__ double sweep2_unit(const S* fin, const T* dm, const T
     return ssq;
 }
 
-// FP32 operating-point sweeps keep six blocks (24 warps) per SM: the kernel is bound by load latency
+// FP32 operating-point sweeps keep five blocks (20 warps, two rows of loads in flight each) per SM
 template <typename T, typename S, bool EXPLICIT, bool GRAPH, bool TRT = false>
-__global__ void __launch_bounds__(kSweepWarps * 32, sizeof(T) == 4 && !TRT ? 6 : 1) k_sweep2(Sweep2Args<T, S> A) {
+__global__ void __launch_bounds__(kSweepWarps * 32, sizeof(T) == 4 && !TRT ? 5 : 1) k_sweep2(Sweep2Args<T, S> A) {
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int n = A.n;

@@ -484,7 +484,7 @@ def measure_adjoint(torch, PL, dev, n=256, dt_target=32.0, fd_dirs=1):
     def ev():
         return torch.cuda.Event(enable_timing=True)
 
-    R.forward(p0_d, u0_d)  # warm-up (graph build)
+    R.backward(R.forward(p0_d, u0_d) - target)  # warm-up (graph builds)
     torch.cuda.synchronize()
     e0, e1, e2 = ev(), ev(), ev()
     e0.record()

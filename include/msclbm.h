@@ -173,6 +173,12 @@ int msc_get_stats(msc_ctx* ctx, msc_stats* out);
    device memory (synchronises). */
 int msc_read_fields(msc_ctx* ctx, double* p_hat, double* u, int on_device);
 
+/* Stream-ordered copy of m^n = (p_hat, u), (d+1) x sites doubles, into device memory m, without
+   synchronising: a kernel on the context's stream reads which buffer holds m^n, so the copy may
+   follow a march that has not finished (e.g. one step of a recorded replay).  Errors: MSC_ERR_ARG
+   for a NULL context or pointer, MSC_ERR_CUDA for a failed launch. */
+int msc_copy_fields_async(msc_ctx* ctx, double* m);
+
 /* Copy the accepted populations f^n (converted to double, Q*sites values) out (synchronises). */
 int msc_read_populations(msc_ctx* ctx, double* f, int on_device);
 
@@ -277,10 +283,43 @@ typedef struct {
    relative residual falls below eps (> 0) or after kmax iterations (MSC_ERR_NONCONVERGED: the
    accumulators are then left untouched).  Uses the context's working arrays as scratch: the forward
    state is undefined afterwards, so load a state (msc_load_state / msc_load_state_device) before
-   the next march.  Synchronises the stream once per iteration.  `out` may be NULL. */
+   the next march.  The iteration runs on the device (a CUDA graph with conditional nodes); the call
+   synchronises the stream once.  `out` may be NULL. */
 int msc_adjoint_step(msc_ctx* ctx, int q, const double* m_new, const double* m_cur, const double* m_prev,
                      const double* abar_new, double* abar_cur, double* abar_prev, double* dforce, double eps,
                      int kmax, msc_adjoint_stats* out);
+
+/* The arrays of one step of msc_adjoint_steps (meaning as in msc_adjoint_step), and its start. */
+typedef struct {
+    int q;
+    const double* m_new;
+    const double* m_cur;
+    const double* m_prev;   /* may be NULL when q = 1 */
+    const double* abar_new;
+    double* abar_cur;
+    double* abar_prev;      /* may be NULL when q = 1 */
+    int warm;               /* 0: the transposed solve starts from theta = c (as msc_adjoint_step does);
+                               1: from c + (theta - c) of the last step that converged on this
+                               context (zero before the first), which a reverse pass sets for every
+                               step after its first.  The result is the same fixed point within eps. */
+} msc_adjoint_io;
+
+/* `count` adjoint steps in array order (a reverse pass lists the last physical step first, so that
+   each step's abar_new is complete when it runs), with one synchronisation per MSC_ADJOINT_CHUNK
+   steps instead of one per step.  Each step is exactly msc_adjoint_step.  After the first step
+   that fails (MSC_ERR_NONCONVERGED or MSC_ERR_NONFINITE) the later steps run no kernels, leave their
+   arrays untouched and report status MSC_ERR_STATE with iters 0.  `out` (count entries) may be
+   NULL.  Returns MSC_OK or the status of the first failing step; MSC_ERR_ARG for a NULL or invalid
+   entry (nothing is run). */
+#define MSC_ADJOINT_CHUNK 64
+int msc_adjoint_steps(msc_ctx* ctx, int count, const msc_adjoint_io* steps, double* dforce, double eps, int kmax,
+                      msc_adjoint_stats* out);
+
+/* msc_adjoint_steps with every kernel launched from the host and the iteration decided on the host
+   (same kernels in the same order, identical results; one synchronisation per iteration).  For
+   profiling: profilers do not descend into the conditional graph nodes of msc_adjoint_steps. */
+int msc_adjoint_steps_stepwise(msc_ctx* ctx, int count, const msc_adjoint_io* steps, double* dforce, double eps,
+                               int kmax, msc_adjoint_stats* out);
 
 /* Self-check of the library's binary32 <-> binary64 conversions (integer-pipe implementations of the
    IEEE 754 widening and round-to-nearest-even narrowing used by the FP32-storage step kernels)

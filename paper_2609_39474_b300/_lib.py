@@ -54,6 +54,12 @@ class AdjointStats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("status", ctypes.c_int), ("residual", ctypes.c_double)]
 
 
+class AdjointIO(ctypes.Structure):
+    _fields_ = [("q", ctypes.c_int), ("m_new", ctypes.c_void_p), ("m_cur", ctypes.c_void_p),
+                ("m_prev", ctypes.c_void_p), ("abar_new", ctypes.c_void_p), ("abar_cur", ctypes.c_void_p),
+                ("abar_prev", ctypes.c_void_p), ("warm", ctypes.c_int)]
+
+
 class MscError(RuntimeError):
     def __init__(self, code: int, where: str):
         self.code = code
@@ -83,6 +89,7 @@ _SIG = {
     "msc_explicit_march": (_i, [_vp, _i]),
     "msc_get_stats": (_i, [_vp, ctypes.POINTER(Stats)]),
     "msc_read_fields": (_i, [_vp, _vp, _vp, _i]),
+    "msc_copy_fields_async": (_i, [_vp, _vp]),
     "msc_read_populations": (_i, [_vp, _vp, _i]),
     "msc_get_residual_history": (_i, [_vp, _vp, _i, ctypes.POINTER(_i)]),
     "msc_get_step_iters": (_i, [_vp, _vp, _i, ctypes.POINTER(_i)]),
@@ -97,6 +104,9 @@ _SIG = {
     "msc_sweep_d2q9_noalloc": (_i, [_i, _i, _d, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "msc_sweep_trt": (_i, [_i, _i, _d, _d, _d, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "msc_adjoint_step": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _d, _i, ctypes.POINTER(AdjointStats)]),
+    "msc_adjoint_steps": (_i, [_vp, _i, ctypes.POINTER(AdjointIO), _vp, _d, _i, ctypes.POINTER(AdjointStats)]),
+    "msc_adjoint_steps_stepwise": (_i, [_vp, _i, ctypes.POINTER(AdjointIO), _vp, _d, _i,
+                                        ctypes.POINTER(AdjointStats)]),
     "msc_save_state_device": (_i, [_vp, _vp, ctypes.POINTER(_sz)]),
     "msc_selftest_conversions": (_i, [_i, _i, ctypes.c_ulonglong, ctypes.POINTER(_i)]),
     "msc_load_state_device": (_i, [_vp, _vp, _sz]),

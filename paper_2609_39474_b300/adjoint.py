@@ -1,10 +1,11 @@
-"""Gradients of a march through its discrete adjoint (msc_adjoint_step), with checkpoints.
+"""Gradients of a march through its discrete adjoint (msc_adjoint_steps), with checkpoints.
 
 The forward march stores a device-resident state blob every `checkpoint_every` physical steps.
-The reverse pass walks the segments last first: it reloads the segment's checkpoint, replays the
-segment one step at a time (the replay is bit-identical to the forward march) while recording
-each step's moments m^{n+1}, then runs the adjoint of those steps last first.  Only three adjoint
-moment arrays (dL/dm^{n+1}, dL/dm^n, dL/dm^{n-1}) are live at any time.  Every step runs in the CUDA
+The reverse pass walks the segments last first.  For each it reloads the checkpoint and replays
+the segment one step at a time (bit-identical to the forward march), recording each step's
+moments m^{n+1} with stream-ordered copies.  Then one msc_adjoint_steps call runs the adjoint of
+those steps, last first, with one synchronisation per segment.  The adjoint moment arrays of one
+segment (checkpoint interval + 2 of them) are live at a time.  Every step runs in the CUDA
 library; this module only orders the calls and holds the buffers.
 
 ``MscMarch.apply(u0, force, runner, p0)`` wraps it as a torch.autograd.Function: the output is the
@@ -82,18 +83,25 @@ class MarchRunner:
             for n in range(s0, s1):  # replay the segment, recording each accepted step's moments
                 self.L.march(1)
                 m = torch.empty(shape, dtype=torch.float64, device=dev)
-                self.L.moments_into(m)
+                self.L.copy_fields_async(m)  # stream-ordered: no synchronisation inside the replay
                 ms[n + 1] = m
+            st = self.L.stats()
+            if st["status"] != 0:
+                raise RuntimeError(f"replay of steps {s0}..{s1} stopped with status {st['status']}")
+            steps = []
             for n in range(s1 - 1, s0 - 1, -1):
                 q = 1 if n == 0 else 2
                 for k in (n, n - 1):
                     if k >= 0 and k not in abar:
                         abar[k] = torch.zeros(shape, dtype=torch.float64, device=dev)
-                r = self.L.adjoint_step(q, ms[n + 1], ms[n], ms.get(n - 1) if q == 2 else None, abar[n + 1],
-                                        abar[n], abar.get(n - 1) if q == 2 else None, dF, self.eps_adj,
-                                        self.kmax_adj)
+                # every step after the first of the reverse pass starts from its successor's solution
+                steps.append((q, ms[n + 1], ms[n], ms.get(n - 1) if q == 2 else None, abar[n + 1], abar[n],
+                              abar.get(n - 1) if q == 2 else None, n != self.steps - 1))
+            # the segment's adjoint steps, last first, in one call (one synchronisation)
+            for n, r in zip(range(s1 - 1, s0 - 1, -1), self.L.adjoint_steps(steps, dF, self.eps_adj, self.kmax_adj)):
                 self.adjoint_iters[n] = r["iters"]
-                del abar[n + 1]
+            for n in range(s0 + 1, s1 + 1):
+                del abar[n]
         return abar[0][0].clone(), abar[0][1:].clone(), dF[:2].clone()
 
 

@@ -103,8 +103,13 @@ struct DevState {
 };
 
 // Layout of the context workspace (byte offsets from the workspace base).
+// workspace bytes of an adjoint run of up to MSC_ADJOINT_CHUNK steps (position block, argument and
+// outcome blocks; sizes checked where the blocks are defined)
+constexpr size_t kAdjCtlBytes = 256, kAdjArgBytes = 160, kAdjStatBytes = 32;
+constexpr size_t kAdjBytes = kAdjCtlBytes + MSC_ADJOINT_CHUNK * (kAdjArgBytes + kAdjStatBytes);
+
 struct Layout {
-    size_t state, fbuf, mbuf, h, pr, dm, spec, tw, coef, partial, counter, iters, hist, replay, total;
+    size_t state, fbuf, mbuf, h, pr, dm, spec, tw, coef, partial, counter, adj, adjw, iters, hist, replay, total;
     size_t fstride;  // bytes of one population array
 };
 

@@ -322,6 +322,14 @@ __global__ void k_solve_tables(double* coef, int dim, int n, double dt, double n
     }
 }
 
+// m^n (the moment buffer the state names) into out, count = (d+1) sites values
+__global__ void __launch_bounds__(kFieldThreads) k_copy_fields(const DevState* st, const double* mbuf,
+                                                               double* __restrict__ out, size_t count) {
+    const double* __restrict__ m = mbuf + (size_t)st->m_cur * count;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+        out[i] = m[i];
+}
+
 // ---- single-thread control kernels ------------------------------------------------------------
 
 __device__ inline void set_step_constants(DevState* st) {

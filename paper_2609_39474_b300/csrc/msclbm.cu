@@ -2,6 +2,7 @@
 // conditional WHILE/IF nodes, so that the acceptance test of Algorithm 1 never leaves the
 // device), the explicit LBM baseline and the stage entry points.  See include/msclbm.h.
 #include <cmath>
+#include <cstddef>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -42,6 +43,7 @@ struct msc_ctx {
     cudaGraphExec_t x_march;
     cudaGraph_t g_ex;
     cudaGraphExec_t x_ex;
+    cudaGraphExec_t x_adj[2];  // transposed solve of one adjoint step, BDF1 and BDF2
     int sweep_blocks;
 };
 
@@ -112,6 +114,8 @@ bool compute_layout(const msc_lattice_desc* d, Layout* L) {
     L->coef = take(2 * 4 * solve_modes(d->dim, d->n) * sizeof(double));
     L->partial = take((size_t)sweep_blocks_for(d->dim, d->n, d->precision) * 8);
     L->counter = take(256);
+    L->adj = take(kAdjBytes);  // adjoint run: position, per-step arguments and outcomes
+    L->adjw = take(d->dim == 2 ? F * sites * e : 0);  // adjoint warm start: theta - c of the last step
     L->iters = take((size_t)d->max_steps * 4);
     L->hist = take((size_t)d->hist_cap * 8);
     L->replay = take((size_t)d->max_steps * 4);
@@ -593,9 +597,10 @@ int msc_create(msc_ctx** out, const msc_lattice_desc* desc, void* ws, size_t byt
     c->ws = (unsigned char*)ws;
     c->stream = (cudaStream_t)stream;
     c->coef_dirty = true;
-    // zero the state, the reduction counter and the correction (first lift reads it only if set)
+    // zero the state, the reduction counter and the adjoint warm start (a first warm step starts cold)
     if (cudaMemsetAsync(c->ws + L.state, 0, sizeof(DevState), c->stream) != cudaSuccess ||
-        cudaMemsetAsync(c->ws + L.counter, 0, 256, c->stream) != cudaSuccess) {
+        cudaMemsetAsync(c->ws + L.counter, 0, 256, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->ws + L.adjw, 0, L.iters - L.adjw, c->stream) != cudaSuccess) {
         free(c);
         return MSC_ERR_CUDA;
     }
@@ -619,6 +624,8 @@ void msc_destroy(msc_ctx* c) {
     if (c->g_march) cudaGraphDestroy(c->g_march);
     if (c->x_ex) cudaGraphExecDestroy(c->x_ex);
     if (c->g_ex) cudaGraphDestroy(c->g_ex);
+    for (int i = 0; i < 2; ++i)
+        if (c->x_adj[i]) cudaGraphExecDestroy(c->x_adj[i]);
     free(c);
 }
 
@@ -723,6 +730,15 @@ int msc_read_fields(msc_ctx* c, double* p, double* u, int on_device) {
     CK(cudaMemcpyAsync(p, m, c->sites * 8, kind, c->stream));
     CK(cudaMemcpyAsync(u, m + c->sites, c->sites * 8 * c->desc.dim, kind, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    return MSC_OK;
+}
+
+int msc_copy_fields_async(msc_ctx* c, double* m) {
+    if (!c || !m) return MSC_ERR_ARG;
+    const size_t count = (size_t)(c->desc.dim + 1) * c->sites;
+    k_copy_fields<<<grid_for(count), kFieldThreads, 0, c->stream>>>(at<const DevState>(c, c->lay.state),
+                                                                     at<const double>(c, c->lay.mbuf), m, count);
+    CK(cudaGetLastError());
     return MSC_OK;
 }
 

@@ -38,12 +38,14 @@ struct Spec2Args {
     double kunit;        // 2 pi / n (formed on the host)
     double nscale;       // 1 / N_Omega (formed on the host)
     const DevState* st;  // graph mode: a and q from the state
-    const double* coef;  // graph mode: per-mode solve coefficients for q = 1, 2 (k_solve_tables)
+    const double* coef;  // per-mode solve coefficients (k_solve_tables): for q = 1, 2 with st, else one table
 };
 
-// pick the coefficient table of the current BDF order (graph mode) or none (stage calls)
+// pick the coefficient table of the current BDF order (graph mode), the table the caller chose
+// (no state), or none (stage calls)
 __device__ inline const double* solve_table(const double* coef, const DevState* st, int dim, int n) {
     if (!coef) return nullptr;
+    if (!st) return coef;
     const int q = st->q;
     return coef + (size_t)(q - 1) * 4 * solve_modes(dim, n);
 }
@@ -123,7 +125,9 @@ __global__ void __launch_bounds__(kFftThreads) k_rowfft_fwd(Spec2Args<T> A) {
     rowfft_fwd_block<T>(A, blockIdx.x);
 }
 
-template <typename T>
+// ACC = false: dm = the correction.  ACC = true (the adjoint's update): dm += pr + the correction,
+// dm holding the iterate and pr the residual the forward pass transformed.
+template <typename T, bool ACC = false>
 __device__ __forceinline__ void rowfft_inv_block(const Spec2Args<T>& A, int bid) {
     using C = typename Cplx<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -157,7 +161,38 @@ __device__ __forceinline__ void rowfft_inv_block(const Spec2Args<T>& A, int bid)
     }
     __syncthreads();
     fft_stockham<C, true>(s, n, logn, P, A.tw);
-    T* rows = A.dm + ((size_t)c * A.rows + y0) * n;
+    T* __restrict__ rows = A.dm + ((size_t)c * A.rows + y0) * n;
+    if (ACC) {
+        // four iterations at a time: all their iterate and residual loads are issued before the
+        // stores, so one memory round trip serves four elements per row pair
+        const T* __restrict__ res = A.pr + ((size_t)c * A.rows + y0) * n;
+        constexpr int U = 4;
+        for (int t0 = threadIdx.x; t0 < P * n; t0 += U * blockDim.x) {
+            T v0[U], v1[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int t = t0 + u * blockDim.x;
+                if (t < P * n) {
+                    const size_t o0 = (size_t)(2 * (t >> logn)) * n + (t & (n - 1));
+                    v0[u] = rows[o0] + res[o0];
+                    v1[u] = rows[o0 + n] + res[o0 + n];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int t = t0 + u * blockDim.x;
+                if (t < P * n) {
+                    const int p = t >> logn;
+                    const int x = t & (n - 1);
+                    const size_t o0 = (size_t)(2 * p) * n + x;
+                    const C z = s[p * plen + pad(x)];
+                    rows[o0] = v0[u] + z.x;
+                    rows[o0 + n] = v1[u] + z.y;
+                }
+            }
+        }
+        return;
+    }
     for (int t = threadIdx.x; t < P * n; t += blockDim.x) {
         const int p = t >> logn;
         const int x = t & (n - 1);
@@ -170,6 +205,12 @@ __device__ __forceinline__ void rowfft_inv_block(const Spec2Args<T>& A, int bid)
 template <typename T>
 __global__ void __launch_bounds__(kFftThreads) k_rowfft_inv(Spec2Args<T> A) {
     rowfft_inv_block<T>(A, blockIdx.x);
+}
+
+// the inverse row pass of the adjoint shadow correction, fused with the iterate update
+template <typename T>
+__global__ void __launch_bounds__(kFftThreads) k_rowfft_inv_acc(Spec2Args<T> A) {
+    rowfft_inv_block<T, true>(A, blockIdx.x);
 }
 
 // Schur solve at one masked wavevector in FP64: dp = A rp - i B (k.rm), du = Dv rm - i Cc k dp

@@ -177,6 +177,11 @@ class MscLattice:
         _check_moments(out)
         L.check(L.lib.msc_read_fields(self._ctx, _ptr(out[0]), _ptr(out[1]), 1), "msc_read_fields")
 
+    def copy_fields_async(self, out: torch.Tensor):
+        """msc_copy_fields_async: m^n into a (d+1, n, ...) float64 device tensor, stream-ordered, no sync."""
+        _check_moments(out)
+        L.check(L.lib.msc_copy_fields_async(self._ctx, _ptr(out)), "msc_copy_fields_async")
+
     def adjoint_step(self, q: int, m_new, m_cur, m_prev, abar_new, abar_cur, abar_prev, dforce,
                      eps: float = 1e-10, kmax: int = 1000) -> dict:
         """msc_adjoint_step: dL/dm^{n+1} -> accumulate into dL/dm^n, dL/dm^{n-1}, dL/dF (device float64)."""
@@ -187,6 +192,25 @@ class MscLattice:
                                     ctypes.byref(st))
         L.check(rc, "msc_adjoint_step")
         return {"iters": st.iters, "residual": st.residual}
+
+    def adjoint_steps(self, steps, dforce, eps: float = 1e-10, kmax: int = 1000, stepwise: bool = False) -> list:
+        """msc_adjoint_steps: several adjoint steps in list order, one synchronisation per 64 steps.
+
+        `steps` holds tuples (q, m_new, m_cur, m_prev, abar_new, abar_cur, abar_prev[, warm]) as in
+        adjoint_step; warm (default False) starts the step's solve from the last converged step.  Returns one dict (iters, residual, status) per step; raises on a failed step.
+        stepwise=True: msc_adjoint_steps_stepwise (host-driven, for profiling; identical results)."""
+        arr = (L.AdjointIO * max(1, len(steps)))()
+        for i, st in enumerate(steps):
+            q, m_new, m_cur, m_prev, abar_new, abar_cur, abar_prev = st[:7]
+            _check_moments(m_new, m_cur, m_prev, abar_new, abar_cur, abar_prev)
+            arr[i] = L.AdjointIO(int(q), _ptr(m_new), _ptr(m_cur), _dptr(m_prev), _ptr(abar_new), _ptr(abar_cur),
+                                 _dptr(abar_prev), int(bool(st[7])) if len(st) > 7 else 0)
+        _check_moments(dforce)
+        out = (L.AdjointStats * max(1, len(steps)))()
+        fn = L.lib.msc_adjoint_steps_stepwise if stepwise else L.lib.msc_adjoint_steps
+        rc = fn(self._ctx, len(steps), arr, _ptr(dforce), float(eps), int(kmax), out)
+        L.check(rc, "msc_adjoint_steps")
+        return [{"iters": s.iters, "residual": s.residual, "status": s.status} for s in out[:len(steps)]]
 
 
 # ---- stage calls ---------------------------------------------------------------------------------

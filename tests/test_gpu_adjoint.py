@@ -143,3 +143,86 @@ def test_autograd_function():
     assert torch.equal(u0_t.grad, gu)
     assert torch.allclose(F_t.grad, gF.cpu())
     assert F_t.grad.abs().sum() > 0 and u0_t.grad.abs().sum() > 0
+
+
+def _step_inputs(N=16, dt=9.0):
+    p0, u0 = random_phase(N, 2, 1.0, seed=3, kmax=3)
+    st, ms, qs = AD.forward_moments(D2Q9, p0, u0, OM.MarchParams(dt=dt, eps=1e-15, kmax=5000), 3)
+    mp, mv = random_phase(N, 2, 50.0, seed=9, kmax=3)
+    mu = np.concatenate([mp[None], mv]) / np.abs(mv).max()
+    return [dev(m) for m in ms], dev(mu)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_adjoint_steps_equal_single_steps_across_chunks(precision):
+    # 70 steps (two runs of the 64-step chunk) through one call are bit-identical to 70 single calls
+    # and to the host-driven run of the same kernels
+    N, dt = 16, 9.0
+    ms, mu = _step_inputs(N, dt)
+    outs = []
+    for mode in ("single", "graph", "stepwise"):
+        L = _lat(N, precision)
+        L.set_params(dt=dt, eps=1e-10)
+        ab_cur = torch.zeros_like(mu)
+        ab_prev = torch.zeros_like(mu)
+        dF = torch.zeros(3, dtype=torch.float64, device="cuda")
+        steps = [(2 if i % 3 else 1, ms[3], ms[2], ms[1], mu, ab_cur, ab_prev) for i in range(70)]
+        eps = 1e-12 if precision == "fp64" else 1e-5
+        if mode == "single":
+            rs = [L.adjoint_step(q, a, b, c if q == 2 else None, d, e, f if q == 2 else None, dF, eps=eps, kmax=500)
+                  for q, a, b, c, d, e, f in steps]
+        else:
+            rs = L.adjoint_steps(steps, dF, eps=eps, kmax=500, stepwise=mode == "stepwise")
+        outs.append((ab_cur, ab_prev, dF, [r["iters"] for r in rs]))
+    for o in outs[1:]:
+        for x, y in zip(outs[0][:3], o[:3]):
+            assert torch.equal(x, y)
+        assert outs[0][3] == o[3]
+    assert min(outs[0][3]) > 0
+
+
+def test_adjoint_steps_stop_after_a_failed_step():
+    # kmax = 0 cannot reach eps: the first step reports MSC_ERR_NONCONVERGED, the later ones are not
+    # run (MSC_ERR_STATE) and every accumulator stays untouched
+    from paper_2609_39474_b300 import _lib
+    N, dt = 16, 9.0
+    ms, mu = _step_inputs(N, dt)
+    L = _lat(N)
+    L.set_params(dt=dt, eps=1e-10)
+    ab_cur = torch.zeros_like(mu)
+    ab_prev = torch.zeros_like(mu)
+    dF = torch.zeros(3, dtype=torch.float64, device="cuda")
+    arr = (_lib.AdjointIO * 3)()
+    for i in range(3):
+        arr[i] = _lib.AdjointIO(2, ms[3].data_ptr(), ms[2].data_ptr(), ms[1].data_ptr(), mu.data_ptr(),
+                                ab_cur.data_ptr(), ab_prev.data_ptr())
+    out = (_lib.AdjointStats * 3)()
+    rc = _lib.lib.msc_adjoint_steps(L._ctx, 3, arr, dF.data_ptr(), 1e-12, 0, out)
+    assert rc == 2  # MSC_ERR_NONCONVERGED
+    assert [s.status for s in out] == [2, 6, 6] and [s.iters for s in out] == [0, 0, 0]
+    assert out[0].residual > 1e-12
+    assert not ab_cur.any() and not ab_prev.any() and not dF.any()
+    # the context stays usable: the same steps then converge
+    rs = L.adjoint_steps([(2, ms[3], ms[2], ms[1], mu, ab_cur, ab_prev)], dF, eps=1e-12, kmax=500)
+    assert rs[0]["status"] == 0 and ab_cur.abs().sum() > 0
+
+
+def test_warm_start_reaches_the_same_fixed_point():
+    # a repeated step started from its predecessor's solution (warm) needs no correction and accumulates
+    # what a cold start accumulates, within the solve's tolerance
+    N, dt = 16, 9.0
+    ms, mu = _step_inputs(N, dt)
+    res = {}
+    for warm in (False, True):
+        L = _lat(N)
+        L.set_params(dt=dt, eps=1e-10)
+        ab_cur = torch.zeros_like(mu)
+        ab_prev = torch.zeros_like(mu)
+        dF = torch.zeros(3, dtype=torch.float64, device="cuda")
+        steps = [(2, ms[3], ms[2], ms[1], mu, ab_cur, ab_prev, warm and i > 0) for i in range(4)]
+        rs = L.adjoint_steps(steps, dF, eps=1e-12, kmax=500)
+        res[warm] = (ab_cur, ab_prev, dF, [r["iters"] for r in rs])
+    cold, hot = res[False], res[True]
+    assert hot[3][0] == cold[3][0] and max(hot[3][1:]) <= 1 and min(cold[3][1:]) > 5
+    for x, y in zip(cold[:3], hot[:3]):
+        assert rel_l2(host(y), host(x)) < 1e-10

@@ -459,6 +459,29 @@ def batch_stage(torch, PL, dev, args):
     return out
 
 
+def adjoint_stepwise(torch, PL, dev, n=256, S=16, dt=32.0):
+    """Profiling aid: the config-5 lattice (N = 256 FP32, eps = 1e-5 U, checkpoints every 8 steps)
+    over S steps, forward and reverse pass driven from the host (one launch per kernel, visible to
+    ncu), after one warm-up pass."""
+    from paper_2609_39474_b300.adjoint import MarchRunner
+    U = NU / n
+    p0, u0 = random_phase(n, 2, 1.0, seed=3, kmax=8)
+    p0_d, u0_d = torch.as_tensor(p0, device=dev), torch.as_tensor(u0, device=dev)
+    R = MarchRunner(PL.MscLattice(2, n, "fp32", max_steps=64, hist_cap=1 << 12, device=str(dev)), dt=dt, steps=S,
+                    eps=1e-5 * U, checkpoint_every=8, eps_adjoint=1e-5, kmax_adjoint=2000, stepwise=True)
+    out = {}
+    for rep in ("warm-up", "profiled"):
+        uS = R.forward(p0_d, u0_d)
+        g = 0.5 * uS
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        R.backward(g)
+        torch.cuda.synchronize()
+        out = {"workload": f"D2Q9 N={n} FP32, S={S}, dt={dt}, host-driven", "t_backward_ms":
+               1e3 * (time.perf_counter() - t0), "adjoint_iters_per_step": float(np.mean(R.adjoint_iters))}
+    return out
+
+
 def measure_adjoint(torch, PL, dev, n=256, dt_target=32.0, fd_dirs=1):
     """Config 5: L = 1/2 sum |u^S - u*|^2 at t = 0.1 N^2 / nu, u* from a seeded target field run
     under a force; gradients with respect to u0 (guess seed 3) and the force (at F = 0) by the
@@ -474,9 +497,10 @@ def measure_adjoint(torch, PL, dev, n=256, dt_target=32.0, fd_dirs=1):
     p0, u0 = random_phase(n, 2, 1.0, seed=3, kmax=8)
     p0_d, u0_d = torch.as_tensor(p0, device=dev), torch.as_tensor(u0, device=dev)
 
-    def runner():
+    def runner(record=False):
         return MarchRunner(PL.MscLattice(2, n, "fp32", max_steps=64, hist_cap=1 << 12, device=str(dev)), dt=dt,
-                           steps=S, eps=eps, checkpoint_every=8, eps_adjoint=1e-5, kmax_adjoint=2000)
+                           steps=S, eps=eps, checkpoint_every=8, eps_adjoint=1e-5, kmax_adjoint=2000,
+                           record_moments=record)
 
     target = runner().forward(torch.as_tensor(pt, device=dev), torch.as_tensor(ut, device=dev), F_star)
     R = runner()
@@ -495,6 +519,20 @@ def measure_adjoint(torch, PL, dev, n=256, dt_target=32.0, fd_dirs=1):
     torch.cuda.synchronize()
     t_fwd, t_bwd = e0.elapsed_time(e1), e1.elapsed_time(e2)
     loss0 = 0.5 * float(((uS - target) ** 2).sum())
+    # the same gradient with every step's moments kept in HBM (no checkpoints, no replay)
+    R2 = runner(record=True)
+    R2.backward(R2.forward(p0_d, u0_d) - target)
+    torch.cuda.synchronize()
+    e0.record()
+    uS2 = R2.forward(p0_d, u0_d)
+    e1.record()
+    g2 = R2.backward(uS2 - target)
+    e2.record()
+    torch.cuda.synchronize()
+    recorded = {"t_forward_ms": e0.elapsed_time(e1), "t_backward_ms": e1.elapsed_time(e2),
+                "moment_bytes": int(R2.recorded.numel() * 8),
+                "same_gradient": bool(all(torch.equal(a, b) for a, b in zip(g2, (gp, gu, gF))))}
+    del R2, g2, uS2
 
     def loss(u0_, F_):
         uu = R.forward(p0_d, u0_, F_)
@@ -521,7 +559,7 @@ def measure_adjoint(torch, PL, dev, n=256, dt_target=32.0, fd_dirs=1):
             "loss": loss0, "t_forward_ms": t_fwd, "t_backward_ms": t_bwd, "backward_over_forward": t_bwd / t_fwd,
             "adjoint_iters_per_step": float(np.mean(it)), "adjoint_iters_max": int(max(it)),
             "grad_norms": {"u0": float(gu.norm()), "F": [float(x) for x in gF]}, "fd_checks": checks,
-            "checkpoint_bytes": int(sum(b.numel() for b in R.checkpoints))}
+            "checkpoint_bytes": int(sum(b.numel() for b in R.checkpoints)), "recorded_moments": recorded}
 
 
 def measure_offdesign(torch, PL, dev, n=128):
@@ -607,6 +645,8 @@ def run_phase(args):
         return {"phase": "batch", **measure_batch(torch, PL, dev)}
     if args.phase == "adjoint":
         return {"phase": "adjoint", **measure_adjoint(torch, PL, dev)}
+    if args.phase == "adjoint-stepwise":
+        return {"phase": "adjoint-stepwise", **adjoint_stepwise(torch, PL, dev)}
     if args.phase == "offdesign":
         return {"phase": "offdesign", **measure_offdesign(torch, PL, dev)}
     n = args.n
@@ -760,12 +800,14 @@ def main():
                     help="--phase batch-stage: a batch tiling as JSON (keys sweep_rows, fft_rows, col_lines, "
                          "sweep_ctas_per_sm) instead of autotuning, so that only the timed launches run")
     ap.add_argument("--phase", default="all",
-                    choices=["all", "msc", "msc-stepwise", "sweep", "batch", "batch-stage", "adjoint", "offdesign"],
+                    choices=["all", "msc", "msc-stepwise", "sweep", "batch", "batch-stage", "adjoint", "adjoint-stepwise",
+                             "offdesign"],
                     help="profiling aids: 'msc' runs only the timed MSC marches of the default candidate, "
                          "'msc-stepwise' the same marches driven from the host (one launch per kernel, "
                          "visible to ncu), 'sweep' only the fused-sweep roofline loop, 'batch' only the "
                          "48-instance batched parameter sweep, 'batch-stage' the batch's kernels timed one "
-                         "family at a time (stateless, visible to ncu)")
+                         "family at a time (stateless, visible to ncu), 'adjoint' the config-5 gradient, "
+                         "'adjoint-stepwise' 16 steps of it driven from the host (visible to ncu)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
 

@@ -226,3 +226,19 @@ def test_warm_start_reaches_the_same_fixed_point():
     assert hot[3][0] == cold[3][0] and max(hot[3][1:]) <= 1 and min(cold[3][1:]) > 5
     for x, y in zip(cold[:3], hot[:3]):
         assert rel_l2(host(y), host(x)) < 1e-10
+
+
+def test_recorded_moments_give_the_checkpointed_gradients():
+    # keeping every step's moments (no replay) changes nothing: same march, same adjoint steps
+    N, S, dt = 64, 12, 24.0
+    p0, u0, pt, ut, F_star = _problem(N, S, dt)
+    out = []
+    for record in (False, True):
+        from paper_2609_39474_b300.adjoint import MarchRunner
+        R = MarchRunner(_lat(N, "fp32"), dt=dt, steps=S, eps=1e-6 * NU / N, checkpoint_every=4, eps_adjoint=1e-5,
+                        record_moments=record)
+        uS = R.forward(dev(p0), dev(u0), F_star)
+        out.append((uS, R.backward(uS - dev(ut)), list(R.adjoint_iters)))
+    assert torch.equal(out[0][0], out[1][0]) and out[0][2] == out[1][2]
+    for a, b in zip(out[0][1], out[1][1]):
+        assert torch.equal(a, b)

@@ -239,6 +239,25 @@ int msc_sweep_trt(int n, int precision, double a, double omega_p, double omega_m
                   const void* h, void* f_out, void* pr_out, double* sumsq_out, void* scratch, size_t scratch_bytes,
                   void* stream);
 
+/* Full-symbol reference correction for D2Q9 (Section 4.1, Eq. full-symbol; the reference operator
+   of the off-design study, Section 4.6): the linearised Newton step about rest,
+       f_out = f + F^{-1}[ (I - Z(k) J)^{-1} F[f_swept - f] ]
+   at every wavevector and on all 9 population fields, where J is the Q x Q Jacobian of the general
+   TRT collision (Eq. collision, rates omega_p, omega_m in (0, 2), BDF reaction a > 0) at the rest
+   state and Z(k) = diag(exp(-i k . c_q)) the streaming symbol.  J is used in closed form (the
+   exact derivative; the paper forms it by a forward difference of step 1e-7, which agrees to that
+   difference error) and every wavevector is solved in FP64 through the pair structure of the TRT
+   relaxation (four 2 x 2 blocks and one 3 x 3 system).  f, f_swept, f_out: 9 x n x n elements of
+   the storage type (FP64 or FP32), f_swept the sweep of f (e.g. msc_sweep_trt); f_out may alias f
+   or f_swept.  Scratch: msc_full_symbol_scratch_bytes(n, precision) bytes of device memory,
+   256-byte aligned (twiddles and the 9-field half spectrum).  n a power of two in
+   [8, MSC_FULL_SYMBOL_MAX_N].  Stream-ordered, no synchronisation.  MSC_ERR_ARG for invalid
+   sizes, rates, pointers or scratch. */
+#define MSC_FULL_SYMBOL_MAX_N 1024
+size_t msc_full_symbol_scratch_bytes(int n, int precision);
+int msc_full_symbol_correct(int n, int precision, double a, double omega_p, double omega_m, const void* f,
+                            const void* f_swept, void* f_out, void* scratch, size_t scratch_bytes, void* stream);
+
 /* Allocation-free variant of msc_sweep for D2Q9 (dim 2).  The paper has no counterpart: this is
    an interface convenience for callers that cannot allocate device memory, such as host
    frameworks that own the whole device-memory budget and forbid plugins from calling cudaMalloc,

@@ -13,7 +13,9 @@ The transforms are numpy FFTs on the full grid (every wavevector is corrected). 
 difference error; ghost vectors (P g = 0) are eigenvectors with the TRT relaxation factors
 1 - omega+ (even) and 1 - omega- (odd), so |1 - omega+| = eta(nu) = |6 nu - 1| / (6 nu + 1)
 (Eq. eta); in the linear regime one corrected iteration removes the residual to the difference
-error of J.
+error of J.  rest_jacobian_exact is the derivative itself (complex step), pinned against the forward
+difference and, at omega+- = 1, against gamma E P to rounding; it is the Jacobian the GPU's
+full-symbol correction is compared with.
 """
 import numpy as np
 
@@ -33,23 +35,41 @@ def eta(nu: float) -> float:
     return abs(6.0 * nu - 1.0) / (6.0 * nu + 1.0)
 
 
-def rest_jacobian(lat: Lattice, a: float, omega, delta: float = 1e-7) -> np.ndarray:
-    """Q x Q forward-difference Jacobian of the collision at rest (Eq. full-symbol)."""
+def _rest_collision(lat: Lattice, a: float, omega):
+    """f -> C(f) at the rest state's history: h = a (1, 0), so that s = h - a m = 0 at m = (1, 0)."""
     F = lat.d + 1
-    f0 = feq(lat, np.ones(()), np.zeros(lat.d))
     h = np.zeros(F)
-    h[0] = a  # s = h - a m = 0 at m = (1, 0)
+    h[0] = a
 
     def coll(f):
         m = reconstruct(moments(lat, f), a, h)
         return collide_trt(lat, f, m, source_moments(a, h, m), omega[0], omega[1])
 
+    return coll, feq(lat, np.ones(()), np.zeros(lat.d))
+
+
+def rest_jacobian(lat: Lattice, a: float, omega, delta: float = 1e-7) -> np.ndarray:
+    """Q x Q forward-difference Jacobian of the collision at rest (Eq. full-symbol)."""
+    coll, f0 = _rest_collision(lat, a, omega)
     c0 = coll(f0)
     J = np.empty((lat.Q, lat.Q))
     for j in range(lat.Q):
         fj = f0.copy()
         fj[j] += delta
         J[:, j] = (coll(fj) - c0) / delta
+    return J
+
+
+def rest_jacobian_exact(lat: Lattice, a: float, omega) -> np.ndarray:
+    """The derivative that rest_jacobian approximates, by complex-step differentiation of the same
+    collision (Im C(f0 + i h e_j) / h with h = 1e-30: no subtraction, exact to rounding)."""
+    coll, f0 = _rest_collision(lat, a, omega)
+    hstep = 1e-30
+    J = np.empty((lat.Q, lat.Q))
+    for j in range(lat.Q):
+        fj = f0.astype(np.complex128)
+        fj[j] += 1j * hstep
+        J[:, j] = np.imag(coll(fj)) / hstep
     return J
 
 

@@ -103,6 +103,8 @@ _SIG = {
     "msc_equilibrium": (_i, [_i, _i, _i, _vp, _vp, _vp, _vp]),
     "msc_sweep_d2q9_noalloc": (_i, [_i, _i, _d, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "msc_sweep_trt": (_i, [_i, _i, _d, _d, _d, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "msc_full_symbol_scratch_bytes": (_sz, [_i, _i]),
+    "msc_full_symbol_correct": (_i, [_i, _i, _d, _d, _d, _vp, _vp, _vp, _vp, _sz, _vp]),
     "msc_adjoint_step": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _d, _i, ctypes.POINTER(AdjointStats)]),
     "msc_adjoint_steps": (_i, [_vp, _i, ctypes.POINTER(AdjointIO), _vp, _d, _i, ctypes.POINTER(AdjointStats)]),
     "msc_adjoint_steps_stepwise": (_i, [_vp, _i, ctypes.POINTER(AdjointIO), _vp, _d, _i,

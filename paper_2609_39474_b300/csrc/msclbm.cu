@@ -1084,3 +1084,4 @@ int msc_equilibrium(int dim, int n, int precision, const double* p, const double
 #include "sweep_noalloc.cuh"
 #include "batch_api.cuh"
 #include "adjoint_api.cuh"
+#include "fullsym_api.cuh"

@@ -348,6 +348,25 @@ def sweep_trt(n: int, precision: str, a: float, omega_p: float, omega_m: float, 
     return f_out, pr, ssq
 
 
+def full_symbol_correct(n: int, precision: str, a: float, omega_p: float, omega_m: float, f: torch.Tensor,
+                        f_swept: torch.Tensor, out: torch.Tensor = None, scratch: torch.Tensor = None, stream=None):
+    """msc_full_symbol_correct: f + F^-1[(I - Z J)^-1 F[f_swept - f]] (D2Q9, FP64 or FP32 storage)."""
+    dt = storage_dtype(precision)
+    for t in (f, f_swept):
+        if t.dtype != dt or not t.is_cuda or not t.is_contiguous() or tuple(t.shape) != (9, n, n):
+            raise ValueError("populations must be contiguous (9, n, n) device tensors of the storage type")
+    need = L.lib.msc_full_symbol_scratch_bytes(n, precision_code(precision))
+    if need == 0:
+        raise ValueError(f"full-symbol correction: unsupported n = {n} or precision {precision}")
+    if scratch is None:
+        scratch = torch.empty(need, dtype=torch.uint8, device=f.device)
+    out = torch.empty_like(f) if out is None else out
+    L.check(L.lib.msc_full_symbol_correct(n, precision_code(precision), float(a), float(omega_p), float(omega_m),
+                                          _ptr(f), _ptr(f_swept), _ptr(out), _ptr(scratch), scratch.numel(),
+                                          _stream(stream)), "msc_full_symbol_correct")
+    return out
+
+
 def shadow_solve(dim: int, n: int, precision: str, a: float, nu: float, pr: torch.Tensor,
                  scratch: StageScratch = None, stream=None):
     """delta m = F^-1[chi H^-1 F[P r]] through msc_shadow_solve."""

@@ -81,3 +81,24 @@ def test_full_symbol_converges_where_the_shadow_correction_fails():
     assert full.converged and full.iters < 20
     assert M.rho_observed(full.residuals, 10) < 0.2
     assert not shadow.converged or M.rho_observed(shadow.residuals, 10) > 0.9
+
+
+@pytest.mark.parametrize("nu,lam", [(1 / 6, 0.25), (0.08, 0.25), (0.25, 0.05), (0.12, 2.0)])
+def test_exact_rest_jacobian(nu, lam):
+    # the complex-step derivative agrees with the paper's forward difference to the difference error
+    # and, at the operating point, with gamma E P (Eq. symbol) to rounding
+    wp, wm = FS.trt_rates(nu, lam)
+    a = 3 / (2 * 20.0)
+    Je = FS.rest_jacobian_exact(D2Q9, a, (wp, wm))
+    Jf = FS.rest_jacobian(D2Q9, a, (wp, wm))
+    assert np.max(np.abs(Je - Jf)) < 3e-7
+    if nu == 1 / 6 and lam == 0.25:
+        ref = gamma(a) * K.lift_matrix(D2Q9) @ K.moment_matrix(D2Q9)
+        assert np.max(np.abs(Je - ref)) < 1e-15
+    # conserved structure: the ghost space relaxes at 1 - omega+- exactly
+    P = K.moment_matrix(D2Q9)
+    _, _, vt = np.linalg.svd(P)
+    for g in vt[P.shape[0]:]:
+        for v, lam_e in ((0.5 * (g + g[D2Q9.opp]), 1 - wp), (0.5 * (g - g[D2Q9.opp]), 1 - wm)):
+            if np.linalg.norm(v) > 1e-12 and np.linalg.norm(P @ v) < 1e-12:
+                assert np.allclose(Je @ v, lam_e * v, atol=1e-14)

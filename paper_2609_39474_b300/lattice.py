@@ -120,11 +120,20 @@ class MscLattice:
         L.check(L.lib.msc_get_stats(self._ctx, ctypes.byref(s)), "msc_get_stats")
         return {k: getattr(s, k) for k, _ in L.Stats._fields_}
 
-    def fields(self, on_device: bool = True):
-        """(p_hat, u) of the accepted state m^n, float64."""
-        dev = self.device if on_device else torch.device("cpu")
-        p = torch.empty(self.grid, dtype=torch.float64, device=dev)
-        u = torch.empty((self.dim,) + self.grid, dtype=torch.float64, device=dev)
+    def fields(self, on_device: bool = True, out=None):
+        """(p_hat, u) of the accepted state m^n, float64.  out: preallocated (p_hat, u) tensors to read
+        into (e.g. pinned host buffers, for a fast device-to-host copy); their side decides on_device."""
+        if out is not None:
+            p, u = out
+            if (p.dtype != torch.float64 or u.dtype != torch.float64 or not p.is_contiguous() or
+                    not u.is_contiguous() or tuple(p.shape) != self.grid or
+                    tuple(u.shape) != (self.dim,) + self.grid or p.is_cuda != u.is_cuda):
+                raise ValueError("out must be contiguous float64 (p_hat, u) tensors of the lattice's shape")
+            on_device = p.is_cuda
+        else:
+            dev = self.device if on_device else torch.device("cpu")
+            p = torch.empty(self.grid, dtype=torch.float64, device=dev)
+            u = torch.empty((self.dim,) + self.grid, dtype=torch.float64, device=dev)
         L.check(L.lib.msc_read_fields(self._ctx, _ptr(p), _ptr(u), int(on_device)), "msc_read_fields")
         return p, u
 

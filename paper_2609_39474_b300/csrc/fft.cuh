@@ -209,6 +209,62 @@ __device__ void fft_stockham(C* x, int n, int logn, int nfft, const C* __restric
     }
 }
 
+// cos(pi k / 16) for 0 <= k <= 16 (the 32-point DFT's rotations; sin(pi k / 16) = cos_pi16(|8 - k|))
+__host__ __device__ constexpr double cos_pi16(int k) {
+    return k > 8 ? -cos_pi16(16 - k)
+                 : (k == 0 ? 1.0
+                    : k == 1 ? 0.98078528040323044913
+                    : k == 2 ? 0.92387953251128675613
+                    : k == 3 ? 0.83146961230254523708
+                    : k == 4 ? 0.70710678118654752440
+                    : k == 5 ? 0.55557023301960222474
+                    : k == 6 ? 0.38268343236508977173
+                    : k == 7 ? 0.19509032201612826785
+                             : 0.0);
+}
+
+// 32 = 2 x 16: X[k] = E[k] + W^k O[k], X[k + 16] = E[k] - W^k O[k] with E, O the 16-point DFTs of the
+// even and odd samples and W = exp(-+ 2 pi i / 32)
+template <typename C, bool INV> struct SmallDft<C, 32, INV> {
+    __device__ __forceinline__ static void run(C* v) {
+        C e[16], o[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) { e[i] = v[2 * i]; o[i] = v[2 * i + 1]; }
+        SmallDft<C, 16, INV>::run(e);
+        SmallDft<C, 16, INV>::run(o);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const int sk = 8 - k < 0 ? k - 8 : 8 - k;
+            const C t = k == 0 ? o[0] : rot(o[k], cos_pi16(k), cos_pi16(sk), INV);
+            v[k] = cadd(e[k], t);
+            v[k + 16] = csub(e[k], t);
+        }
+    }
+};
+
+// ---- one warp per line of 1024 points: two radix-32 Stockham stages --------------------------------
+// The line sits in shared memory in the padded layout (element i at pad(i)).  Lane j holds, on entry
+// to stage 1, the samples x[j + 32 r] (r = 0 .. 31) in v; stage 1 forms their 32-point DFT and stores
+// it at 32 j + r; stage 2 reads y[j + 32 r], applies the twiddles w_1024^(j r) and forms the second
+// 32-point DFT, leaving X[j + 32 r] in v (natural order).  Only __syncwarp separates the stages, so
+// the warps of a block proceed independently.  `s` may hold the stage-1 input (then the caller's
+// loads from s are complete before stage 1 stores: the __syncwarp at its start orders them).
+template <typename C, bool INV>
+__device__ __forceinline__ void fft1024_warp(C* v, C* s, const C* __restrict__ tw) {
+    const int j = threadIdx.x & 31;
+    SmallDft<C, 32, INV>::run(v);
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < 32; ++r) s[pad(32 * j + r)] = v[r];
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < 32; ++r) v[r] = s[pad(j + 32 * r)];
+#pragma unroll
+    for (int r = 1; r < 32; ++r) v[r] = cmul(v[r], twiddle(tw, j * r, INV));
+    SmallDft<C, 32, INV>::run(v);
+    __syncwarp();  // every lane's stage-2 reads are done before the caller stores into s
+}
+
 // tw[j] = exp(-2 pi i j / n) for j < n, evaluated in FP64 and rounded to the storage type.
 template <typename C>
 __global__ void k_twiddles(C* tw, int n) {

@@ -232,12 +232,11 @@ void add_spectral_nodes(msc_ctx* c, cudaGraph_t g, cudaError_t* err) {
         S.rows = n;
         S.P = rg.P;
         S.nscale = 1.0 / ((double)n * n);
-        cudaGraphNode_t n1 = add_kernel(g, {}, (const void*)k_rowfft_fwd<T>, dim3(rg.blocks), dim3(rg.threads),
-                                        spec_row_smem<T>(n, rg.P), args, err);
-        cudaGraphNode_t n2 = add_kernel(g, {n1}, (const void*)k_colsolve<T>, dim3(n / 4 + 1),
-                                        dim3(spec2_col_threads(n)), spec2_col_smem<T>(n), args, err);
-        add_kernel(g, {n2}, (const void*)k_rowfft_inv<T>, dim3(rg.blocks), dim3(rg.threads),
-                   spec_row_smem<T>(n, rg.P), args, err);
+        Spec2Launch L[3];
+        spectral2_launches<T>(n, L);
+        cudaGraphNode_t n1 = add_kernel(g, {}, L[0].fn, L[0].grid, L[0].block, L[0].smem, args, err);
+        cudaGraphNode_t n2 = add_kernel(g, {n1}, L[1].fn, L[1].grid, L[1].block, L[1].smem, args, err);
+        add_kernel(g, {n2}, L[2].fn, L[2].grid, L[2].block, L[2].smem, args, err);
     } else {
         LaunchDesc L[5];
         spectral3_launches<T>(n, L);
@@ -261,6 +260,10 @@ int set_smem_limits(int dim, int n) {
                                 (int)spec_row_smem<T>(n, rg.P)));
         CK(cudaFuncSetAttribute(k_colsolve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)spec2_col_smem<T>(n)));
+        Spec2Launch L[3];
+        spectral2_launches<T>(n, L);
+        for (int i = 0; i < 3; ++i)
+            CK(cudaFuncSetAttribute(L[i].fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L[i].smem));
     } else {
         if (set_spec3_smem_limits<T>(n) != 0) return MSC_ERR_CUDA;
         if (set_sweep3_smem_limits<T>(n) != 0) return MSC_ERR_CUDA;
@@ -503,9 +506,9 @@ int run_stepwise(msc_ctx* c, int n_steps) {
         S.rows = n;
         S.P = rg.P;
         S.nscale = 1.0 / ((double)n * n);
-        spec[0] = {(const void*)k_rowfft_fwd<T>, dim3(rg.blocks), dim3(rg.threads), spec_row_smem<T>(n, rg.P)};
-        spec[1] = {(const void*)k_colsolve<T>, dim3(n / 4 + 1), dim3(spec2_col_threads(n)), spec2_col_smem<T>(n)};
-        spec[2] = {(const void*)k_rowfft_inv<T>, dim3(rg.blocks), dim3(rg.threads), spec_row_smem<T>(n, rg.P)};
+        Spec2Launch SL[3];
+        spectral2_launches<T>(n, SL);
+        for (int i = 0; i < 3; ++i) spec[i] = {SL[i].fn, SL[i].grid, SL[i].block, SL[i].smem};
         nspec = 3;
     } else {
         spectral3_launches<T>(c->desc.n, spec);
@@ -1005,10 +1008,10 @@ int stage_shadow(int dim, int n, double a, double nu, const void* pr, void* dm, 
         A.kunit = 6.283185307179586476925286766559 / (double)n;
         A.nscale = 1.0 / ((double)n * n);
         A.st = nullptr;
-        k_rowfft_fwd<T><<<rg.blocks, rg.threads, spec_row_smem<T>(n, rg.P), stream>>>(A);
-        k_colsolve<T><<<n / 4 + 1, spec2_col_threads(n), spec2_col_smem<T>(n), stream>>>(A);
-        k_rowfft_inv<T><<<rg.blocks, rg.threads, spec_row_smem<T>(n, rg.P), stream>>>(A);
-        CK(cudaGetLastError());
+        Spec2Launch L[3];
+        spectral2_launches<T>(n, L);
+        void* args[] = {&A};
+        for (int i = 0; i < 3; ++i) CK(cudaLaunchKernel(L[i].fn, L[i].grid, L[i].block, args, L[i].smem, stream));
         return MSC_OK;
     }
     return launch_spectral3<T>(n, ilog2(n), a, nu, (const T*)pr, (C*)S.spec, (T*)dm, (const C*)S.tw, stream);

@@ -260,6 +260,33 @@ __device__ __forceinline__ void schur_apply_adjoint(C* v[D + 1], const double* k
     }
 }
 
+// The Schur solve of one (j_x, j_y) mode of the column pass in place on its three field values v
+// (zero outside the mask |j_y| <= n/4 or for a column past the last kept one)
+template <typename T, bool ADJ>
+__device__ __forceinline__ void solve_mode(const Spec2Args<T>& A, typename Cplx<T>::type* v[3], int jx, int jy,
+                                           bool live, double a, const double* tab) {
+    using C = typename Cplx<T>::type;
+    const int n = A.n, nx4 = n / 4 + 1;
+    const int jys = jy <= n / 2 ? jy : jy - n;
+    if (jys > n / 4 || jys < -(n / 4) || !live) {
+        C z; z.x = T(0); z.y = T(0);
+        *v[0] = z; *v[1] = z; *v[2] = z;
+        return;
+    }
+    double kv[2];
+    kv[0] = A.kunit * (double)jx;
+    kv[1] = A.kunit * (double)jys;
+    double cf[4];
+    if (tab) {
+        const double* tt = tab + 4 * ((size_t)(jys + n / 4) * nx4 + jx);
+        cf[0] = tt[0]; cf[1] = tt[1]; cf[2] = tt[2]; cf[3] = tt[3];
+    } else {
+        solve_coefficients(a, A.nu, kv[0] * kv[0] + kv[1] * kv[1], A.nscale, cf);
+    }
+    if (ADJ) schur_apply_adjoint<C, 2>(v, kv, cf);
+    else schur_apply<C, 2>(v, kv, cf);
+}
+
 // 2D: G consecutive kept j_x columns per block (G a power of two; the last block of a lattice may
 // hold fewer), all three fields of each.  Line (c, g) of the block sits at (c G + g) plen in shared memory.
 template <typename T, bool ADJ = false>
@@ -288,31 +315,11 @@ __device__ __forceinline__ void colsolve_block(const Spec2Args<T>& A, int bid, i
     fft_stockham<C, false>(s, n, logn, 3 * G, A.tw);
     const double a = A.st ? A.st->a : A.a;
     const double* tab = solve_table(A.coef, A.st, 2, n);
-    const double two_pi_n = A.kunit;
-    const double scale = A.nscale;
     for (int t = threadIdx.x; t < gn; t += blockDim.x) {
         const int g = t >> logn;
         const int jy = t & (n - 1);
-        const int jx = jx0 + g;
-        const int jys = jy <= n / 2 ? jy : jy - n;
         C* v[3] = {s + g * plen + pad(jy), s + (G + g) * plen + pad(jy), s + (2 * G + g) * plen + pad(jy)};
-        if (jys > n / 4 || jys < -(n / 4) || g >= ng) {
-            C z; z.x = T(0); z.y = T(0);
-            *v[0] = z; *v[1] = z; *v[2] = z;
-            continue;
-        }
-        double kv[2];
-        kv[0] = two_pi_n * (double)jx;
-        kv[1] = two_pi_n * (double)jys;
-        double cf[4];
-        if (tab) {
-            const double* tt = tab + 4 * ((size_t)(jys + n / 4) * nx4 + jx);
-            cf[0] = tt[0]; cf[1] = tt[1]; cf[2] = tt[2]; cf[3] = tt[3];
-        } else {
-            solve_coefficients(a, A.nu, kv[0] * kv[0] + kv[1] * kv[1], scale, cf);
-        }
-        if (ADJ) schur_apply_adjoint<C, 2>(v, kv, cf);
-        else schur_apply<C, 2>(v, kv, cf);
+        solve_mode<T, ADJ>(A, v, jx0 + g, jy, g < ng, a, tab);
     }
     __syncthreads();
     fft_stockham<C, true>(s, n, logn, 3 * G, A.tw);
@@ -341,6 +348,65 @@ inline int spec2_col_threads(int n) {
 template <typename T>
 inline size_t spec2_col_smem(int n) {
     return (size_t)3 * padded_len(n) * sizeof(typename Cplx<T>::type);
+}
+
+// ---- N = 1024 with FP32 working fields: the column pass with one warp per line ----------------------
+// The generic column pass synchronises the whole block between the radix stages of its transforms;
+// at N = 1024 (FP32, the benchmark size) this variant gives each 1024-point column line to one warp
+// (fft1024_warp: two radix-32 stages separated by __syncwarp), loads the first stage's samples
+// straight from global memory into registers and stores the last stage's outputs straight from
+// registers, both coalesced.  Same inputs, outputs and layout as k_colsolve (the transform differs
+// only in rounding order); the per-mode solve is the same function.  (The row passes stay generic:
+// written the same way they needed 170 and 232 registers per thread, which left too few warps per
+// SM, and ran slower than the block-synchronous versions.)
+// column pass at N = 1024: warp c transforms field c of kept column j_x = blockIdx.x
+__global__ void __launch_bounds__(96) k_colsolve_1024(Spec2Args<float> A) {
+    using C = float2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* s = reinterpret_cast<C*>(smem_raw);
+    constexpr int n = 1024;
+    const int plen = padded_len(n), nx4 = n / 4 + 1;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int jx = blockIdx.x;
+    C* col = A.spec + ((size_t)warp * nx4 + jx) * n;  // spec[c][jx][y], c = warp
+    C* line = s + warp * plen;
+    C v[32];
+#pragma unroll
+    for (int r = 0; r < 32; ++r) v[r] = col[lane + 32 * r];
+    fft1024_warp<C, false>(v, line, A.tw);
+#pragma unroll
+    for (int r = 0; r < 32; ++r) line[pad(lane + 32 * r)] = v[r];
+    __syncthreads();
+    const double a = A.st ? A.st->a : A.a;
+    const double* tab = solve_table(A.coef, A.st, 2, n);
+    for (int jy = threadIdx.x; jy < n; jy += blockDim.x) {
+        C* w[3] = {s + pad(jy), s + plen + pad(jy), s + 2 * plen + pad(jy)};
+        solve_mode<float, false>(A, w, jx, jy, true, a, tab);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 32; ++r) v[r] = line[pad(lane + 32 * r)];
+    fft1024_warp<C, true>(v, line, A.tw);
+#pragma unroll
+    for (int r = 0; r < 32; ++r) col[lane + 32 * r] = v[r];
+}
+
+// The three launches of the 2D shadow correction (row FFTs, column FFT + solve + inverse, inverse
+// row FFTs) for lattice size n and working type T, all taking one Spec2Args block.
+struct Spec2Launch {
+    const void* fn;
+    dim3 grid, block;
+    size_t smem;
+};
+template <typename T>
+inline void spectral2_launches(int n, Spec2Launch L[3]) {
+    const RowGeom rg = row_geometry(n, 3, n);
+    const size_t rsm = spec_row_smem<T>(n, rg.P);
+    L[0] = {(const void*)k_rowfft_fwd<T>, dim3(rg.blocks), dim3(rg.threads), rsm};
+    L[1] = {(const void*)k_colsolve<T>, dim3(n / 4 + 1), dim3(spec2_col_threads(n)), spec2_col_smem<T>(n)};
+    if (std::is_same<T, float>::value && n == 1024)
+        L[1] = {(const void*)k_colsolve_1024, dim3(n / 4 + 1), dim3(96), spec2_col_smem<T>(n)};
+    L[2] = {(const void*)k_rowfft_inv<T>, dim3(rg.blocks), dim3(rg.threads), rsm};
 }
 
 }  // namespace msc

@@ -54,12 +54,18 @@ __host__ __device__ constexpr int shift_slot(int k) { return k - (k > 0) - (k > 
 
 inline Sweep3Geom sweep3_geometry(int n, int elem) {
     Sweep3Geom g;
-    g.tyb = elem == 8 ? 8 : 16;
+    // 32 x 8 tiles in both precisions: at 127 registers per thread (FP32) a 512-thread block of 32 x 16
+    // leaves one block per SM, whose two barriers per plane stall all 16 warps at once; two
+    // independent 256-thread blocks per SM hide them better despite the extra halo rows (A/B at
+    // N = 128 FP32: tiles 32 x 16 with 16 planes 162 us, 32 x 8 with 16 planes 149 us, with 32 or 64
+    // planes 160-170 us; the march 5.10 -> 4.85 ms)
+    g.tyb = 8;
     g.nsx = (n + kStripOut - 1) / kStripOut;
     g.nsy = (n + (g.tyb - 2) - 1) / (g.tyb - 2);
+    const int target_blocks = elem == 8 ? 2 * 148 : 4 * 148;
     int hb = 4;
     for (int c = 64; c >= 4; c >>= 1) {
-        if (c <= n && g.nsx * g.nsy * (n / c) >= 2 * 148) { hb = c; break; }
+        if (c <= n && g.nsx * g.nsy * (n / c) >= target_blocks) { hb = c; break; }
     }
     if (hb > n) hb = n;
     g.hb = hb;

@@ -660,6 +660,8 @@ def run_phase(args):
     from paper_2609_39474_b300 import lattice as PL
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
+    if args.phase == "sweep3":
+        return {"phase": "sweep3", **sweep3_time(torch, PL, dev, reps=args.steps)}
     if args.phase == "sweep":
         return {"phase": "sweep", **sweep_time(torch, PL, dev, ROOF_N, reps=args.steps, precision=args.precision)}
     if args.phase == "batch-stage":
@@ -719,6 +721,31 @@ def sweep_time(torch, PL, dev, n, reps=20, precision="fp32"):
     ms = e0.elapsed_time(e1) / reps
     bps = SWEEP_BYTES_PER_SITE_FP16 if precision == "fp16" else SWEEP_BYTES_PER_SITE_FP32
     return {"n": n, "ms": ms, "gbs": bps * sites / (ms * 1e6), "bytes_per_site": bps, "precision": precision}
+
+
+SWEEP3_BYTES_PER_SITE_FP32 = 2 * 19 * 4 + 4 * (4 + 4 + 4)  # f in and out, h, dm, P r
+
+
+def sweep3_time(torch, PL, dev, n=128, reps=20):
+    """Mean duration (ms) of the fused D3Q19 FP32 sweep with the lift (stage call), CUDA events."""
+    f = torch.randn((19, n, n, n), device=dev, dtype=torch.float32) * 1e-3
+    h = torch.randn((4, n, n, n), device=dev, dtype=torch.float32) * 1e-4
+    dm = torch.randn((4, n, n, n), device=dev, dtype=torch.float32) * 1e-5
+    sc = PL.StageScratch(3, n, "fp32", dev)
+    for _ in range(3):
+        PL.sweep(3, n, "fp32", 0.01, f, h, dm, sc)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        PL.sweep(3, n, "fp32", 0.01, f, h, dm, sc)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    peak, src = load_peaks()
+    gbs = SWEEP3_BYTES_PER_SITE_FP32 * n ** 3 / (ms * 1e6)
+    return {"n": n, "ms": ms, "gbs": gbs, "frac": gbs / peak, "peak_source": f"{src} hbm_gbs",
+            "bytes_per_site": SWEEP3_BYTES_PER_SITE_FP32}
 
 
 def sweep_roofline(torch, PL, dev):
@@ -823,14 +850,15 @@ def main():
                     help="--phase batch-stage: a batch tiling as JSON (keys sweep_rows, fft_rows, col_lines, "
                          "sweep_ctas_per_sm) instead of autotuning, so that only the timed launches run")
     ap.add_argument("--phase", default="all",
-                    choices=["all", "msc", "msc-stepwise", "sweep", "batch", "batch-stage", "adjoint", "adjoint-stepwise",
-                             "offdesign"],
+                    choices=["all", "msc", "msc-stepwise", "sweep", "sweep3", "batch", "batch-stage", "adjoint",
+                             "adjoint-stepwise", "offdesign"],
                     help="profiling aids: 'msc' runs only the timed MSC marches of the default candidate, "
                          "'msc-stepwise' the same marches driven from the host (one launch per kernel, "
                          "visible to ncu), 'sweep' only the fused-sweep roofline loop, 'batch' only the "
                          "48-instance batched parameter sweep, 'batch-stage' the batch's kernels timed one "
                          "family at a time (stateless, visible to ncu), 'adjoint' the config-5 gradient, "
-                         "'adjoint-stepwise' 16 steps of it driven from the host (visible to ncu)")
+                         "'adjoint-stepwise' 16 steps of it driven from the host (visible to ncu), 'sweep3' the "
+                         "D3Q19 FP32 sweep at N = 128")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
 

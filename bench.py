@@ -121,6 +121,17 @@ class ClockSampler:
 # our arm: the CUDA library through its Python binding
 # ---------------------------------------------------------------------------------------------------
 
+def max_over_ranks(dist, x, device):
+    """x of the slowest replica: the largest value over the ranks of the process group (x itself on
+    one GPU).  Replicas run independent instances; this is their only exchange."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def measure_workload(torch, PL, dev, dim, n, steps, warmup, dist=None, full=False, precision="fp32",
                      explicit_ref=None):
     """Explicit baseline, candidate search, timed MSC marches (and, for the headline, e2e).
@@ -152,7 +163,7 @@ def measure_workload(torch, PL, dev, dim, n, steps, warmup, dist=None, full=Fals
 
     L.init_fields(p_d, u_d)
     L.explicit_march(10)  # builds and warms the explicit graph
-    t_ex = min(explicit_once() for _ in range(2))
+    t_ex = max_over_ranks(dist, min(explicit_once() for _ in range(2)), dev)
     u_ex = L.fields()[1].cpu().numpy()
     e_ex = velocity_error(u_ex, u_ref)
     t_ex_own, e_ex_own = t_ex, e_ex
@@ -213,12 +224,7 @@ def measure_workload(torch, PL, dev, dim, n, steps, warmup, dist=None, full=Fals
         launches += 2 + 4 * S + st["inner_total"] + nspec * (st["inner_total"] - S)
     torch.cuda.synchronize()
     clk = clocks.stop() if clocks else None
-    ms_step = statistics.mean(times)
-    if dist is not None:
-        import torch.distributed as tdist
-        t = torch.tensor([ms_step], device=dev)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = max_over_ranks(dist, statistics.mean(times), dev)
     u_msc = L.fields()[1].cpu().numpy()
     e_msc = velocity_error(u_msc, u_ref)
     # diagnostics of the last timed march (Eqs. rho-observed, swork)

@@ -97,3 +97,42 @@ def test_batch_rejects_invalid_lists_without_a_device(L):
     assert L.lib.msc_batch_create(ctypes.byref(h), None, 0, None, 0, None) == L.MSC_ERR_ARG
     assert L.lib.msc_batch_march(None, None) == L.MSC_ERR_ARG
     assert L.lib.msc_batch_autotune(None, 1, None) == L.MSC_ERR_ARG
+
+
+def test_adjoint_io_struct_matches_header(L, tmp_path):
+    # the ctypes mirror of msc_adjoint_io has the C layout (size and the offsets around the padding)
+    src = tmp_path / "t.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "msclbm.h"\nint main(void){'
+                   'printf("%zu %zu %zu %zu\\n", sizeof(msc_adjoint_io), offsetof(msc_adjoint_io, m_new),'
+                   ' offsetof(msc_adjoint_io, abar_prev), offsetof(msc_adjoint_io, warm)); return 0; }\n')
+    import subprocess
+    exe = tmp_path / "t"
+    r = subprocess.run(["gcc", "-std=c99", str(src), "-I", os.path.dirname(HEADER), "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
+    S = L.AdjointIO
+    assert got == [ctypes.sizeof(S), S.m_new.offset, S.abar_prev.offset, S.warm.offset]
+
+
+def test_new_entry_points_reject_bad_arguments_without_a_device(L):
+    fp64, fp32 = L.MSC_FP64, L.MSC_FP32
+    # full-symbol scratch: twiddles (n complex) + 9 x (n/2 + 1) x n complex, each 256-byte aligned
+    for n, prec, cb in ((64, fp64, 16), (1024, fp32, 8)):
+        want = -(-n * cb // 256) * 256 + -(-9 * (n // 2 + 1) * n * cb // 256) * 256
+        assert L.lib.msc_full_symbol_scratch_bytes(n, prec) == want
+    for n, prec in ((2048, fp32), (100, fp64), (4, fp64), (64, L.MSC_FP16)):
+        assert L.lib.msc_full_symbol_scratch_bytes(n, prec) == 0
+    buf = ctypes.c_void_p(256)  # never dereferenced: every call below fails its host-side checks
+    assert L.lib.msc_full_symbol_correct(2048, fp32, 0.1, 1.0, 1.0, buf, buf, buf, buf, 1 << 40, None) == L.MSC_ERR_ARG
+    assert L.lib.msc_full_symbol_correct(64, fp64, 0.1, 2.0, 1.0, buf, buf, buf, buf, 1 << 40, None) == L.MSC_ERR_ARG
+    assert L.lib.msc_full_symbol_correct(64, fp64, 0.0, 1.0, 1.0, buf, buf, buf, buf, 1 << 40, None) == L.MSC_ERR_ARG
+    assert L.lib.msc_full_symbol_correct(64, fp64, 0.1, 1.0, 1.0, None, buf, buf, buf, 1 << 40, None) == L.MSC_ERR_ARG
+    assert L.lib.msc_full_symbol_correct(64, fp64, 0.1, 1.0, 1.0, buf, buf, buf, buf, 16, None) == L.MSC_ERR_ARG
+    assert L.lib.msc_full_symbol_correct(64, fp64, 0.1, 1.0, 1.0, buf, buf, buf, ctypes.c_void_p(264), 1 << 40,
+                                         None) == L.MSC_ERR_ARG  # scratch not 256-byte aligned
+    io = (L.AdjointIO * 1)()
+    out = (L.AdjointStats * 1)()
+    assert L.lib.msc_adjoint_steps(None, 1, io, buf, 1e-8, 10, out) == L.MSC_ERR_ARG
+    assert L.lib.msc_adjoint_step(None, 1, buf, buf, None, buf, buf, None, buf, 1e-8, 10, None) == L.MSC_ERR_ARG
+    assert L.lib.msc_copy_fields_async(None, buf) == L.MSC_ERR_ARG

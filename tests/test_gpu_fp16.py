@@ -143,3 +143,45 @@ def test_fp16_full_size_march_runs_at_a_few_iterations():
     s = L.stats()
     assert s["status"] == 0 and s["steps_done"] == 8
     assert np.all(L.step_iters() <= 6)
+
+
+@pytest.mark.parametrize("nu,lam", [(0.12, 0.25), (1 / 6, 0.05), (0.25, 1.0)])
+def test_fp16_trt_sweep_within_one_ulp_of_the_oracle(nu, lam):
+    # the general TRT collision (Eq. collision) with binary16 storage: the same one-ulp bar
+    from oracle import fullsymbol as FS
+    PL = _lib()
+    lat = lattice_for_dim(2)
+    n = 64
+    wp, wm = FS.trt_rates(nu, lam)
+    f = 0.5 + random_populations(9, (n, n), seed=4, scale=0.2)
+    h = random_moments(2, (n, n), seed=5, scale=1e-2)
+    dm = random_moments(2, (n, n), seed=6, scale=1e-2)
+    f_s, h_s, dm_s = dev(f, torch.float16), dev(h, torch.float32), dev(dm, torch.float32)
+    a = 0.05
+    f_out, pr, ss = PL.sweep_trt(n, "fp16", a, wp, wm, f_s, h_s, dm_s)
+    torch.cuda.synchronize()
+    trial = host(f_s) + OK.linear_lift(lat, host(dm_s))
+    f_T = OSW.sweep(lat, trial, a, host(h_s), omega=(wp, wm))
+    r, _ = OSW.residual(f_T, trial)
+    assert np.max(_ulps16(host(f_out), f_T)) <= 1.0
+    assert rel_l2(host(pr), OK.moments(lat, r)) < 1e-5
+    assert abs(float(ss.item()) / float(np.sum(r * r)) - 1) < 1e-5
+
+
+def test_fp16_adjoint_gradients_track_fp32():
+    # the discrete adjoint on a binary16-storage march (FP32 fields, FP64 history and solve): its
+    # gradients follow the FP32-storage ones to the storage format's relative precision
+    from paper_2609_39474_b300.adjoint import MarchRunner
+    N, S, dt = 64, 8, 24.0
+    nu = 1.0 / 6.0
+    p0, u0 = random_phase(N, 2, 1.0, seed=3, kmax=8)
+    pt, ut = random_phase(N, 2, 1.0, seed=2, kmax=8)
+    grads = {}
+    for prec in ("fp32", "fp16"):
+        # eps above the binary16 rounding floor (~1e-4 U), the same for both storages
+        R = MarchRunner(_lib().MscLattice(2, N, prec), dt=dt, steps=S, eps=2e-4 * nu / N, checkpoint_every=4,
+                        eps_adjoint=1e-5)
+        uS = R.forward(dev(p0), dev(u0))
+        grads[prec] = R.backward(uS - dev(ut))
+    for a, b in zip(grads["fp16"][1:], grads["fp32"][1:]):
+        assert rel_l2(host(a), host(b)) < 5e-3

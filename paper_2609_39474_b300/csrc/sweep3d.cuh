@@ -72,7 +72,7 @@ inline Sweep3Geom sweep3_geometry(int n, int elem) {
     g.nzblk = n / hb;
     g.blocks = g.nsx * g.nsy * g.nzblk;
     g.threads = 32 * g.tyb;
-    g.smem = (size_t)16 * g.tyb * 32 * elem;
+    g.smem = (size_t)2 * 16 * g.tyb * 32 * elem;  // two exchange buffers, alternating by plane
     return g;
 }
 
@@ -80,7 +80,7 @@ template <typename T, bool EXPLICIT, bool GRAPH>
 __global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 512) k_sweep3(Sweep3Args<T> A) {
     using L = D3Q19;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* sC = reinterpret_cast<T*>(smem_raw);  // [16][TYB][32]
+    T* sC0 = reinterpret_cast<T*>(smem_raw);  // [2][16][TYB][32]: plane j uses buffer j & 1
     const int tyb = A.g.tyb;
     const int tx = threadIdx.x & 31;
     const int ty = threadIdx.x >> 5;
@@ -178,7 +178,10 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 512) k_sweep3(Sweep3Arg
             const T cs = T(L::cx(k)) * sxx + T(L::cy(k)) * syy + T(L::cz(k)) * szz;
             C[k] = (T)L::w(k) * (A0 + T(3) * cu + T(1.5) * cs + T(4.5) * cu * (cu + cs));
         }
-        // x/y streaming through shared memory
+        // x/y streaming through shared memory: the planes alternate between two buffers, so one
+        // barrier per plane suffices (a buffer is rewritten two planes later, after every thread
+        // has passed the barrier of the plane in between, hence finished reading it)
+        T* sC = sC0 + (size_t)(j & 1) * 16 * tyb * 32;
 #pragma unroll
         for (int k = 0; k < 19; ++k)
             if (L::cx(k) != 0 || L::cy(k) != 0) sC[(shift_slot(k) * tyb + ty) * 32 + tx] = C[k];
@@ -189,7 +192,6 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 512) k_sweep3(Sweep3Arg
                 if (L::cx(k) != 0 || L::cy(k) != 0)
                     C[k] = sC[(shift_slot(k) * tyb + (ty - L::cy(k))) * 32 + (tx - L::cx(k))];
         }
-        __syncthreads();
         // plane j-1 receives the c_z = -1 directions and is complete
 #pragma unroll
         for (int k = 0; k < 19; ++k)

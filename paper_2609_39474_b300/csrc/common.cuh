@@ -84,6 +84,7 @@ struct DevState {
     double inv_a;           // 1 / (1 + a_q / 2)
     double c1, c2;          // h_q = c1 m^n - c2 m^{n-1}
     double n1, n2;          // BDF2 coefficients 4 / (2 dt), 1 / (2 dt) of the next step
+    double qa[2], qinv[2], qc1[2], qc2[2];  // a_q, 1 / (1 + a_q / 2), c1, c2 for q = 1, 2 (set with dt)
     double isig;            // 1 / fscale
     int iter;               // inner iterations done in the current step
     int lift;               // next sweep applies f = f_cur + E dm

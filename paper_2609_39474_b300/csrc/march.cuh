@@ -332,17 +332,31 @@ __global__ void __launch_bounds__(kFieldThreads) k_copy_fields(const DevState* s
 
 // ---- single-thread control kernels ------------------------------------------------------------
 
-__device__ inline void set_step_constants(DevState* st) {
+// the step constants of BDF order q = 1, 2 (Eq. bdf2), formed once per dt by tabulate_step_constants:
+// a single-thread control kernel would otherwise run five FP64 divisions on every physical step
+__device__ inline void tabulate_step_constants(DevState* st) {
     const double dt = st->dt;
-    st->a = st->q == 1 ? 1.0 / dt : 3.0 / (2.0 * dt);
-    st->inv_a = 1.0 / (1.0 + st->a / 2.0);
-    st->c1 = st->q == 1 ? 1.0 / dt : 4.0 / (2.0 * dt);
-    st->c2 = st->q == 1 ? 0.0 : 1.0 / (2.0 * dt);
+    st->qa[0] = 1.0 / dt;
+    st->qa[1] = 3.0 / (2.0 * dt);
+    for (int i = 0; i < 2; ++i) st->qinv[i] = 1.0 / (1.0 + st->qa[i] / 2.0);
+    st->qc1[0] = 1.0 / dt;
+    st->qc1[1] = 4.0 / (2.0 * dt);
+    st->qc2[0] = 0.0;
+    st->qc2[1] = 1.0 / (2.0 * dt);
+}
+
+__device__ inline void set_step_constants(DevState* st) {
+    const int i = st->q == 1 ? 0 : 1;
+    st->a = st->qa[i];
+    st->inv_a = st->qinv[i];
+    st->c1 = st->qc1[i];
+    st->c2 = st->qc2[i];
 }
 
 __global__ void k_set_params(DevState* st, msc_params p) {
     st->nu = p.nu;
     st->dt = p.dt;
+    tabulate_step_constants(st);
     st->n1 = 4.0 / (2.0 * p.dt);
     st->n2 = 1.0 / (2.0 * p.dt);
     st->eps = p.eps;

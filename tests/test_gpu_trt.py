@@ -106,3 +106,50 @@ def test_shadow_correction_off_design_contraction():
     assert rho[1 / 6][0] == 0 and rho[1 / 6][1] < 0.15
     assert rho[0.12][0] == 0 and 0.2 < rho[0.12][1] < 0.6
     assert rho[0.10][0] != 0 and rho[0.10][1] > 1.0
+
+
+def _mode_fields(N, jvec, amp):
+    x = np.arange(N)
+    ph = 2 * np.pi * (jvec[0] * x[None, :] + jvec[1] * x[:, None]) / N
+    return amp * np.cos(ph), np.stack([0.3 * amp * np.sin(ph), -0.7 * amp * np.cos(ph + 0.4)])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("nu,lam,jvec", [(0.1, 0.25, (8, 8)), (0.12, 0.25, (8, -8)), (0.14, 0.25, (8, 0)),
+                                         (1 / 6, 2.0, (4, 2)), (0.25, 0.05, (4, 2))])
+def test_off_design_contraction_matches_the_linear_symbol(nu, lam, jvec, precision):
+    # The linear Fourier analysis of Section 4.6 on the GPU march: a 1e-12 single mode, one BDF1 step
+    # with the general TRT sweep and the shadow correction, no acceptance (eps = 0, 60 inner
+    # iterations).  Each inner residual shrinks or grows by the spectral radius of the oracle's
+    # linearised corrected iteration G(k) (the mask corner diverges at nu = 0.10 and 0.12), and the
+    # whole residual history matches the oracle march.
+    from oracle import linear as OL
+    from paper_2609_39474_b300 import diagnostics as DG
+    PL = _PL()
+    N, dt, K = 32, 20.0, 60
+    omega = FS.trt_rates(nu, lam)
+    k = 2 * np.pi * np.array(jvec) / N
+    rho = OL.spectral_radius(OL.trt_corrected_symbol(D2Q9, k, 1.0 / dt, nu, omega))
+    p, u = _mode_fields(N, jvec, 1e-12)
+    L = PL.MscLattice(2, N, precision)
+    L.set_params(dt=dt, eps=0.0, nu=nu, kmax=K, omega=omega)
+    L.init_fields(p, u)
+    L.march(1)
+    s = L.stats()
+    R = L.residual_history()
+    L.close()
+    assert s["status"] != 0 and s["steps_done"] == 0 and len(R) == K
+    assert (rho > 1) == (nu <= 0.12)
+    Ro = np.asarray(OM.physical_step(OM.init_state(D2Q9, p, u),
+                                     OM.MarchParams(dt=dt, nu=nu, eps=0.0, kmax=K, omega=omega)).residuals)
+    if precision == "fp64":
+        assert abs(DG.rho_observed(R, 10) / rho - 1) < 1e-6
+        # to 1e-9 of each residual, or to rounding of the mode (1e-14 R_0) once it has decayed
+        assert np.all(np.abs(R - Ro) < 1e-9 * Ro + 1e-14 * Ro[0])
+    else:
+        # binary32 populations round at ~1e-7 of the mode's amplitude (~1e-6 R_0): the history to 1e-3
+        # above that floor, and the rate where at least 20 residuals stay above 1e-4 R_0
+        assert np.all(np.abs(R - Ro) < 1e-3 * Ro + 1e-5 * Ro[0])
+        above = R[:int(np.argmax(R < 1e-4 * R[0]))] if np.any(R < 1e-4 * R[0]) else R
+        if len(above) >= 20:
+            assert abs(DG.rho_observed(above, 10) / rho - 1) < 2e-3

@@ -83,6 +83,7 @@ struct DevState {
     // division costs ~10 FP64 instructions on a pipe that runs at ~1/58 of the FP32 rate)
     double inv_a;           // 1 / (1 + a_q / 2)
     double c1, c2;          // h_q = c1 m^n - c2 m^{n-1}
+    double k1, k2;          // c1 inv_a / 2, c2 inv_a / 2: the history weights of the reconstruction
     double n1, n2;          // BDF2 coefficients 4 / (2 dt), 1 / (2 dt) of the next step
     double qa[2], qinv[2], qc1[2], qc2[2];  // a_q, 1 / (1 + a_q / 2), c1, c2 for q = 1, 2 (set with dt)
     double isig;            // 1 / fscale

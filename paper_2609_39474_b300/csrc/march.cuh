@@ -28,7 +28,7 @@ __device__ __forceinline__ double cdotu(int k, const double* u) {
 template <typename T>
 __device__ __forceinline__ T bdf_history(double c1, double ma, double c2, double mb, double fc) {
     if constexpr (std::is_same<T, float>::value)
-        return fmaf((float)c1, narrow_f64(ma), fmaf(-(float)c2, narrow_f64(mb), (float)fc));
+        return fmaf(narrow_f64(c1), narrow_f64(ma), fmaf(-narrow_f64(c2), narrow_f64(mb), narrow_f64(fc)));
     else
         return (T)fma(c1, ma, fma(-c2, mb, fc));
 }
@@ -152,7 +152,7 @@ __device__ __forceinline__ void step_begin_range(const DevState* __restrict__ st
     const double c1 = vs->c1, c2 = vs->c2;
     (void)q;
     (void)dt;
-    const T sig = (T)vs->fscale, isig = (T)vs->isig;
+    const T sig = from_f64<T>(vs->fscale), isig = from_f64<T>(vs->isig);
     const double fc[4] = {0.0, vs->force[0], vs->force[1], vs->force[2]};
     for (size_t i = i0; i < sites; i += istride) {
 #pragma unroll
@@ -201,7 +201,6 @@ __device__ __forceinline__ void step_end_range(const DevState* __restrict__ st, 
     if (!vs->accepted) return;
     const double inv = vs->inv_a;
     const size_t mstride = (size_t)(L::D + 1) * sites;
-    const double c1 = vs->c1, c2 = vs->c2;
     const bool next = vs->status == MSC_OK && vs->steps_target > 1;
     int nav = vs->n_avail + 1 < 3 ? vs->n_avail + 1 : 3;  // accepted states after rotation
     if (nav > vs->warm_order) nav = vs->warm_order;
@@ -213,9 +212,9 @@ __device__ __forceinline__ void step_end_range(const DevState* __restrict__ st, 
     const S* __restrict__ f0 = fbase + (size_t)vs->slot_fn[0] * fstride;
     const S* __restrict__ f1 = fbase + (size_t)vs->slot_fn[1] * fstride;
     S* __restrict__ trial = fbase + (size_t)vs->slot_nxt * fstride;
-    const T sig = (T)vs->fscale, isig = (T)vs->isig;
+    const T sig = from_f64<T>(vs->fscale), isig = from_f64<T>(vs->isig);
     const double n1 = vs->n1, n2 = vs->n2;  // BDF2 for the next step
-    const double k1 = 0.5 * c1 * inv, k2 = 0.5 * c2 * inv;
+    const double k1 = vs->k1, k2 = vs->k2;  // formed once per step (FP64 products are slow on B300)
     // body force: (0, F) joins h in the reconstruction and in the next step's h (FORCE = false: F = 0)
     const double fc[4] = {0.0, FORCE ? vs->force[0] : 0.0, FORCE ? vs->force[1] : 0.0, FORCE ? vs->force[2] : 0.0};
     const double kf[4] = {0.0, 0.5 * inv * fc[1], 0.5 * inv * fc[2], 0.5 * inv * fc[3]};
@@ -351,6 +350,8 @@ __device__ inline void set_step_constants(DevState* st) {
     st->inv_a = st->qinv[i];
     st->c1 = st->qc1[i];
     st->c2 = st->qc2[i];
+    st->k1 = 0.5 * st->c1 * st->inv_a;
+    st->k2 = 0.5 * st->c2 * st->inv_a;
 }
 
 __global__ void k_set_params(DevState* st, msc_params p) {

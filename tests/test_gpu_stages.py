@@ -129,3 +129,55 @@ def test_integer_pipe_conversions_match_the_hardware():
     bad = ctypes.c_int(-1)
     assert L.lib.msc_selftest_conversions(64, 1024, 12345, ctypes.byref(bad)) == 0
     assert bad.value == 0
+
+
+def _periodic_window(t, starts, size):
+    """Rows starts[i] - 1 .. starts[i] + size of each grid axis of the device tensor t (C, *grid), with
+    periodic wrap, as a host array: a window whose interior sweeps exactly like the full grid."""
+    n = t.shape[1]
+    idx = [torch.as_tensor(np.arange(s - 1, s + size + 1) % n, device=t.device) for s in starts]
+    w = t
+    for ax, ix in enumerate(idx):
+        w = torch.index_select(w, 1 + ax, ix)
+    return host(w)
+
+
+@pytest.mark.parametrize("dim,n,precision", [(2, 4096, "fp32"), (2, 2048, "fp64"), (3, 256, "fp32"),
+                                             (3, 128, "fp64")])
+def test_sweep_at_the_largest_sizes_sampled(dim, n, precision):
+    # the largest lattices each precision supports (D2Q9 N = 4096 is also the size of the benchmark's
+    # roofline loop): the oracle sweeps small periodic windows around sampled sites (the wrap-around
+    # corners, strip and tile boundaries, the ragged last strip) whose interiors are exact, and the
+    # reported sum r^2 equals the norm of the GPU outputs' own residual
+    PL = _lib()
+    lat = lattice_for_dim(dim)
+    shape = (n,) * dim
+    T = PL.storage_dtype(precision)
+    a = 0.05
+    f_s = dev(random_populations(lat.Q, shape, seed=11, scale=1e-3), T)
+    h_s = dev(random_moments(dim, shape, seed=12, scale=1e-4), T)
+    dm_s = dev(random_moments(dim, shape, seed=13, scale=1e-4), T)
+    f_out, pr, ss = PL.sweep(dim, n, precision, a, f_s, h_s, dm_s)
+    torch.cuda.synchronize()
+    size = 8 if dim == 2 else 4
+    last = n - size
+    picks = [0, last, 29, 30 * (n // 30) - 3, n // 2 - 1] if dim == 2 else [0, last, 28, 5, n // 2 - 2]
+    corners = [(picks[i], picks[(i + 1) % len(picks)], picks[(i + 2) % len(picks)]) for i in range(len(picks))]
+    tol = TOL[precision]
+    for c in corners:
+        starts = c[:dim]
+        f_w = _periodic_window(f_s, starts, size)
+        trial = f_w + OK.linear_lift(lat, _periodic_window(dm_s, starts, size))
+        f_T = OSW.sweep(lat, trial, a, _periodic_window(h_s, starts, size))
+        inner = (slice(None),) + (slice(1, -1),) * dim
+        r = (f_T - trial)[inner]
+        assert rel_l2(_periodic_window(f_out, starts, size)[inner], f_T[inner]) < tol["f"]
+        assert rel_l2(_periodic_window(pr, starts, size)[inner], OK.moments(lat, r)) < tol["pr"]
+    # sum r^2 against the outputs' residual, r = f_out - (f + E dm), formed in FP64 on the device
+    w = torch.as_tensor(lat.w, dtype=torch.float64, device="cuda")
+    c = torch.as_tensor(lat.c, dtype=torch.float64, device="cuda")
+    ssq = 0.0
+    for k in range(lat.Q):
+        lift = w[k] * (dm_s[0].double() + 3.0 * sum(c[k, al] * dm_s[1 + al].double() for al in range(dim)))
+        ssq += float(((f_out[k].double() - f_s[k].double() - lift) ** 2).sum())
+    assert abs(float(ss.item()) / ssq - 1) < tol["ss"]

@@ -181,3 +181,44 @@ def test_sweep_at_the_largest_sizes_sampled(dim, n, precision):
         lift = w[k] * (dm_s[0].double() + 3.0 * sum(c[k, al] * dm_s[1 + al].double() for al in range(dim)))
         ssq += float(((f_out[k].double() - f_s[k].double() - lift) ** 2).sum())
     assert abs(float(ss.item()) / ssq - 1) < tol["ss"]
+
+
+@pytest.mark.parametrize("dim,n,precision", [(2, 4096, "fp32"), (2, 2048, "fp64"), (3, 256, "fp32"),
+                                             (3, 128, "fp64")])
+def test_shadow_solve_at_the_largest_sizes_single_modes(dim, n, precision):
+    # The shadow solve is linear and diagonal in k (Eqs. shadow-update, schur): a cosine mode in
+    # moment field q comes back as Re(H(k)^{-1} e_q e^{ik.x}) inside the mask (|j_alpha| <= N/4,
+    # the edge included) and as zero outside it; checked on the whole field at the largest lattices
+    PL = _lib()
+    a, nu = 3.0 / (2 * 64.0), 1.0 / 6.0
+    T = PL.storage_dtype(precision)
+    q4 = n // 4
+    if dim == 2:
+        modes = [((3, -5), 0), ((q4, q4), 1), ((-q4, 7), 2), ((0, 0), 0), ((q4 + 1, 2), 1), ((1, -q4 - 3), 2)]
+    else:
+        modes = [((1, 2, -3), 0), ((q4, 0, -q4), 3), ((0, q4, 5), 1), ((0, 0, 0), 2), ((q4 + 1, 0, 0), 1),
+                 ((2, 1, q4 + 2), 3)]
+    grids = np.meshgrid(*([np.arange(n, dtype=np.int64)] * dim), indexing="ij")  # (z,) y, x
+    tol = 1e-12 if precision == "fp64" else 5e-6  # binary32 transforms of 2 x 12 radix-2 levels
+    for j, q in modes:
+        # phase 2 pi (j . x) / N with the integer part reduced exactly; j[alpha] pairs with grid axis d-1-alpha
+        iph = sum(j[al] * grids[dim - 1 - al] for al in range(dim)) % n
+        ph = iph.astype(np.float64) * (2 * np.pi / n)
+        pr = torch.zeros((dim + 1,) + (n,) * dim, dtype=T, device="cuda")
+        pr[q] = torch.as_tensor(np.cos(ph), device="cuda").to(T)
+        dm = PL.shadow_solve(dim, n, precision, a, nu, pr)
+        torch.cuda.synchronize()
+        dm = host(dm)
+        inside = all(abs(v) <= q4 for v in j)
+        if not inside:
+            assert np.max(np.abs(dm)) < tol / a
+            continue
+        e = np.zeros(dim + 1)
+        e[q] = 1.0
+        kvec = [2 * np.pi * j[al] / n for al in range(dim)]
+        dp, du = OS.schur_solve(np.complex128(e[0]), e[1:].astype(np.complex128), kvec, a, nu)
+        sol = [dp] + [du[al] for al in range(dim)]
+        z = np.exp(1j * ph)
+        ref = np.stack([np.real(sol[c] * z) for c in range(dim + 1)])
+        del z
+        assert rel_l2(dm, ref) < tol

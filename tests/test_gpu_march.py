@@ -253,6 +253,37 @@ def test_full_size_march_conserves_and_converges():
     assert max(abs(a - b) for a, b in zip(m0, m1)) < 1e-6 * scale
 
 
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_benchmark_configuration_matches_oracle(precision):
+    # The benchmark's workload itself: D2Q9 N = 1024, the random-phase field of seed 1 at Re = 1, the
+    # headline candidate's step dt = T_end / 16 (T_end = nint(0.15 N^2)) and eps = 1e-6, through the
+    # BDF1 starter and one BDF2 step, with each precision's default warm start and pairing; the GPU
+    # replays the oracle's inner counts.
+    # Gate, derived from the arithmetic: the sweep forms the residual moments P r from |f|-sized terms,
+    # so their rounding is ~3 unit roundoffs of max|f| per site whatever |r| is, and the Schur solve
+    # (Eq. schur) divides the long waves by a + nu |k|^2; at this step a_1 = 1/dt ~ 1e-4, so that
+    # rounding reaches u amplified by A = 1/(a_1 + nu k_1^2) ~ 9.3e3:
+    #   bound = A * 3 u_r * max|f^0| / rms(u^0)   (binary32: 1.5e-3, binary64: 2.8e-12).
+    N = 1024
+    p, u = random_phase(N, 2, 1.0, seed=1)
+    fp32 = precision == "fp32"
+    prm = OM.MarchParams(dt=nint(0.15 * N * N) / 16, eps=1e-6, nmin=2, warm_order=2 if fp32 else 3,
+                         count_multiple=2 if fp32 else 1)
+    st = OM.init_state(lattice_for_dim(2), p, u)
+    recs = OM.march(st, prm, 2)
+    assert all(r.converged for r in recs)
+    L = _replay_run(2, N, precision, p, u, prm, [r.iters for r in recs])
+    assert L.stats()["status"] == 0 and L.stats()["steps_done"] == 2
+    _, uu = L.fields()
+    k1 = 2 * np.pi / N
+    A = 1.0 / (1.0 / prm.dt + prm.nu * k1 * k1)
+    f0 = OK.feq(lattice_for_dim(2), p, u)
+    bound = A * 3 * (2.0 ** -24 if fp32 else 2.0 ** -53) * np.max(np.abs(f0)) / np.sqrt(np.mean(u * u))
+    # the gate is on u; p_hat of this field is the quadratic (Poisson) pressure, O(U^2), so its relative
+    # error is not informative at this size
+    assert rel_l2(host(uu), st.m_n[1:]) < bound
+
+
 @pytest.mark.parametrize("dim,N,precision", [(2, 64, "fp64"), (2, 128, "fp32"), (3, 16, "fp64")])
 def test_stepwise_march_equals_graph_march(dim, N, precision):
     # the host-driven march launches the same kernels: identical bits to the graph march

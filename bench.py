@@ -772,7 +772,7 @@ def sweep_roofline(torch, PL, dev):
 def kernel_hash():
     import hashlib
     hsh = hashlib.sha256()
-    for f in ("sweep2d.cuh",):
+    for f in ("sweep2d.cuh", "common.cuh"):  # the sweep and the device helpers it inlines
         with open(os.path.join(ROOT, "paper_2609_39474_b300", "csrc", f), "rb") as fh:
             hsh.update(fh.read())
     return hsh.hexdigest()[:16]

@@ -167,6 +167,23 @@ __device__ __forceinline__ double to_f64(T x) {
     if constexpr (std::is_same<T, float>::value) return widen_f32(x);
     else return (double)x;
 }
+// w x for a lattice weight w (a compile-time constant).  In binary32 the weight is split into its
+// rounded value and the remainder, w = hi + lo, and the product formed as fma(x, hi, x lo): one
+// rounding and no bias from the rounded weight.  1/9, 1/36, 4/9 (and 1/3, 1/18) are not binary32
+// numbers, and their fixed relative errors would shift the moments of every site's collision
+// output by the same relative amount; the shadow solve divides the long waves of such a coherent
+// shift by a + nu |k|^2 (Eq. schur), which at large physical steps is ~1e-4.
+template <typename T>
+__device__ __forceinline__ T wmul(double w, T x) {
+    if constexpr (std::is_same<T, float>::value) {
+        const float hi = (float)w;
+        const float lo = (float)(w - (double)hi);
+        return fmaf(x, hi, x * lo);
+    } else {
+        return (T)w * x;
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ T from_f64(double x) {
     if constexpr (std::is_same<T, float>::value) return narrow_f64(x);

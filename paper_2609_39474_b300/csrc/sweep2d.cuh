@@ -141,7 +141,7 @@ __device__ __forceinline__ double sweep2_unit(const S* fin, const T* dm, const T
         if (!EXPLICIT && lift) {  // trial f = f_T,prev + E dm   (Eq. lift)
 #pragma unroll
             for (int k = 0; k < 9; ++k)
-                f[k] += (T)L::w(k) * (dp + T(3) * (T(L::cx(k)) * dux + T(L::cy(k)) * duy));
+                f[k] += wmul<T>(L::w(k), dp + T(3) * (T(L::cx(k)) * dux + T(L::cy(k)) * duy));
         }
         // moments (Eq. moments)
         T rho = T(0), jx = T(0), jy = T(0);
@@ -155,9 +155,13 @@ __device__ __forceinline__ double sweep2_unit(const S* fin, const T* dm, const T
         if (EXPLICIT) {
             p = rho; ux = jx; uy = jy;
         } else {  // half-source reconstruction and source moments (Eqs. macro-reconstruct, source-moments)
-            p = (rho + h0 * T(0.5)) * inv;
-            ux = (jx + h1 * T(0.5)) * inv;
-            uy = (jy + h2 * T(0.5)) * inv;
+            // m = (P f + h/2) / (1 + a/2) written as P f + (h - a P f) / (2 (1 + a/2)): the rounded
+            // 1/(1 + a/2) then scales only the O(a) term, not m itself, so it cannot bias the moments
+            // by a relative unit roundoff (which the long-wave solve would amplify by ~1/a)
+            const T hinv = T(0.5) * inv;
+            p = rho + (h0 - a * rho) * hinv;
+            ux = jx + (h1 - a * jx) * hinv;
+            uy = jy + (h2 - a * jy) * hinv;
             s0 = h0 - a * p;
             sx = h1 - a * ux;
             sy = h2 - a * uy;
@@ -170,7 +174,7 @@ __device__ __forceinline__ double sweep2_unit(const S* fin, const T* dm, const T
             for (int k = 0; k < 9; ++k) {
                 const T cu = T(L::cx(k)) * ux + T(L::cy(k)) * uy;
                 const T cs = T(L::cx(k)) * sx + T(L::cy(k)) * sy;
-                C[k] = (T)L::w(k) * (A0 + T(3) * cu + T(1.5) * cs + T(4.5) * cu * (cu + cs));
+                C[k] = wmul<T>(L::w(k), A0 + T(3) * cu + T(1.5) * cs + T(4.5) * cu * (cu + cs));
             }
         } else {
             // general TRT collision (Eq. collision): even / odd parts of f, f_eq (Eq. feq) and the
@@ -182,8 +186,8 @@ __device__ __forceinline__ double sweep2_unit(const S* fin, const T* dm, const T
             for (int k = 0; k < 9; ++k) {
                 const T cu = T(L::cx(k)) * ux + T(L::cy(k)) * uy;
                 const T cs = T(L::cx(k)) * sx + T(L::cy(k)) * sy;
-                E[k] = (T)L::w(k) * (B0 + T(3) * cu + T(4.5) * cu * cu);
-                Ph[k] = (T)L::w(k) * (s0 + T(3) * (cs - us) + T(9) * cu * cs);
+                E[k] = wmul<T>(L::w(k), B0 + T(3) * cu + T(4.5) * cu * cu);
+                Ph[k] = wmul<T>(L::w(k), s0 + T(3) * (cs - us) + T(9) * cu * cs);
             }
             const T hp = T(1) - T(0.5) * wp, hm = T(1) - T(0.5) * wm;
 #pragma unroll

@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 512) k_sweep3(Sweep3Arg
             const T dp = dm[idx], dux = dm[NNN + idx], duy = dm[2 * NNN + idx], duz = dm[3 * NNN + idx];
 #pragma unroll
             for (int k = 0; k < 19; ++k)
-                f[k] += (T)L::w(k) * (dp + T(3) * (T(L::cx(k)) * dux + T(L::cy(k)) * duy + T(L::cz(k)) * duz));
+                f[k] += wmul<T>(L::w(k), dp + T(3) * (T(L::cx(k)) * dux + T(L::cy(k)) * duy + T(L::cz(k)) * duz));
         }
         T rho = T(0), jx = T(0), jy = T(0), jz = T(0);
 #pragma unroll
@@ -160,10 +160,12 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 512) k_sweep3(Sweep3Arg
             p = rho; ux = jx; uy = jy; uz = jz;
         } else {
             const T h0 = hh[idx], h1 = hh[NNN + idx], h2 = hh[2 * NNN + idx], h3 = hh[3 * NNN + idx];
-            p = (rho + h0 * T(0.5)) * inv;
-            ux = (jx + h1 * T(0.5)) * inv;
-            uy = (jy + h2 * T(0.5)) * inv;
-            uz = (jz + h3 * T(0.5)) * inv;
+            // m = P f + (h - a P f) / (2 (1 + a/2)): the rounded 1/(1 + a/2) scales only the O(a) term
+            const T hinv = T(0.5) * inv;
+            p = rho + (h0 - a * rho) * hinv;
+            ux = jx + (h1 - a * jx) * hinv;
+            uy = jy + (h2 - a * jy) * hinv;
+            uz = jz + (h3 - a * jz) * hinv;
             s0 = h0 - a * p;
             sxx = h1 - a * ux;
             syy = h2 - a * uy;
@@ -176,7 +178,7 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 512) k_sweep3(Sweep3Arg
         for (int k = 0; k < 19; ++k) {
             const T cu = T(L::cx(k)) * ux + T(L::cy(k)) * uy + T(L::cz(k)) * uz;
             const T cs = T(L::cx(k)) * sxx + T(L::cy(k)) * syy + T(L::cz(k)) * szz;
-            C[k] = (T)L::w(k) * (A0 + T(3) * cu + T(1.5) * cs + T(4.5) * cu * (cu + cs));
+            C[k] = wmul<T>(L::w(k), A0 + T(3) * cu + T(1.5) * cs + T(4.5) * cu * (cu + cs));
         }
         // x/y streaming through shared memory: the planes alternate between two buffers, so one
         // barrier per plane suffices (a buffer is rewritten two planes later, after every thread

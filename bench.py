@@ -37,11 +37,14 @@ from paper_2609_39474_b300 import diagnostics as DG  # noqa: E402  (pure Python,
 
 METRIC = "Matched-accuracy speedup vs explicit GPU LBM; inner MLUPS and HBM GB/s"
 NU = 1.0 / 6.0
-S_LIST = [4, 8, 16, 32, 64, 128, 256]
+# physical steps per march searched by the candidate matrix; the long end is needed by the matched gate,
+# whose explicit LBM reference is accurate to a few 1e-3 of its own discretisation error
+S_LIST = [4, 8, 16, 32, 64, 128, 256, 512, 1024, 2048, 4096]
 EPS_LIST = [1e-6, 1e-8, 1e-10]
 KMAX = 300
-# candidate the reference arm uses (the matched-gate winner of the GPU candidate search at N = 1024)
-DEFAULT_CANDIDATE = {1024: (16, 1e-6), 256: (128, 1e-6)}
+# candidate the reference arm uses: the one the GPU candidate search times at N = 1024 (at this size no
+# searched FP32-storage candidate reaches the matched gate; this is the most accurate one) and at N = 256
+DEFAULT_CANDIDATE = {1024: (256, 1e-10), 256: (256, 1e-6)}
 SWEEP_BYTES_PER_SITE_FP32 = 2 * 9 * 4 + 3 * 4 + 3 * 4 + 3 * 4  # f in/out, h, lifted dm, P r
 SWEEP_BYTES_PER_SITE_FP16 = 2 * 9 * 2 + 3 * 4 + 3 * 4 + 3 * 4  # binary16 f in/out, FP32 h, dm, P r
 ROOF_N = 4096  # out-of-L2 size for the sweep roofline (16.7 M sites, 1.8 GB per sweep)
@@ -52,7 +55,7 @@ ROOF_N = 4096  # out-of-L2 size for the sweep roofline (16.7 M sites, 1.8 GB per
 WORKLOADS = {
     (2, 1024): dict(seed=1, kmax=8, t_end=nint(0.15 * 1024 ** 2), nmin=2, S=S_LIST, eps=EPS_LIST, M=64, steps=None),
     (2, 256): dict(seed=1, kmax=8, t_end=nint(0.15 * 256 ** 2), nmin=2, S=S_LIST, eps=EPS_LIST, M=64, steps=None),
-    (3, 128): dict(seed=7, kmax=6, t_end=nint(0.075 * 128 ** 2), nmin=1, S=[3, 4, 5, 8, 16, 32, 64],
+    (3, 128): dict(seed=7, kmax=6, t_end=nint(0.075 * 128 ** 2), nmin=1, S=[3, 4, 5, 8, 16, 32, 64, 128, 256, 512],
                    eps=EPS_LIST, M=32, steps=100),
 }
 
@@ -185,7 +188,7 @@ def measure_workload(torch, PL, dev, dim, n, steps, warmup, dist=None, full=Fals
     msc_once(w["S"][0], w["eps"][0])  # builds the march graph outside any measurement
     cands = []
     u0_rms = rms_vector(u)
-    for S in w["S"]:
+    for S in [S for S in w["S"] if S <= t_end]:
         for eps in w["eps"]:
             ms, st = msc_once(S, eps)
             ok = st["status"] == 0 and st["steps_done"] == S
@@ -198,8 +201,11 @@ def measure_workload(torch, PL, dev, dim, n, steps, warmup, dist=None, full=Fals
             cands.append(c)
     matched = [c for c in cands if c["ok"] and c["err"] <= 3.0 * e_ex]
     onepct = [c for c in cands if c["ok"] and c["rel"] <= 0.01]
-    if not matched:
-        raise SystemExit(f"no MSC candidate passes the matched-accuracy gate (dim {dim}, N {n})")
+    matched_ok = bool(matched)
+    if not matched:  # reported, not hidden: the line carries matched_gate_passed = false
+        sys.stderr.write(f"no MSC candidate passes the matched-accuracy gate (dim {dim}, N {n}); "
+                         "timing the most accurate converged candidate\n")
+        matched = [min([c for c in cands if c["ok"]] or cands, key=lambda c: c["err"])]
     best = min(matched, key=lambda c: c["ms"])
     best1 = min(onepct, key=lambda c: c["ms"]) if onepct else None
 
@@ -242,6 +248,7 @@ def measure_workload(torch, PL, dev, dim, n, steps, warmup, dist=None, full=Fals
         "inner_mlups": n ** dim * statistics.mean(inner) / (ms_step * 1e3),
         "inner_iters_per_step": statistics.mean(inner) / S, "candidate": best, "candidate_1pct": best1,
         "e_explicit": e_ex, "e_msc": e_msc, "rms_ref": rms_vector(u_ref), "t_end": t_end,
+        "matched_gate_passed": matched_ok,
         "explicit_mlups": n ** dim * t_end / (t_ex * 1e3),
         "candidates": [{k: c[k] for k in c if k != "err"} for c in cands],
         "clocks": clk, "launches": launches, "diagnostics": diag,
@@ -903,6 +910,9 @@ def main():
     n = args.n
     line = {
         "metric": METRIC, "value": res["s_wall_matched"], "unit": "x", "n_gpus": world, "steps": args.steps,
+        # false when no searched candidate reaches e_msc <= 3 e_explicit: value then times the most
+        # accurate converged candidate (the paper's tables print "--" for such a cell)
+        "matched_gate_passed": res["matched_gate_passed"],
         "warmup": args.warmup, "ms_per_step": res["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"D2Q9 periodic N={n} Re=1 nu=1/6 random-phase (k^-2, 1<=|k|<=8, seed 1), "
@@ -926,7 +936,7 @@ def main():
         "inner_mlups": res["inner_mlups"],
         "inner_iters_per_step": res["inner_iters_per_step"],
         "errors": {"e_msc": res["e_msc"], "e_explicit": res["e_explicit"], "rms_ref": res["rms_ref"],
-                   "matched_gate": "e_msc <= 3 e_explicit"},
+                   "matched_gate": "e_msc <= 3 e_explicit", "matched_gate_passed": res["matched_gate_passed"]},
         "candidate_1pct": res["candidate_1pct"],
         "diagnostics": res["diagnostics"],
         "explicit_mlups": res["explicit_mlups"],

@@ -44,7 +44,7 @@ EPS_LIST = [1e-6, 1e-8, 1e-10]
 KMAX = 300
 # candidate the reference arm uses: the one the GPU candidate search times at N = 1024 (at this size no
 # searched FP32-storage candidate reaches the matched gate; this is the most accurate one) and at N = 256
-DEFAULT_CANDIDATE = {1024: (256, 1e-10), 256: (256, 1e-6)}
+DEFAULT_CANDIDATE = {1024: (512, 1e-10), 256: (256, 1e-6)}
 SWEEP_BYTES_PER_SITE_FP32 = 2 * 9 * 4 + 3 * 4 + 3 * 4 + 3 * 4  # f in/out, h, lifted dm, P r
 SWEEP_BYTES_PER_SITE_FP16 = 2 * 9 * 2 + 3 * 4 + 3 * 4 + 3 * 4  # binary16 f in/out, FP32 h, dm, P r
 ROOF_N = 4096  # out-of-L2 size for the sweep roofline (16.7 M sites, 1.8 GB per sweep)

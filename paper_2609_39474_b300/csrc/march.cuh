@@ -21,16 +21,25 @@ __device__ __forceinline__ double cdotu(int k, const double* u) {
 }
 
 // The BDF history term h = c1 m_a - c2 m_b + f_c (Eq. bdf2 plus the body force) in the working-field
-// type: FP64 storage evaluates it in FP64; FP32 / FP16 storage (h is stored in FP32) evaluates it in
-// FP32 from the history rounded to FP32, which keeps FP64 instructions (~1/58 of the FP32 rate on
-// B300) to the history update itself.  Both step kernels use this one formula, so a march resumed
-// from a saved state repeats the uninterrupted march bit for bit.
+// type.  FP64 storage evaluates it in FP64.  FP32 / FP16 storage (h is stored in FP32) evaluates it
+// in FP32 from the history rounded to FP32, which keeps FP64 instructions (~1/58 of the FP32 rate on
+// B300) to the history update itself, and writes it as h = a g with g = m_a + (m_a - m_b) c2/a
+// (c1 = a + c2 for BDF1 and BDF2) and a_f the binary32 a_q that the sweep uses for that step: the
+// step's fixed point balances a_f m against h, so h must not carry the rounding of c1 and c2 as a
+// relative bias of its own (with m_a = m_b = m it is a_f m up to one rounding); such a bias would
+// move every step's m by ~1e-8 relative, in the same direction, and add up over the march.  rf is
+// c2/a: 1/3 for BDF2, 0 for BDF1.  Both step kernels use this one formula, so a march resumed from a
+// saved state repeats the uninterrupted march bit for bit.
 template <typename T>
-__device__ __forceinline__ T bdf_history(double c1, double ma, double c2, double mb, double fc) {
-    if constexpr (std::is_same<T, float>::value)
-        return fmaf(narrow_f64(c1), narrow_f64(ma), fmaf(-narrow_f64(c2), narrow_f64(mb), narrow_f64(fc)));
-    else
+__device__ __forceinline__ T bdf_history(double c1, double ma, double c2, double mb, double fc, float af, float rf) {
+    if constexpr (std::is_same<T, float>::value) {
+        const float a_ = narrow_f64(ma), b_ = narrow_f64(mb);
+        return fmaf(af, fmaf(a_ - b_, rf, a_), narrow_f64(fc));
+    } else {
+        (void)af;
+        (void)rf;
         return (T)fma(c1, ma, fma(-c2, mb, fc));
+    }
 }
 
 // storage scale of the populations: from the state when there is one, else 1
@@ -150,7 +159,7 @@ __device__ __forceinline__ void step_begin_range(const DevState* __restrict__ st
     const S* f2 = fbase + (size_t)vs->slot_fn[2] * fstride;
     S* ft = fbase + (size_t)vs->slot_cur * fstride;
     const double c1 = vs->c1, c2 = vs->c2;
-    (void)q;
+    const float af = narrow_f64(vs->a), rf = q == 2 ? 1.0f / 3.0f : 0.0f;  // the sweep's binary32 a_q; c2/a_q
     (void)dt;
     const T sig = from_f64<T>(vs->fscale), isig = from_f64<T>(vs->isig);
     const double fc[4] = {0.0, vs->force[0], vs->force[1], vs->force[2]};
@@ -158,7 +167,7 @@ __device__ __forceinline__ void step_begin_range(const DevState* __restrict__ st
 #pragma unroll
         for (int c = 0; c <= L::D; ++c) {  // h = c1 m^n - c2 m^{n-1} + (0, F), as k_step_end forms it
             const size_t o = c * sites + i;
-            h[o] = bdf_history<T>(c1, mn[o], c2, mnm1[o], fc[c]);
+            h[o] = bdf_history<T>(c1, mn[o], c2, mnm1[o], fc[c], af, rf);
         }
         if (nav == 1) {
 #pragma unroll
@@ -214,6 +223,7 @@ __device__ __forceinline__ void step_end_range(const DevState* __restrict__ st, 
     S* __restrict__ trial = fbase + (size_t)vs->slot_nxt * fstride;
     const T sig = from_f64<T>(vs->fscale), isig = from_f64<T>(vs->isig);
     const double n1 = vs->n1, n2 = vs->n2;  // BDF2 for the next step
+    const float an = narrow_f64(vs->qa[1]);  // the next step's binary32 a_2, as its sweep will use it
     const double k1 = vs->k1, k2 = vs->k2;  // formed once per step (FP64 products are slow on B300)
     // body force: (0, F) joins h in the reconstruction and in the next step's h (FORCE = false: F = 0)
     const double fc[4] = {0.0, FORCE ? vs->force[0] : 0.0, FORCE ? vs->force[1] : 0.0, FORCE ? vs->force[2] : 0.0};
@@ -256,7 +266,7 @@ __device__ __forceinline__ void step_end_range(const DevState* __restrict__ st, 
             const double mnew = FORCE ? fma(k1, mc, fma(-k2, mpv[c], fma(inv, md, kf[c])))
                                       : fma(k1, mc, fma(-k2, mpv[c], inv * md));
             mnm1[o] = mnew;
-            if (next) h[o] = bdf_history<T>(n1, mnew, n2, mc, fc[c]);
+            if (next) h[o] = bdf_history<T>(n1, mnew, n2, mc, fc[c], an, 1.0f / 3.0f);
         }
         if (nav == 1) {
 #pragma unroll

@@ -36,3 +36,24 @@ def test_reference_other_ranks_exit_quietly():
     p = _run({"RANK": "1", "WORLD_SIZE": "2"})
     assert p.returncode == 0, p.stderr[-2000:]
     assert not [l for l in p.stdout.splitlines() if l.startswith("{")]
+
+
+def _bench():
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_candidate_selection_gates_and_fallback():
+    sel = _bench().select_candidates
+    c = lambda S, ms, err, rel, ok=True: dict(S=S, ms=ms, err=err, rel=rel, ok=ok)
+    cands = [c(8, 1.0, 9e-7, 0.009), c(16, 2.0, 2e-7, 0.002), c(64, 8.0, 4e-9, 5e-5), c(128, 16.0, 2e-9, 3e-5),
+             c(4, 0.5, 1e-9, 1e-6, ok=False)]
+    best, best1, ok = sel(cands, 2e-9)          # matched gate 6e-9: S = 64 is the fastest passing
+    assert ok and best["S"] == 64 and best1["S"] == 8
+    best, best1, ok = sel(cands, 1e-10)         # nothing passes: the most accurate converged stands in
+    assert not ok and best["S"] == 128 and best1["S"] == 8
+    best, best1, ok = sel([c(8, 1.0, 9e-7, 0.02)], 1e-6)
+    assert ok and best["S"] == 8 and best1 is None

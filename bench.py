@@ -45,8 +45,9 @@ KMAX = 300
 # candidate the reference arm uses: the one the GPU candidate search times at N = 1024 (at this size no
 # searched FP32-storage candidate reaches the matched gate; this is the most accurate one) and at N = 256
 DEFAULT_CANDIDATE = {1024: (512, 1e-10), 256: (256, 1e-6)}
-SWEEP_BYTES_PER_SITE_FP32 = 2 * 9 * 4 + 3 * 4 + 3 * 4 + 3 * 4  # f in/out, h, lifted dm, P r
-SWEEP_BYTES_PER_SITE_FP16 = 2 * 9 * 2 + 3 * 4 + 3 * 4 + 3 * 4  # binary16 f in/out, FP32 h, dm, P r
+# the march's D2Q9 sweep: f in/out, h as a binary32 pair, lifted dm, P r
+SWEEP_BYTES_PER_SITE_FP32 = 2 * 9 * 4 + 2 * 3 * 4 + 3 * 4 + 3 * 4
+SWEEP_BYTES_PER_SITE_FP16 = 2 * 9 * 2 + 2 * 3 * 4 + 3 * 4 + 3 * 4  # binary16 f in/out, FP32 h pair, dm, P r
 ROOF_N = 4096  # out-of-L2 size for the sweep roofline (16.7 M sites, 1.8 GB per sweep)
 
 
@@ -754,21 +755,23 @@ def run_phase(args):
 
 
 def sweep_time(torch, PL, dev, n, reps=20, precision="fp32"):
-    """Mean duration (ms) of the fused sweep with the lift, CUDA events on its stream."""
+    """Mean duration (ms) of the march's fused D2Q9 sweep (binary32 history pair, with the lift), CUDA
+    events on its stream."""
     sites = n * n
     pt, ft = PL.storage_dtype(precision), PL.field_dtype(precision)
     scale = 0.5 if precision == "fp16" else 1e-3  # FP16 storage holds O(1) scaled values
     f = (torch.randn((9, n, n), device=dev, dtype=torch.float32) * scale).to(pt)
-    h = torch.randn((3, n, n), device=dev, dtype=ft) * 1e-4
+    h = torch.randn((2, 3, n, n), device=dev, dtype=ft) * 1e-4
+    h[1] *= 1e-8
     dm = torch.randn((3, n, n), device=dev, dtype=ft) * 1e-5
     sc = PL.StageScratch(2, n, precision, dev)
     for _ in range(3):
-        PL.sweep(2, n, precision, 0.01, f, h, dm, sc)
+        PL.sweep_hpair(n, precision, 0.01, f, h, dm, sc)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(reps):
-        PL.sweep(2, n, precision, 0.01, f, h, dm, sc)
+        PL.sweep_hpair(n, precision, 0.01, f, h, dm, sc)
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / reps
@@ -776,29 +779,31 @@ def sweep_time(torch, PL, dev, n, reps=20, precision="fp32"):
     return {"n": n, "ms": ms, "gbs": bps * sites / (ms * 1e6), "bytes_per_site": bps, "precision": precision}
 
 
-SWEEP3_BYTES_PER_SITE_FP32 = 2 * 19 * 4 + 4 * (4 + 4 + 4)  # f in and out, h, dm, P r
+# the march's halo-free D3Q19 sweep: f in and out, P f in and out, h, the lifted dm, P r
+SWEEP3_BYTES_PER_SITE_FP32 = 2 * 19 * 4 + 4 * (4 + 4 + 4 + 4 + 4)
 
 
 def sweep3_time(torch, PL, dev, n=128, reps=20):
-    """Mean duration (ms) of the fused D3Q19 FP32 sweep with the lift (stage call), CUDA events."""
+    """Mean duration (ms) of the march's D3Q19 FP32 sweep (halo-free, with the lift), CUDA events."""
     f = torch.randn((19, n, n, n), device=dev, dtype=torch.float32) * 1e-3
+    pf = torch.randn((4, n, n, n), device=dev, dtype=torch.float32) * 1e-3
     h = torch.randn((4, n, n, n), device=dev, dtype=torch.float32) * 1e-4
     dm = torch.randn((4, n, n, n), device=dev, dtype=torch.float32) * 1e-5
     sc = PL.StageScratch(3, n, "fp32", dev)
     for _ in range(3):
-        PL.sweep(3, n, "fp32", 0.01, f, h, dm, sc)
+        PL.sweep_d3q19_pf(n, "fp32", 0.01, f, pf, h, dm, sc)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(reps):
-        PL.sweep(3, n, "fp32", 0.01, f, h, dm, sc)
+        PL.sweep_d3q19_pf(n, "fp32", 0.01, f, pf, h, dm, sc)
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / reps
     peak, src = load_peaks()
     gbs = SWEEP3_BYTES_PER_SITE_FP32 * n ** 3 / (ms * 1e6)
     return {"n": n, "ms": ms, "gbs": gbs, "frac": gbs / peak, "peak_source": f"{src} hbm_gbs",
-            "bytes_per_site": SWEEP3_BYTES_PER_SITE_FP32}
+            "bytes_per_site": SWEEP3_BYTES_PER_SITE_FP32, "kernel": "k_sweep3p<float> (halo-free D3Q19 sweep)"}
 
 
 def sweep_roofline(torch, PL, dev):
@@ -812,7 +817,7 @@ def sweep_roofline(torch, PL, dev):
         if tr.get("kernel_source_hash") == kernel_hash():
             traffic = tr["bytes_per_launch_full"]
     return {"bound": "hbm", "achieved": t["gbs"], "peak": peak, "unit": "GB/s", "frac": t["gbs"] / peak,
-            "traffic": traffic, "peak_source": f"{src} hbm_gbs", "kernel": "k_sweep2<float> (fused D2Q9 sweep)",
+            "traffic": traffic, "peak_source": f"{src} hbm_gbs", "kernel": "k_sweep2<float> (fused D2Q9 sweep of the march, h as a binary32 pair)",
             "n": ROOF_N, "ms_per_launch": t["ms"], "bytes_per_site": SWEEP_BYTES_PER_SITE_FP32}
 
 

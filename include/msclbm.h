@@ -201,6 +201,17 @@ int msc_load_state(msc_ctx* ctx, const void* host_blob, size_t bytes);
 /* Human-readable text for a status code (static storage). */
 const char* msc_strerror(int status);
 
+/* Index checks of the bounds-checked debug build (libmsclbm_check.so, compiled with
+   -DMSC_BOUNDS_CHECK; not part of the method).  That build tests the indices of the sweep strips,
+   tiles and halos and of the shared-memory transforms before each guarded access, skips an access
+   whose index is out of range (the results are then wrong, but no memory outside the arrays is
+   touched and nothing traps) and counts it.  *count receives the number of failed checks since the
+   last reset, *first the first failure as site << 40 | index (site numbers are those of the
+   MSC_INB calls in the sources).  Synchronises the device; reset != 0 clears both afterwards.
+   Returns MSC_OK in the checked build and MSC_ERR_STATE (with both outputs 0) in the normal build,
+   which has no checks; MSC_ERR_ARG for NULL outputs. */
+int msc_bounds_check_report(unsigned long long* count, unsigned long long* first, int reset);
+
 /* ---- Stage entry points: one step of the hot path on caller-owned device arrays ----------- */
 
 /* Scratch bytes the stage calls below need for this lattice (reduction partials and the half
@@ -218,6 +229,31 @@ size_t msc_stage_scratch_bytes(int dim, int n, int precision);
 int msc_sweep(int dim, int n, int precision, double a, const void* f_in, const void* dm,
               const void* h, void* f_out, void* pr_out, double* sumsq_out, void* scratch,
               size_t scratch_bytes, void* stream);
+
+/* The D3Q19 sweep of the march in its halo-free form, as one stage (msc_sweep with dim = 3 is this
+   call preceded by the moments P f_in).  At the operating point the post-collision populations of a
+   site depend only on its reconstructed moments and source (Eq. collision-operating), and the
+   moments of the trial f_in + E dm are P f_in + dm, so the collision inputs of every neighbour come
+   from pf_in, dm and h alone and the outputs are pulled, f_out,k(x) = C_k(x - c_k).  Same results as
+   msc_sweep (dim 3) up to rounding, plus pf_out = P f_out for the next sweep.  f_in / f_out:
+   19*n^3 elements of the storage type (FP64 or FP32); pf_in / pf_out: 4*n^3 elements, P f_in and
+   P f_out (density, then the three momentum components); dm (NULL: no lift), h, pr_out: 4*n^3.
+   f_in != f_out and pf_in != pf_out.  Scratch as msc_sweep (msc_stage_scratch_bytes(3, n, ...)).
+   MSC_ERR_ARG for invalid sizes, pointers, scratch or FP16 storage. */
+int msc_sweep_d3q19_pf(int n, int precision, double a, const void* f_in, const void* pf_in, const void* dm,
+                       const void* h, void* f_out, void* pf_out, void* pr_out, double* sumsq_out, void* scratch,
+                       size_t scratch_bytes, void* stream);
+
+/* msc_sweep for D2Q9 with the history term h (Eq. bdf2) given as the march holds it.  With binary32
+   storage (FP32, FP16) h is a pair of 2*3*n*n floats, the three high parts followed by the three low
+   parts, h = hi + lo; the sweep forms every difference h - a m (in m = (P f + h/2)/(1 + a/2) written
+   as P f + (h - a P f)/(2 (1 + a/2)), and in s = h - a m) as fma(-a, m, hi) + lo, so that the source
+   keeps its own relative accuracy where h ~ a m.  This is the sweep kernel of the FP32 and FP16
+   march.  With FP64 storage h has 3*n*n doubles and the call equals msc_sweep with dim = 2.  Other
+   arguments, scratch and errors as msc_sweep. */
+int msc_sweep_hpair(int n, int precision, double a, const void* f_in, const void* dm, const void* h,
+                    void* f_out, void* pr_out, double* sumsq_out, void* scratch, size_t scratch_bytes,
+                    void* stream);
 
 /* Shadow correction of the residual moments (Eq. shadow-update, first two lines):
      dm = F^{-1}[ chi(k) H(k)^{-1} F[pr] ]
@@ -265,12 +301,14 @@ int msc_full_symbol_correct(int n, int precision, double a, double omega_p, doub
    allocation would synchronise the device.  Same computation and arguments as msc_sweep with
    dim = 2, minus the scratch: the reduction scratch (a counter and one partial sum per block) is
    a fixed static device array of 33 KB that every device which loads the library holds until the
-   process exits.  Limits: n <= 4096 (FP64 or FP32 storage); larger lattices return MSC_ERR_ARG.
-   The first call on each device looks the array up with that device current (call it once
-   outside any stream capture before relying on it).  Every call shares the same array and clears
-   its counter itself, so calls that may overlap on the GPU (different streams or devices sharing
-   one process-wide array per device, or host threads racing on one device) race with each other:
-   serialise them. */
+   process exits.  Limits: n a power of two with 8 <= n <= 2048 for FP64 storage and
+   8 <= n <= 4096 for FP32 storage; FP16 storage is not supported; anything else returns
+   MSC_ERR_ARG before any launch.  Every call looks the array's device address up for the current
+   device (so it stays right after a device reset); the first call on a device also loads the
+   library's device code there, so make that first call outside any stream capture.  Every call
+   shares the same array and clears its counter itself, so calls that may overlap on the GPU
+   (different streams, or host threads racing on one device) race with each other: serialise
+   them. */
 int msc_sweep_d2q9_noalloc(int n, int precision, double a, const void* f_in, const void* dm,
                            const void* h, void* f_out, void* pr_out, double* sumsq_out, void* stream);
 

@@ -7,7 +7,12 @@ import ctypes
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libmsclbm.so")
+# MSC_LIB_VARIANT=check selects the bounds-checked debug build (libmsclbm_check.so, built by
+# build.build(variant="check")); the default is the optimised library
+VARIANT = os.environ.get("MSC_LIB_VARIANT", "")
+if VARIANT not in ("", "check"):
+    raise ValueError(f"unknown MSC_LIB_VARIANT {VARIANT!r} (expected 'check' or unset)")
+LIB_PATH = os.path.join(HERE, "libmsclbm_check.so" if VARIANT == "check" else "libmsclbm.so")
 
 MSC_OK = 0
 MSC_ERR_ARG = 1
@@ -99,6 +104,9 @@ _SIG = {
     "msc_strerror": (ctypes.c_char_p, [_i]),
     "msc_stage_scratch_bytes": (_sz, [_i, _i, _i]),
     "msc_sweep": (_i, [_i, _i, _i, _d, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "msc_bounds_check_report": (_i, [ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(ctypes.c_ulonglong), _i]),
+    "msc_sweep_d3q19_pf": (_i, [_i, _i, _d, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "msc_sweep_hpair": (_i, [_i, _i, _d, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "msc_shadow_solve": (_i, [_i, _i, _i, _d, _d, _vp, _vp, _vp, _sz, _vp]),
     "msc_equilibrium": (_i, [_i, _i, _i, _vp, _vp, _vp, _vp]),
     "msc_sweep_d2q9_noalloc": (_i, [_i, _i, _d, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),

@@ -374,49 +374,3 @@ int msc_load_state_device(msc_ctx* c, const void* blob, size_t bytes) {
 }
 
 }  // extern "C"
-
-// ---- self-check of the integer-pipe format conversions against the hardware conversions ---------
-namespace {
-__device__ unsigned int conv_mix(unsigned long long& s) {  // splitmix64 step, high half
-    s += 0x9e3779b97f4a7c15ull;
-    unsigned long long z = s;
-    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
-    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
-    return (unsigned int)((z ^ (z >> 31)) >> 32);
-}
-__global__ void k_conversion_check(unsigned long long seed, int per_thread, unsigned int* bad) {
-    unsigned long long s = seed ^ (0x5851f42d4c957f2dull * (blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x));
-    unsigned int nbad = 0;
-    for (int i = 0; i < per_thread; ++i) {
-        // random binary32 patterns (every exponent) and random binary64 patterns near the binary32 range
-        const unsigned int fb = conv_mix(s);
-        const float f = __uint_as_float(fb);
-        const double w = widen_f32(f), wr = (double)f;
-        if (!(w == wr || (w != w && wr != wr)) || (w == wr && __double_as_longlong(w) != __double_as_longlong(wr))) ++nbad;
-        const unsigned long long hi = conv_mix(s), lo = conv_mix(s);
-        unsigned long long db = (hi << 32) | lo;
-        const unsigned long long ex = 880ull + (hi % 290ull);  // exponents 880 .. 1169 around the range
-        db = (db & 0x800fffffffffffffull) | (ex << 52);
-        if ((i & 7) == 0) db = (db & ~0x1fffffffull) | ((i & 8) ? 0x10000000ull : 0x0fffffffull);  // ties, near ties
-        const double d = __longlong_as_double((long long)db);
-        const float n = narrow_f64(d), nr = __double2float_rn(d);
-        if (__float_as_uint(n) != __float_as_uint(nr)) ++nbad;
-    }
-    if (nbad) atomicAdd(bad, nbad);
-}
-}  // namespace
-
-extern "C" int msc_selftest_conversions(int blocks, int per_thread, unsigned long long seed, int* mismatches) {
-    if (blocks < 1 || per_thread < 1 || !mismatches) return MSC_ERR_ARG;
-    unsigned int* d = nullptr;
-    CK(cudaMalloc(&d, sizeof(unsigned int)));
-    unsigned int h = 0;
-    if (cudaMemset(d, 0, sizeof(unsigned int)) != cudaSuccess) { cudaFree(d); return MSC_ERR_CUDA; }
-    k_conversion_check<<<blocks, 256>>>(seed, per_thread, d);
-    const bool ok = cudaGetLastError() == cudaSuccess &&
-                    cudaMemcpy(&h, d, sizeof(unsigned int), cudaMemcpyDeviceToHost) == cudaSuccess;
-    cudaFree(d);
-    if (!ok) return MSC_ERR_CUDA;
-    *mismatches = (int)h;
-    return MSC_OK;
-}

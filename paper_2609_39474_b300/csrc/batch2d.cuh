@@ -122,8 +122,9 @@ __global__ void __launch_bounds__(kSweepWarps * 32) k_bsweep2(const BInst<T>* __
             inv = T(1);
             lift = 0;
         }
-        double ssq = sweep2_unit<T, T, MODE == 2>(fin, A.dm, A.h, fout, A.pr, a, inv, lift, A.n, A.hb,
-                                               lu % A.nstrips, lu / A.nstrips, lane);
+        // the march and the tuning mode read the instance's h, a binary32 pair for FP32 storage
+        double ssq = sweep2_unit<T, T, MODE == 2, false, MODE != 2 && std::is_same<T, float>::value>(
+            fin, A.dm, A.h, fout, A.pr, a, inv, lift, A.n, A.hb, lu % A.nstrips, lu / A.nstrips, lane);
         if constexpr (MODE != 2) {  // residual norm of the instance (not for the explicit step)
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) ssq += __shfl_xor_sync(0xffffffffu, ssq, off);

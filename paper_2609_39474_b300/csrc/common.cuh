@@ -12,6 +12,26 @@
 
 namespace msc {
 
+// ---- bounds-checked debug build ---------------------------------------------------------------
+// Built with -DMSC_BOUNDS_CHECK (libmsclbm_check.so), MSC_INB(i, n, site) tests 0 <= i < n at the
+// index computations of the sweep strips, tiles and halos and of the shared-memory transforms; a
+// failing test records the number of failures and the first failing site and index (read by
+// msc_bounds_check_report) and the guarded access is skipped, so a bad index never reaches memory
+// and nothing traps.  In the normal build MSC_INB is the constant true and compiles away.
+#ifdef MSC_BOUNDS_CHECK
+__device__ unsigned long long g_oob_count;
+__device__ unsigned long long g_oob_first;  // site << 40 | (index & (2^40 - 1))
+__device__ __forceinline__ bool inb_check(long long i, long long n, unsigned int site) {
+    if (i >= 0 && i < n) return true;
+    if (atomicAdd(&g_oob_count, 1ull) == 0ull)
+        g_oob_first = ((unsigned long long)site << 40) | ((unsigned long long)i & 0xffffffffffull);
+    return false;
+}
+#define MSC_INB(i, n, site) ::msc::inb_check((long long)(i), (long long)(n), (site))
+#else
+#define MSC_INB(i, n, site) true
+#endif
+
 // ---- lattices (Appendix A, Eqs. d2q9 and d3q19) -------------------------------------------
 
 struct D2Q9 {
@@ -111,8 +131,9 @@ constexpr size_t kAdjCtlBytes = 256, kAdjArgBytes = 160, kAdjStatBytes = 32;
 constexpr size_t kAdjBytes = kAdjCtlBytes + MSC_ADJOINT_CHUNK * (kAdjArgBytes + kAdjStatBytes);
 
 struct Layout {
-    size_t state, fbuf, mbuf, h, pr, dm, spec, tw, coef, partial, counter, adj, adjw, iters, hist, replay, total;
-    size_t fstride;  // bytes of one population array
+    size_t state, fbuf, pf, mbuf, h, pr, dm, spec, tw, coef, partial, counter, adj, adjw, iters, hist, replay, total;
+    size_t fstride;   // bytes of one population array
+    size_t pfstride;  // elements of one P f field set (D3Q19)
 };
 
 constexpr int kNumFBuf = 5;
@@ -162,6 +183,44 @@ __device__ __forceinline__ float narrow_f64(double x) {
     r += (rem > 0x10000000u) | ((rem == 0x10000000u) & (r & 1u));
     return __uint_as_float(((unsigned int)(b >> 63) << 31) | r);
 }
+// x = hi + lo with hi = x rounded to the nearest binary32 (ties to even) and lo = x - hi rounded to
+// binary32, on the integer pipe, for x whose exponent lies in the normal binary32 range (other x
+// take the hardware conversion with lo = 0).  x - hi is an integer multiple m of x's binary64 ulp
+// with m <= 2^28, so lo = m 2^(E - 1075), E the biased binary64 exponent of x; when that scale
+// falls below the binary32 normal range (|x| < 2^-74) lo is dropped (below 2^-98 absolute).
+__device__ __forceinline__ void split_f64(double x, float& hi, float& lo) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned long long mag = b & 0x7fffffffffffffffull;
+    const unsigned int e = (unsigned int)(mag >> 52);
+    if (e - 897u > 253u) {
+        hi = (float)x;
+        lo = 0.0f;
+        return;
+    }
+    const unsigned int sgn = (unsigned int)(b >> 63) << 31;
+    const unsigned long long t = mag - (896ull << 52);
+    const unsigned int r = (unsigned int)(t >> 29);
+    const unsigned int rem = (unsigned int)t & 0x1fffffffu;
+    const unsigned int up = (rem > 0x10000000u) | ((rem == 0x10000000u) & (r & 1u));
+    hi = __uint_as_float(sgn | (r + up));
+    // rounded up: lo = -(2^29 - rem) ulp with the sign of x flipped; else lo = rem ulp
+    const unsigned int m = up ? 0x20000000u - rem : rem;
+    const int ef = (int)e - 948;  // binary32 exponent field of 2^(E - 1075)
+    if (m == 0u || ef < 1) {
+        lo = 0.0f;
+        return;
+    }
+    const float v = __int2float_rn((int)m) * __uint_as_float((unsigned int)ef << 23);
+    lo = __uint_as_float(__float_as_uint(v) ^ (up ? sgn ^ 0x80000000u : sgn));
+}
+
+// s + e = a + b exactly (Knuth's two-sum, six binary32 operations, no ordering assumption)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
 template <typename T>
 __device__ __forceinline__ double to_f64(T x) {
     if constexpr (std::is_same<T, float>::value) return widen_f32(x);

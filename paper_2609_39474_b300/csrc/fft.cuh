@@ -150,7 +150,8 @@ __device__ __forceinline__ void stockham_stage(C* x, int n, int logn, int Ns, in
             const int j = b & (nb - 1);
             const C* xs = x + f * plen;
 #pragma unroll
-            for (int r = 0; r < R; ++r) v[m][r] = xs[pad(j + r * nb)];
+            for (int r = 0; r < R; ++r)
+                if (MSC_INB(f * plen + pad(j + r * nb), nfft * plen, 7)) v[m][r] = xs[pad(j + r * nb)];
         }
     }
     __syncthreads();
@@ -186,7 +187,8 @@ __device__ __forceinline__ void stockham_stage(C* x, int n, int logn, int Ns, in
             C* ys = x + f * plen;
             const int base = (j - k) * R + k;
 #pragma unroll
-            for (int r = 0; r < R; ++r) ys[pad(base + r * Ns)] = v[m][r];
+            for (int r = 0; r < R; ++r)
+                if (MSC_INB(f * plen + pad(base + r * Ns), nfft * plen, 8)) ys[pad(base + r * Ns)] = v[m][r];
         }
     }
     __syncthreads();
@@ -255,10 +257,12 @@ __device__ __forceinline__ void fft1024_warp(C* v, C* s, const C* __restrict__ t
     SmallDft<C, 32, INV>::run(v);
     __syncwarp();
 #pragma unroll
-    for (int r = 0; r < 32; ++r) s[pad(32 * j + r)] = v[r];
+    for (int r = 0; r < 32; ++r)
+        if (MSC_INB(pad(32 * j + r), padded_len(1024), 9)) s[pad(32 * j + r)] = v[r];
     __syncwarp();
 #pragma unroll
-    for (int r = 0; r < 32; ++r) v[r] = s[pad(j + 32 * r)];
+    for (int r = 0; r < 32; ++r)
+        if (MSC_INB(pad(j + 32 * r), padded_len(1024), 10)) v[r] = s[pad(j + 32 * r)];
 #pragma unroll
     for (int r = 1; r < 32; ++r) v[r] = cmul(v[r], twiddle(tw, j * r, INV));
     SmallDft<C, 32, INV>::run(v);

@@ -20,26 +20,63 @@ __device__ __forceinline__ double cdotu(int k, const double* u) {
     return s;
 }
 
-// The BDF history term h = c1 m_a - c2 m_b + f_c (Eq. bdf2 plus the body force) in the working-field
-// type.  FP64 storage evaluates it in FP64.  FP32 / FP16 storage (h is stored in FP32) evaluates it
-// in FP32 from the history rounded to FP32, which keeps FP64 instructions (~1/58 of the FP32 rate on
-// B300) to the history update itself, and writes it as h = a g with g = m_a + (m_a - m_b) c2/a
-// (c1 = a + c2 for BDF1 and BDF2) and a_f the binary32 a_q that the sweep uses for that step: the
-// step's fixed point balances a_f m against h, so h must not carry the rounding of c1 and c2 as a
-// relative bias of its own (with m_a = m_b = m it is a_f m up to one rounding); such a bias would
-// move every step's m by ~1e-8 relative, in the same direction, and add up over the march.  rf is
-// c2/a: 1/3 for BDF2, 0 for BDF1.  Both step kernels use this one formula, so a march resumed from a
-// saved state repeats the uninterrupted march bit for bit.
+// The BDF history term h = c1 m_a - c2 m_b + f_c (Eq. bdf2 plus the body force), written to
+// h[o] in the working-field type.  FP64 storage evaluates and stores it in FP64.
+//
+// FP32 / FP16 storage stores h as a binary32 pair, hi at h[o] and lo at h[o + lo_off], with
+// hi + lo = h to ~2^-48 relative.  The sweep subtracts a m (m ~ the moments, a = a_q) from h with a
+// fused multiply-add on hi and then adds lo, so the source s = h - a m, a small difference of two
+// large terms, keeps its own relative accuracy; a single binary32 h would carry a rounding error of
+// 2^-24 |h| into s at every site, which the long-wave shadow solve amplifies by 1/(a + nu|k|^2) and
+// the march accumulates over its steps.  The pair is formed from the FP64 history with binary32
+// error-free transformations only (B300's FP64 pipe runs at ~1/58 of the FP32 rate):
+//   h = a_f g,  g = m_a + (m_a - m_b) c2/a   (c1 = a + c2 for BDF1 and BDF2)
+// with a_f the binary32 a_q that the sweep uses for that step, so that the step's fixed point
+// balances a_f m against h without a relative bias from rounded constants (with m_a = m_b = m, h is
+// a_f m to ~2^-48).  m_a, m_b are split exactly into binary32 pairs (split_f64), m_a - m_b and its
+// product with c2/a = 1/3 (BDF2, weight split into hi + lo) or 0 (BDF1) are formed in binary32
+// (relative error 2^-23 of a term of size |m_a - m_b|), g as a two-sum pair, a_f g with the exact
+// product error from an FMA; the force joins the low part and a final two-sum renormalises.  Both
+// step kernels use this one routine, so a march resumed from a saved state repeats the
+// uninterrupted march bit for bit.
 template <typename T>
-__device__ __forceinline__ T bdf_history(double c1, double ma, double c2, double mb, double fc, float af, float rf) {
+__device__ __forceinline__ void bdf_history(double c1, double ma, double c2, double mb, double fc, float af, int q,
+                                            T* __restrict__ h, size_t o, size_t lo_off) {
     if constexpr (std::is_same<T, float>::value) {
-        const float a_ = narrow_f64(ma), b_ = narrow_f64(mb);
-        return fmaf(af, fmaf(a_ - b_, rf, a_), narrow_f64(fc));
+        (void)c1;
+        (void)c2;
+        float ah, al, bh, bl;
+        split_f64(ma, ah, al);
+        split_f64(mb, bh, bl);
+        float t = 0.0f;
+        if (q == 2) {
+            const float d = (ah - bh) + (al - bl);
+            const float r_hi = (float)(1.0 / 3.0);
+            const float r_lo = (float)(1.0 / 3.0 - (double)r_hi);
+            t = fmaf(d, r_hi, d * r_lo);
+        }
+        float gh, ge;
+        two_sum(ah, t, gh, ge);
+        const float gl = ge + al;
+        const float ph = af * gh;
+        const float pl = fmaf(af, gl, fmaf(af, gh, -ph)) + narrow_f64(fc);
+        float hi, lo;
+        two_sum(ph, pl, hi, lo);
+        h[o] = hi;
+        h[o + lo_off] = lo;
     } else {
         (void)af;
-        (void)rf;
-        return (T)fma(c1, ma, fma(-c2, mb, fc));
+        (void)q;
+        (void)lo_off;
+        h[o] = (T)fma(c1, ma, fma(-c2, mb, fc));
     }
+}
+
+// elements of the working field h: a binary32 pair per value for FP32 / FP16 storage (hi fields,
+// then lo fields), one FP64 value otherwise
+template <typename T>
+__host__ __device__ constexpr int h_parts() {
+    return std::is_same<T, float>::value ? 2 : 1;
 }
 
 // storage scale of the populations: from the state when there is one, else 1
@@ -140,12 +177,30 @@ __global__ void k_moments(const S* __restrict__ f, double* __restrict__ m, doubl
     }
 }
 
+// P of one site's trial populations into the P f field of its ring slot (D3Q19: the halo-free sweep
+// reads the moments of its input from there)
+template <class L, typename T, typename S>
+__device__ __forceinline__ void store_trial_moments(S* __restrict__ pf, size_t sites, size_t i, const T* tv) {
+    T q[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+    for (int k = 0; k < L::Q; ++k) {
+        q[0] += tv[k];
+        if (L::cx(k)) q[1] += T(L::cx(k)) * tv[k];
+        if (L::cy(k)) q[2] += T(L::cy(k)) * tv[k];
+        if (L::D == 3 && L::cz(k)) q[3] += T(L::cz(k)) * tv[k];
+    }
+#pragma unroll
+    for (int c = 0; c <= L::D; ++c) pf[c * sites + i] = (S)q[c];
+}
+
 // Start of a physical step: h_q from the accepted moment histories (Eq. bdf2) and the trial
-// populations from the population-history extrapolation (Section 3.1) into the working slot.
+// populations from the population-history extrapolation (Section 3.1) into the working slot
+// (and, with pfbase, their moments P f into the slot's P f field).
 template <class L, typename T, typename S = T>
 __device__ __forceinline__ void step_begin_range(const DevState* __restrict__ st, S* __restrict__ fbase,
                                                  size_t fstride, const double* __restrict__ mbuf,
-                                                 T* __restrict__ h, size_t sites, size_t i0, size_t istride) {
+                                                 T* __restrict__ h, size_t sites, size_t i0, size_t istride,
+                                                 S* __restrict__ pfbase = nullptr, size_t pfstride = 0) {
     const DevState* vs = st;
     if (vs->prepared) return;  // formed by the previous step's k_step_end
     const int q = vs->q;
@@ -158,8 +213,10 @@ __device__ __forceinline__ void step_begin_range(const DevState* __restrict__ st
     const S* f1 = fbase + (size_t)vs->slot_fn[1] * fstride;
     const S* f2 = fbase + (size_t)vs->slot_fn[2] * fstride;
     S* ft = fbase + (size_t)vs->slot_cur * fstride;
+    S* pft = pfbase ? pfbase + (size_t)vs->slot_cur * pfstride : nullptr;
     const double c1 = vs->c1, c2 = vs->c2;
-    const float af = narrow_f64(vs->a), rf = q == 2 ? 1.0f / 3.0f : 0.0f;  // the sweep's binary32 a_q; c2/a_q
+    const float af = narrow_f64(vs->a);  // the sweep's binary32 a_q
+    const size_t lo_off = (size_t)(L::D + 1) * sites;
     (void)dt;
     const T sig = from_f64<T>(vs->fscale), isig = from_f64<T>(vs->isig);
     const double fc[4] = {0.0, vs->force[0], vs->force[1], vs->force[2]};
@@ -167,7 +224,23 @@ __device__ __forceinline__ void step_begin_range(const DevState* __restrict__ st
 #pragma unroll
         for (int c = 0; c <= L::D; ++c) {  // h = c1 m^n - c2 m^{n-1} + (0, F), as k_step_end forms it
             const size_t o = c * sites + i;
-            h[o] = bdf_history<T>(c1, mn[o], c2, mnm1[o], fc[c], af, rf);
+            bdf_history<T>(c1, mn[o], c2, mnm1[o], fc[c], af, q, h, o, lo_off);
+        }
+        if constexpr (L::D == 3) {
+            if (pft) {  // the trial in the storage type and its moments
+                T tv[L::Q];
+#pragma unroll
+                for (int k = 0; k < L::Q; ++k) {
+                    const size_t o = k * sites + i;
+                    const T v0 = ld_pop<T, S>(f0, o, sig);
+                    tv[k] = nav == 1 ? v0
+                                     : (nav == 2 ? T(2) * v0 - ld_pop<T, S>(f1, o, sig)
+                                                 : T(3) * (v0 - ld_pop<T, S>(f1, o, sig)) + ld_pop<T, S>(f2, o, sig));
+                    st_pop<T, S>(ft, o, tv[k], isig);
+                }
+                store_trial_moments<L, T, S>(pft, sites, i, tv);
+                continue;
+            }
         }
         if (nav == 1) {
 #pragma unroll
@@ -191,9 +264,10 @@ __device__ __forceinline__ void step_begin_range(const DevState* __restrict__ st
 
 template <class L, typename T, typename S = T>
 __global__ void k_step_begin(const DevState* __restrict__ st, S* __restrict__ fbase, size_t fstride,
-                             const double* __restrict__ mbuf, T* __restrict__ h, size_t sites) {
+                             const double* __restrict__ mbuf, T* __restrict__ h, size_t sites,
+                             S* __restrict__ pfbase, size_t pfstride) {
     step_begin_range<L, T, S>(st, fbase, fstride, mbuf, h, sites, blockIdx.x * (size_t)blockDim.x + threadIdx.x,
-                           (size_t)gridDim.x * blockDim.x);
+                           (size_t)gridDim.x * blockDim.x, pfbase, pfstride);
 }
 
 // Acceptance: m^{n+1} = R_{q,h}(f^{n+1}) with the unrotated histories (Eq. macro-reconstruct),
@@ -205,7 +279,8 @@ __global__ void k_step_begin(const DevState* __restrict__ st, S* __restrict__ fb
 template <class L, typename T, typename S = T, bool FORCE = true>
 __device__ __forceinline__ void step_end_range(const DevState* __restrict__ st, S* __restrict__ fbase,
                                                size_t fstride, double* __restrict__ mbuf, T* __restrict__ h,
-                                               size_t sites, size_t i0, size_t istride) {
+                                               size_t sites, size_t i0, size_t istride, S* __restrict__ pfbase = nullptr,
+                                               size_t pfstride = 0) {
     const DevState* vs = st;
     if (!vs->accepted) return;
     const double inv = vs->inv_a;
@@ -221,9 +296,11 @@ __device__ __forceinline__ void step_end_range(const DevState* __restrict__ st, 
     const S* __restrict__ f0 = fbase + (size_t)vs->slot_fn[0] * fstride;
     const S* __restrict__ f1 = fbase + (size_t)vs->slot_fn[1] * fstride;
     S* __restrict__ trial = fbase + (size_t)vs->slot_nxt * fstride;
+    S* __restrict__ ptrial = pfbase ? pfbase + (size_t)vs->slot_nxt * pfstride : nullptr;
     const T sig = from_f64<T>(vs->fscale), isig = from_f64<T>(vs->isig);
     const double n1 = vs->n1, n2 = vs->n2;  // BDF2 for the next step
     const float an = narrow_f64(vs->qa[1]);  // the next step's binary32 a_2, as its sweep will use it
+    const size_t lo_off = (size_t)(L::D + 1) * sites;
     const double k1 = vs->k1, k2 = vs->k2;  // formed once per step (FP64 products are slow on B300)
     // body force: (0, F) joins h in the reconstruction and in the next step's h (FORCE = false: F = 0)
     const double fc[4] = {0.0, FORCE ? vs->force[0] : 0.0, FORCE ? vs->force[1] : 0.0, FORCE ? vs->force[2] : 0.0};
@@ -266,7 +343,19 @@ __device__ __forceinline__ void step_end_range(const DevState* __restrict__ st, 
             const double mnew = FORCE ? fma(k1, mc, fma(-k2, mpv[c], fma(inv, md, kf[c])))
                                       : fma(k1, mc, fma(-k2, mpv[c], inv * md));
             mnm1[o] = mnew;
-            if (next) h[o] = bdf_history<T>(n1, mnew, n2, mc, fc[c], an, 1.0f / 3.0f);
+            if (next) bdf_history<T>(n1, mnew, n2, mc, fc[c], an, 2, h, o, lo_off);
+        }
+        if constexpr (L::D == 3) {
+            if (ptrial && nav >= 1) {
+                T tv[L::Q];
+#pragma unroll
+                for (int k = 0; k < L::Q; ++k) {
+                    tv[k] = nav == 1 ? fv[k] : (nav == 2 ? T(2) * fv[k] - g0[k] : T(3) * (fv[k] - g0[k]) + g1[k]);
+                    st_pop<T, S>(trial, k * sites + i, tv[k], isig);
+                }
+                store_trial_moments<L, T, S>(ptrial, sites, i, tv);
+                continue;
+            }
         }
         if (nav == 1) {
 #pragma unroll
@@ -285,11 +374,10 @@ __device__ __forceinline__ void step_end_range(const DevState* __restrict__ st, 
 // enough warps resident)
 template <class L, typename T, typename S = T, bool FORCE = true>
 __global__ void __launch_bounds__(kFieldThreads)
-    k_step_end(const DevState* __restrict__ st, S* __restrict__ fbase,
-                                                            size_t fstride, double* __restrict__ mbuf, T* __restrict__ h,
-                                                            size_t sites) {
+    k_step_end(const DevState* __restrict__ st, S* __restrict__ fbase, size_t fstride, double* __restrict__ mbuf,
+               T* __restrict__ h, size_t sites, S* __restrict__ pfbase, size_t pfstride) {
     step_end_range<L, T, S, FORCE>(st, fbase, fstride, mbuf, h, sites, blockIdx.x * (size_t)blockDim.x + threadIdx.x,
-                         (size_t)gridDim.x * blockDim.x);
+                                   (size_t)gridDim.x * blockDim.x, pfbase, pfstride);
 }
 
 // FP64 coefficients of the closed-form Schur solve (Eq. schur) at every masked wavevector, for

@@ -15,6 +15,7 @@
 #include "spectral3d.cuh"
 #include "sweep2d.cuh"
 #include "sweep3d.cuh"
+#include "sweep3p.cuh"
 
 using namespace msc;
 
@@ -56,7 +57,7 @@ P* at(msc_ctx* c, size_t off) {
 
 int sweep_blocks_for(int dim, int n, int precision) {
     if (dim == 2) return sweep2_geometry(n).blocks;
-    return sweep3_geometry(n, precision == MSC_FP64 ? 8 : 4).blocks;
+    return sweep3p_geometry(n, precision == MSC_FP64 ? 8 : 4).blocks;
 }
 
 // off-design TRT rates in effect (0 means the operating point)
@@ -105,8 +106,11 @@ bool compute_layout(const msc_lattice_desc* d, Layout* L) {
     L->state = take(sizeof(DevState));
     L->fstride = Q * sites * ep;
     L->fbuf = take(kNumFBuf * L->fstride);
+    // D3Q19: P f of every ring slot (the halo-free sweep reads its input's moments from there)
+    L->pfstride = F * sites;
+    L->pf = take(d->dim == 3 ? kNumFBuf * F * sites * ep : 0);
     L->mbuf = take(2 * F * sites * 8);
-    L->h = take(F * sites * e);
+    L->h = take(F * sites * e * (e == 4 ? 2 : 1));  // binary32 storage: h as a hi + lo pair
     L->pr = take(F * sites * e);
     L->dm = take(F * sites * e);
     L->spec = take(spec_bytes(d->dim, d->n, d->precision));
@@ -179,6 +183,36 @@ Sweep3Args<T> sweep3_args_graph(msc_ctx* c) {
     A.replay_counts = at<int>(c, c->lay.replay);
     A.max_steps = c->desc.max_steps;
     return A;
+}
+
+// the D3Q19 sweep of the march: halo-free, reading and writing the P f field of its ring slots
+template <typename T>
+Sweep3PArgs<T> sweep3p_args_graph(msc_ctx* c) {
+    Sweep3PArgs<T> A;
+    memset(&A, 0, sizeof(A));
+    A.g = sweep3p_geometry(c->desc.n, sizeof(T));
+    A.dm = at<T>(c, c->lay.dm);
+    A.h = at<T>(c, c->lay.h);
+    A.pr = at<T>(c, c->lay.pr);
+    A.partial = at<double>(c, c->lay.partial);
+    A.counter = at<unsigned int>(c, c->lay.counter);
+    A.n = c->desc.n;
+    A.st = at<DevState>(c, c->lay.state);
+    A.fbase = at<T>(c, c->lay.fbuf);
+    A.fstride = c->lay.fstride / sizeof(T);
+    A.pfbase = at<T>(c, c->lay.pf);
+    A.pfstride = c->lay.pfstride;
+    A.hist = at<double>(c, c->lay.hist);
+    A.hist_cap = c->desc.hist_cap;
+    A.replay_counts = at<int>(c, c->lay.replay);
+    A.max_steps = c->desc.max_steps;
+    return A;
+}
+
+// P f field base of a context's ring (D3Q19), null for D2Q9
+template <typename FS>
+FS* pf_base(msc_ctx* c) {
+    return c->desc.dim == 3 ? at<FS>(c, c->lay.pf) : nullptr;
 }
 
 cudaGraphNode_t add_kernel(cudaGraph_t g, const std::vector<cudaGraphNode_t>& deps, const void* fn,
@@ -269,6 +303,7 @@ int set_smem_limits(int dim, int n) {
     } else {
         if (set_spec3_smem_limits<T>(n) != 0) return MSC_ERR_CUDA;
         if (set_sweep3_smem_limits<T>(n) != 0) return MSC_ERR_CUDA;
+        if (set_sweep3p_smem_limits<T>(n) != 0) return MSC_ERR_CUDA;
     }
     return MSC_OK;
 }
@@ -302,13 +337,15 @@ int build_march_graph(msc_ctx* c) {
     int cond1 = 1;
     void* a_setup[] = {&st, &h_iter, &cond1};
     cudaGraphNode_t setup = add_kernel(body_step, {}, (const void*)k_step_setup, dim3(1), dim3(1), 0, a_setup, &err);
-    void* a_begin[] = {&st, &fbase, (void*)&fstride, &mbuf, &h, &sites};
+    FS* pfbase = pf_base<FS>(c);
+    size_t pfstride = c->lay.pfstride;
+    void* a_begin[] = {&st, &fbase, (void*)&fstride, &mbuf, &h, &sites, &pfbase, &pfstride};
     cudaGraphNode_t begin = add_kernel(body_step, {setup}, (const void*)k_step_begin<L, T, FS>, dim3(fgrid),
                                        dim3(kFieldThreads), 0, a_begin, &err);
     cudaGraph_t body_iter;
     cudaGraphNode_t wit = add_cond(body_step, {begin}, h_iter, cudaGraphCondTypeWhile, &body_iter, &err);
     if (err != cudaSuccess) { cudaGraphDestroy(g); return MSC_ERR_CUDA; }
-    void* a_end[] = {&st, &fbase, (void*)&fstride, &mbuf, &h, &sites};
+    void* a_end[] = {&st, &fbase, (void*)&fstride, &mbuf, &h, &sites, &pfbase, &pfstride};
     cudaGraphNode_t end = add_kernel(body_step, {wit}, step_end_kernel<L, T, FS>(c), dim3(fgrid),
                                      dim3(kFieldThreads), 0, a_end, &err);
     void* a_fin[] = {&st, &iters, &max_steps, &h_step, &cond1};
@@ -325,13 +362,13 @@ int build_march_graph(msc_ctx* c) {
         sw = add_kernel(body_iter, {}, sweep2_kernel<T, FS, false, true>(c), dim3(sweep2_geometry(c->desc.n).blocks),
                         dim3(kSweepWarps * 32), 0, a_sw, &err);
     } else {
-        Sweep3Args<T> A = sweep3_args_graph<T>(c);
+        Sweep3PArgs<T> A = sweep3p_args_graph<T>(c);
         A.h_iter = h_iter;
         A.h_corr = h_corr;
         A.cond = 1;
         void* a_sw[] = {&A};
-        sw = add_kernel(body_iter, {}, (const void*)k_sweep3<T, false, true>, dim3(A.g.blocks),
-                        dim3(A.g.threads), A.g.smem, a_sw, &err);
+        sw = add_kernel(body_iter, {}, (const void*)k_sweep3p<T, true>, dim3(A.g.blocks), dim3(kP3Threads), A.g.smem,
+                        a_sw, &err);
     }
     cudaGraph_t body_corr;
     add_cond(body_iter, {sw}, h_corr, cudaGraphCondTypeIf, &body_corr, &err);
@@ -521,7 +558,8 @@ int run_stepwise(msc_ctx* c, int n_steps) {
     DevState hs;
     for (int step = 0; step < n_steps; ++step) {
         k_step_setup<<<1, 1, 0, c->stream>>>(st, none, 0);
-        k_step_begin<L, T, FS><<<fgrid, kFieldThreads, 0, c->stream>>>(st, fbase, fstride, mbuf, h, c->sites);
+        k_step_begin<L, T, FS><<<fgrid, kFieldThreads, 0, c->stream>>>(st, fbase, fstride, mbuf, h, c->sites,
+                                                                        pf_base<FS>(c), c->lay.pfstride);
         for (;;) {
             if (L::D == 2) {
                 Sweep2Args<T, FS> A = sweep2_args_graph<T, FS>(c);
@@ -529,8 +567,8 @@ int run_stepwise(msc_ctx* c, int n_steps) {
                 CK(cudaLaunchKernel(sweep2_kernel<T, FS, false, true>(c), dim3(sweep2_geometry(c->desc.n).blocks),
                                     dim3(kSweepWarps * 32), aa, 0, c->stream));
             } else {
-                Sweep3Args<T> A = sweep3_args_graph<T>(c);
-                k_sweep3<T, false, true><<<A.g.blocks, A.g.threads, A.g.smem, c->stream>>>(A);
+                Sweep3PArgs<T> A = sweep3p_args_graph<T>(c);
+                k_sweep3p<T, true><<<A.g.blocks, kP3Threads, A.g.smem, c->stream>>>(A);
             }
             CK(cudaGetLastError());
             rc = read_state(c, &hs);
@@ -543,7 +581,9 @@ int run_stepwise(msc_ctx* c, int n_steps) {
             if (hs.accepted || hs.status != MSC_OK) break;
         }
         {
-            void* ea[] = {&st, &fbase, (void*)&fstride, &mbuf, &h, (void*)&c->sites};
+            FS* pfb = pf_base<FS>(c);
+            size_t pfs = c->lay.pfstride;
+            void* ea[] = {&st, &fbase, (void*)&fstride, &mbuf, &h, (void*)&c->sites, &pfb, &pfs};
             CK(cudaLaunchKernel(step_end_kernel<L, T, FS>(c), dim3(fgrid), dim3(kFieldThreads), ea, 0, c->stream));
         }
         k_step_finish<<<1, 1, 0, c->stream>>>(st, at<int>(c, c->lay.iters), c->desc.max_steps, none, 0);
@@ -602,8 +642,10 @@ int msc_create(msc_ctx** out, const msc_lattice_desc* desc, void* ws, size_t byt
     c->ws = (unsigned char*)ws;
     c->stream = (cudaStream_t)stream;
     c->coef_dirty = true;
-    // zero the state, the reduction counter and the adjoint warm start (a first warm step starts cold)
+    // zero the state, the reduction counter, h (read by stateless timing sweeps before any step) and
+    // the adjoint warm start (a first warm step starts cold)
     if (cudaMemsetAsync(c->ws + L.state, 0, sizeof(DevState), c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->ws + L.h, 0, L.pr - L.h, c->stream) != cudaSuccess ||
         cudaMemsetAsync(c->ws + L.counter, 0, 256, c->stream) != cudaSuccess ||
         cudaMemsetAsync(c->ws + L.adjw, 0, L.iters - L.adjw, c->stream) != cudaSuccess) {
         free(c);
@@ -894,6 +936,26 @@ int msc_load_state(msc_ctx* c, const void* blob, size_t bytes) {
     return MSC_OK;
 }
 
+int msc_bounds_check_report(unsigned long long* count, unsigned long long* first, int reset) {
+    if (!count || !first) return MSC_ERR_ARG;
+    *count = 0;
+    *first = 0;
+#ifdef MSC_BOUNDS_CHECK
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpyFromSymbol(count, g_oob_count, sizeof(unsigned long long)));
+    CK(cudaMemcpyFromSymbol(first, g_oob_first, sizeof(unsigned long long)));
+    if (reset) {
+        const unsigned long long zero = 0;
+        CK(cudaMemcpyToSymbol(g_oob_count, &zero, sizeof(zero)));
+        CK(cudaMemcpyToSymbol(g_oob_first, &zero, sizeof(zero)));
+    }
+    return MSC_OK;
+#else
+    (void)reset;
+    return MSC_ERR_STATE;
+#endif
+}
+
 // ---- stage entry points ------------------------------------------------------------------------
 
 size_t msc_stage_scratch_bytes(int dim, int n, int precision) {
@@ -903,6 +965,7 @@ size_t msc_stage_scratch_bytes(int dim, int n, int precision) {
     o = align_up(o + (size_t)sweep_blocks_for(dim, n, precision) * 8, 256);  // partials
     o = align_up(o + (size_t)n * (precision == MSC_FP64 ? 16 : 8), 256);  // twiddles
     o = align_up(o + spec_bytes(dim, n, precision), 256);         // half spectrum
+    if (dim == 3) o = align_up(o + (size_t)2 * 4 * n * n * n * field_elem(precision), 256);  // P f in, out
     return o;
 }
 
@@ -914,6 +977,7 @@ struct StageScratch {
     double* partial;
     void* tw;
     void* spec;
+    void* pf;  // D3Q19 sweep: P f of the input, then of the output
 };
 StageScratch stage_scratch(int dim, int n, int precision, void* base) {
     StageScratch s;
@@ -926,12 +990,15 @@ StageScratch stage_scratch(int dim, int n, int precision, void* base) {
     s.tw = b + o;
     o = align_up(o + (size_t)n * (precision == MSC_FP64 ? 16 : 8), 256);
     s.spec = b + o;
+    o = align_up(o + spec_bytes(dim, n, precision), 256);
+    s.pf = dim == 3 ? b + o : nullptr;
     return s;
 }
 
 template <typename T, typename FS = T>
 int stage_sweep(int dim, int n, double a, const void* fin, const void* dm, const void* h, void* fout,
-                void* pr, double* sumsq, void* scratch, cudaStream_t stream, double wp = 0.0, double wm = 0.0) {
+                void* pr, double* sumsq, void* scratch, cudaStream_t stream, double wp = 0.0, double wm = 0.0,
+                bool hpair = false) {
     StageScratch S = stage_scratch(dim, n, sizeof(T) == 8 ? MSC_FP64 : MSC_FP32, scratch);
     CK(cudaMemsetAsync(S.counter, 0, 4, stream));
     if (dim == 2) {
@@ -958,17 +1025,29 @@ int stage_sweep(int dim, int n, double a, const void* fin, const void* dm, const
         A.nrowblk = g.nrowblk;
         if (wp > 0.0)
             k_sweep2<T, FS, false, false, true><<<g.blocks, kSweepWarps * 32, 0, stream>>>(A);
+        else if (hpair)
+            k_sweep2<T, FS, false, false, false, std::is_same<T, float>::value><<<g.blocks, kSweepWarps * 32, 0,
+                                                                                 stream>>>(A);
         else
             k_sweep2<T, FS, false, false><<<g.blocks, kSweepWarps * 32, 0, stream>>>(A);
     } else if constexpr (std::is_same<T, FS>::value) {
-        if (set_sweep3_smem_limits<T>(n) != 0) return MSC_ERR_CUDA;
-        Sweep3Args<T> A;
+        // the march's halo-free D3Q19 sweep: P f of the input first, then the sweep
+        if (set_sweep3p_smem_limits<T>(n) != 0) return MSC_ERR_CUDA;
+        const size_t sites = (size_t)n * n * n;
+        T* pfin = (T*)S.pf;
+        T* pfout = pfin + 4 * sites;
+        size_t b = (sites + kFieldThreads - 1) / kFieldThreads;
+        if (b > 148 * 12) b = 148 * 12;
+        k_pop_moments3<T><<<(int)b, kFieldThreads, 0, stream>>>((const T*)fin, pfin, sites);
+        Sweep3PArgs<T> A;
         memset(&A, 0, sizeof(A));
-        A.g = sweep3_geometry(n, sizeof(T));
+        A.g = sweep3p_geometry(n, sizeof(T));
         A.fin = (const T*)fin;
+        A.pfin = pfin;
         A.dm = (const T*)dm;
         A.h = (const T*)h;
         A.fout = (T*)fout;
+        A.pfout = pfout;
         A.pr = (T*)pr;
         A.a = a;
         A.inv = 1.0 / (1.0 + a / 2.0);
@@ -977,7 +1056,7 @@ int stage_sweep(int dim, int n, double a, const void* fin, const void* dm, const
         A.partial = S.partial;
         A.counter = S.counter;
         A.n = n;
-        k_sweep3<T, false, false><<<A.g.blocks, A.g.threads, A.g.smem, stream>>>(A);
+        k_sweep3p<T, false><<<A.g.blocks, kP3Threads, A.g.smem, stream>>>(A);
     }
     CK(cudaGetLastError());
     return MSC_OK;
@@ -1036,6 +1115,58 @@ int msc_sweep(int dim, int n, int precision, double a, const void* f_in, const v
     return stage_sweep<float>(dim, n, a, f_in, dm, h, f_out, pr_out, sumsq_out, scratch, (cudaStream_t)stream);
 }
 
+int msc_sweep_d3q19_pf(int n, int precision, double a, const void* f_in, const void* pf_in, const void* dm,
+                       const void* h, void* f_out, void* pf_out, void* pr_out, double* sumsq_out, void* scratch,
+                       size_t scratch_bytes, void* stream) {
+    if (!valid_lattice(3, n, precision) || precision == MSC_FP16 || !f_in || !pf_in || !h || !f_out || !pf_out ||
+        !pr_out || !sumsq_out || !scratch || f_in == f_out || pf_in == pf_out ||
+        scratch_bytes < msc_stage_scratch_bytes(3, n, precision) || !(a >= 0.0))
+        return MSC_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    auto run = [&](auto tag) -> int {
+        using T = decltype(tag);
+        if (set_sweep3p_smem_limits<T>(n) != 0) return MSC_ERR_CUDA;
+        StageScratch S = stage_scratch(3, n, precision, scratch);
+        CK(cudaMemsetAsync(S.counter, 0, 4, st));
+        Sweep3PArgs<T> A;
+        memset(&A, 0, sizeof(A));
+        A.g = sweep3p_geometry(n, sizeof(T));
+        A.fin = (const T*)f_in;
+        A.pfin = (const T*)pf_in;
+        A.dm = (const T*)dm;
+        A.h = (const T*)h;
+        A.fout = (T*)f_out;
+        A.pfout = (T*)pf_out;
+        A.pr = (T*)pr_out;
+        A.a = a;
+        A.inv = 1.0 / (1.0 + a / 2.0);
+        A.lift = dm != nullptr;
+        A.sumsq_out = sumsq_out;
+        A.partial = S.partial;
+        A.counter = S.counter;
+        A.n = n;
+        k_sweep3p<T, false><<<A.g.blocks, kP3Threads, A.g.smem, st>>>(A);
+        CK(cudaGetLastError());
+        return MSC_OK;
+    };
+    return precision == MSC_FP64 ? run(double{}) : run(float{});
+}
+
+int msc_sweep_hpair(int n, int precision, double a, const void* f_in, const void* dm, const void* h,
+                    void* f_out, void* pr_out, double* sumsq_out, void* scratch, size_t scratch_bytes,
+                    void* stream) {
+    if (!valid_lattice(2, n, precision) || !f_in || !h || !f_out || !pr_out || !sumsq_out || !scratch ||
+        f_in == f_out || scratch_bytes < msc_stage_scratch_bytes(2, n, precision) || !(a >= 0.0))
+        return MSC_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (precision == MSC_FP64)
+        return stage_sweep<double>(2, n, a, f_in, dm, h, f_out, pr_out, sumsq_out, scratch, st);
+    if (precision == MSC_FP16)
+        return stage_sweep<float, __half>(2, n, a, f_in, dm, h, f_out, pr_out, sumsq_out, scratch, st, 0.0, 0.0,
+                                          true);
+    return stage_sweep<float>(2, n, a, f_in, dm, h, f_out, pr_out, sumsq_out, scratch, st, 0.0, 0.0, true);
+}
+
 int msc_sweep_trt(int n, int precision, double a, double omega_p, double omega_m, const void* f_in, const void* dm,
                   const void* h, void* f_out, void* pr_out, double* sumsq_out, void* scratch, size_t scratch_bytes,
                   void* stream) {
@@ -1090,3 +1221,4 @@ int msc_equilibrium(int dim, int n, int precision, const double* p, const double
 #include "batch_api.cuh"
 #include "adjoint_api.cuh"
 #include "fullsym_api.cuh"
+#include "selftest.cuh"

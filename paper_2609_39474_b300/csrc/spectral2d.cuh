@@ -95,6 +95,9 @@ __device__ __forceinline__ void rowfft_fwd_block(const Spec2Args<T>& A, int bid)
     for (int t = threadIdx.x; t < P * n; t += blockDim.x) {
         const int p = t >> logn;
         const int x = t & (n - 1);
+        if (!MSC_INB(((size_t)c * A.rows + y0 + 2 * p + 1) * n + x, (size_t)A.nf * A.rows * n, 11) ||
+            !MSC_INB(p * plen + pad(x), P * plen, 12))
+            continue;
         C z;
         z.x = rows[(size_t)(2 * p) * n + x];
         z.y = rows[(size_t)(2 * p + 1) * n + x];
@@ -119,7 +122,8 @@ __device__ __forceinline__ void rowfft_fwd_block(const Spec2Args<T>& A, int bid)
             v.x = T(0.5) * (zj.y + zm.y);
             v.y = T(-0.5) * (zj.x - zm.x);
         }
-        out[(size_t)jx * A.rows + r] = v;
+        if (MSC_INB((size_t)c * nx4 * A.rows + y0 + (size_t)jx * A.rows + r, (size_t)A.nf * nx4 * A.rows, 13))
+            out[(size_t)jx * A.rows + r] = v;
     }
 }
 
@@ -151,6 +155,10 @@ __device__ __forceinline__ void rowfft_inv_block(const Spec2Args<T>& A, int bid)
         const int j = t >> lp;
         C z;
         z.x = T(0); z.y = T(0);
+        const int jr = j <= n / 4 ? j : n - j;
+        if (!MSC_INB((size_t)c * nx4 * A.rows + y0 + (size_t)(jr <= n / 4 ? jr : 0) * A.rows + 2 * p + 1,
+                     (size_t)A.nf * nx4 * A.rows, 14))
+            continue;
         if (j <= n / 4) {
             const C xa = in[(size_t)j * A.rows + 2 * p], xb = in[(size_t)j * A.rows + 2 * p + 1];
             z.x = xa.x - xb.y;
@@ -199,6 +207,7 @@ __device__ __forceinline__ void rowfft_inv_block(const Spec2Args<T>& A, int bid)
     for (int t = threadIdx.x; t < P * n; t += blockDim.x) {
         const int p = t >> logn;
         const int x = t & (n - 1);
+        if (!MSC_INB(((size_t)c * A.rows + y0 + 2 * p + 1) * n + x, (size_t)A.nf * A.rows * n, 15)) continue;
         const C z = s[p * plen + pad(x)];
         rows[(size_t)(2 * p) * n + x] = z.x;
         rows[(size_t)(2 * p + 1) * n + x] = z.y;
@@ -311,8 +320,9 @@ __device__ __forceinline__ void colsolve_block(const Spec2Args<T>& A, int bid, i
         const int gy = t & (gn - 1);  // g * n + y
         C v;
         v.x = T(0); v.y = T(0);
-        if ((gy >> logn) < ng) v = col[c * fs + gy];
-        s[(c * G + (gy >> logn)) * plen + pad(gy & (n - 1))] = v;
+        if ((gy >> logn) < ng && MSC_INB((size_t)jx0 * n + c * fs + gy, (size_t)A.nf * fs, 16)) v = col[c * fs + gy];
+        if (MSC_INB((c * G + (gy >> logn)) * plen + pad(gy & (n - 1)), 3 * G * plen, 17))
+            s[(c * G + (gy >> logn)) * plen + pad(gy & (n - 1))] = v;
     }
     __syncthreads();
     fft_stockham<C, false>(s, n, logn, 3 * G, A.tw);
@@ -329,7 +339,8 @@ __device__ __forceinline__ void colsolve_block(const Spec2Args<T>& A, int bid, i
     for (int t = threadIdx.x; t < 3 * gn; t += blockDim.x) {
         const int c = t >> lgn;
         const int gy = t & (gn - 1);
-        if ((gy >> logn) < ng) col[c * fs + gy] = s[(c * G + (gy >> logn)) * plen + pad(gy & (n - 1))];
+        if ((gy >> logn) < ng && MSC_INB((size_t)jx0 * n + c * fs + gy, (size_t)A.nf * fs, 16))
+            col[c * fs + gy] = s[(c * G + (gy >> logn)) * plen + pad(gy & (n - 1))];
     }
 }
 
@@ -374,6 +385,7 @@ __global__ void __launch_bounds__(96) k_colsolve_1024(Spec2Args<float> A) {
     C* col = A.spec + ((size_t)warp * nx4 + jx) * n;  // spec[c][jx][y], c = warp
     C* line = s + warp * plen;
     C v[32];
+    if (!MSC_INB(((size_t)warp * nx4 + jx) * n + 1023, (size_t)3 * nx4 * n, 18)) return;
 #pragma unroll
     for (int r = 0; r < 32; ++r) v[r] = col[lane + 32 * r];
     fft1024_warp<C, false>(v, line, A.tw);

@@ -97,7 +97,9 @@ __device__ inline void march_after_sweep(DevState* st, double total, double qsit
 
 // One warp unit of the sweep: output columns [strip*30, strip*30 + 30) of rows [rb*hb, rb*hb + hb).
 // Returns this lane's share of sum r^2 (zero in EXPLICIT mode).  Called by all 32 lanes.
-template <typename T, typename S, bool EXPLICIT, bool TRT = false>
+// HPAIR: h is a binary32 pair, the low parts at hh + 3 n^2 (the march's working field); the
+// differences h - a m are then formed as fma(-a, m, h_hi) + h_lo.
+template <typename T, typename S, bool EXPLICIT, bool TRT = false, bool HPAIR = false>
 __device__ __forceinline__ double sweep2_unit(const S* fin, const T* dm, const T* hh, S* fout, T* pr, T a, T inv,
                                               int lift, int n, int hb, int strip, int rb, int lane,
                                               T sig = T(1), T isig = T(1), T wp = T(1), T wm = T(1)) {
@@ -118,26 +120,30 @@ __device__ __forceinline__ double sweep2_unit(const S* fin, const T* dm, const T
     // software pipeline, two rows deep: the loads of rows j+1 and j+2 are in flight while row j is
     // collided (a warp keeps ~2 rows x 15 values of 128 B outstanding; the kernel is bound by load
     // latency, not by issue)
-    T nf[9], ndp = T(0), ndx = T(0), ndy = T(0), nh0 = T(0), nh1 = T(0), nh2 = T(0);  // row j+1
-    T qf[9], qdp = T(0), qdx = T(0), qdy = T(0), qh0 = T(0), qh1 = T(0), qh2 = T(0);  // row j+2
-    auto load_row = [&](int jr, T* g, T& gdp, T& gdx, T& gdy, T& gh0, T& gh1, T& gh2) {
+    T nf[9], ndp = T(0), ndx = T(0), ndy = T(0), nh[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};  // row j+1
+    T qf[9], qdp = T(0), qdx = T(0), qdy = T(0), qh[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};  // row j+2
+    auto load_row = [&](int jr, T* g, T& gdp, T& gdx, T& gdy, T* gh) {
         const size_t id = (size_t)(jr & nmask) * n + x;
+        if (!MSC_INB(id, NN, 1)) return;
 #pragma unroll
         for (int k = 0; k < 9; ++k) g[k] = ld_pop<T, S>(fin, k * NN + id, sig);
         if (!EXPLICIT) {
             if (lift) { gdp = dm[id]; gdx = dm[NN + id]; gdy = dm[2 * NN + id]; }
-            gh0 = hh[id]; gh1 = hh[NN + id]; gh2 = hh[2 * NN + id];
+#pragma unroll
+            for (int c = 0; c < (HPAIR ? 6 : 3); ++c) gh[c] = hh[c * NN + id];
         }
     };
-    load_row(y0 - 1, nf, ndp, ndx, ndy, nh0, nh1, nh2);
-    load_row(y0, qf, qdp, qdx, qdy, qh0, qh1, qh2);
+    load_row(y0 - 1, nf, ndp, ndx, ndy, nh);
+    load_row(y0, qf, qdp, qdx, qdy, qh);
     for (int j = y0 - 1; j <= y0 + hb; ++j) {
-        T f[9];
+        T f[9], hv[6];
 #pragma unroll
         for (int k = 0; k < 9; ++k) { f[k] = nf[k]; nf[k] = qf[k]; }
-        const T dp = ndp, dux = ndx, duy = ndy, h0 = nh0, h1 = nh1, h2 = nh2;
-        ndp = qdp; ndx = qdx; ndy = qdy; nh0 = qh0; nh1 = qh1; nh2 = qh2;
-        if (j + 2 <= y0 + hb) load_row(j + 2, qf, qdp, qdx, qdy, qh0, qh1, qh2);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) { hv[c] = nh[c]; nh[c] = qh[c]; }
+        const T dp = ndp, dux = ndx, duy = ndy;
+        ndp = qdp; ndx = qdx; ndy = qdy;
+        if (j + 2 <= y0 + hb) load_row(j + 2, qf, qdp, qdx, qdy, qh);
         if (!EXPLICIT && lift) {  // trial f = f_T,prev + E dm   (Eq. lift)
 #pragma unroll
             for (int k = 0; k < 9; ++k)
@@ -152,6 +158,7 @@ __device__ __forceinline__ double sweep2_unit(const S* fin, const T* dm, const T
             if (L::cy(k)) jy += T(L::cy(k)) * f[k];
         }
         T p, ux, uy, s0 = T(0), sx = T(0), sy = T(0);
+        T yx = T(0), yy = T(0);  // HPAIR: u = (jx + yx, jy + yy) kept unrounded for the collision
         if (EXPLICIT) {
             p = rho; ux = jx; uy = jy;
         } else {  // half-source reconstruction and source moments (Eqs. macro-reconstruct, source-moments)
@@ -159,15 +166,63 @@ __device__ __forceinline__ double sweep2_unit(const S* fin, const T* dm, const T
             // 1/(1 + a/2) then scales only the O(a) term, not m itself, so it cannot bias the moments
             // by a relative unit roundoff (which the long-wave solve would amplify by ~1/a)
             const T hinv = T(0.5) * inv;
-            p = rho + (h0 - a * rho) * hinv;
-            ux = jx + (h1 - a * jx) * hinv;
-            uy = jy + (h2 - a * jy) * hinv;
-            s0 = h0 - a * p;
-            sx = h1 - a * ux;
-            sy = h2 - a * uy;
+            if constexpr (HPAIR) {
+                // d = h - a P f with h = hi + lo: the FMA forms hi - a P f exactly and rounds once, then
+                // lo is added, so d keeps its own relative accuracy where h ~ a m.  The source follows
+                // from d alone, s = h - a m = (h - a P f) / (1 + a/2): it never sees the rounding of m
+                // (a u_r |m| = u_r |h| absolute, as large as the rounding of a single binary32 h).
+                const T d0 = fma(-a, rho, hv[0]) + hv[3];
+                const T dx = fma(-a, jx, hv[1]) + hv[4];
+                const T dy = fma(-a, jy, hv[2]) + hv[5];
+                p = rho + d0 * hinv;
+                yx = dx * hinv;
+                yy = dy * hinv;
+                ux = jx + yx;
+                uy = jy + yy;
+                s0 = d0 * inv;
+                sx = dx * inv;
+                sy = dy * inv;
+            } else {
+                p = rho + (hv[0] - a * rho) * hinv;
+                ux = jx + (hv[1] - a * jx) * hinv;
+                uy = jy + (hv[2] - a * jy) * hinv;
+                s0 = hv[0] - a * p;
+                sx = hv[1] - a * ux;
+                sy = hv[2] - a * uy;
+            }
         }
         T C[9];
-        if constexpr (!TRT) {
+        if constexpr (!TRT && HPAIR) {
+            // operating-point collision C = f_eq + Phi/2 (Eq. collision-operating) in binary32 with the
+            // dominant term kept exact.  With u = J + Y (J = P_u f the moment sums, Y the O(a) correction)
+            // C_k = (3 w_k) c_k.J + w_k (A0 + 3 c_k.Y + 1.5 c_k.s + 4.5 c_k.u (c_k.u + c_k.s)): the first
+            // term is ~10^3 times the rest and is formed exactly (two-sum of c_k.J, two-product with the
+            // split weight 3 w_k = hi + lo), the rest is small and rounds relative to its own size, and
+            // the sum rounds once.  Forming u = J + Y in binary32 instead would quantise the slowly
+            // varying Y on the grid of J: a rounding error that is smooth across sites, so that the
+            // collision's mass and momentum are off by a long-wave field which the shadow solve's
+            // 1/(a + nu |k|^2) and the march's steps accumulate (at N = 1024, dt = 307, ~40 times the
+            // level of independent per-site rounding errors).
+            const T A0 = p + T(0.5) * s0 - T(1.5) * (ux * ux + uy * uy) - T(1.5) * (ux * sx + uy * sy);
+#pragma unroll
+            for (int k = 0; k < 9; ++k) {
+                const T cs = T(L::cx(k)) * sx + T(L::cy(k)) * sy;
+                if (L::cx(k) == 0 && L::cy(k) == 0) {
+                    C[k] = wmul<T>(L::w(k), A0 + T(1.5) * cs);
+                    continue;
+                }
+                T cjh, cje = T(0);  // c_k.J = cjh + cje exactly
+                if (L::cx(k) != 0 && L::cy(k) != 0) two_sum(T(L::cx(k)) * jx, T(L::cy(k)) * jy, cjh, cje);
+                else cjh = L::cx(k) != 0 ? T(L::cx(k)) * jx : T(L::cy(k)) * jy;
+                const T cyk = T(L::cx(k)) * yx + T(L::cy(k)) * yy;
+                const T cu = cjh + (cje + cyk);
+                const T small = A0 + T(3) * (cje + cyk) + T(1.5) * cs + T(4.5) * cu * (cu + cs);
+                const T w3h = (T)(3.0 * L::w(k)), w3l = (T)(3.0 * L::w(k) - (double)w3h);
+                const T ph = w3h * cjh;
+                const T pe = fma(w3h, cjh, -ph) + w3l * cjh;
+                C[k] = ph + (pe + wmul<T>(L::w(k), small));
+            }
+        } else if constexpr (!TRT) {
             // operating-point collision C = f_eq + Phi/2 (Eq. collision-operating)
             const T A0 = p + T(0.5) * s0 - T(1.5) * (ux * ux + uy * uy) - T(1.5) * (ux * sx + uy * sy);
 #pragma unroll
@@ -209,7 +264,7 @@ __device__ __forceinline__ double sweep2_unit(const S* fin, const T* dm, const T
 #pragma unroll
         for (int k = 0; k < 9; ++k)
             if (L::cy(k) == -1) Ar[k] = C[k];
-        if (j - 1 >= y0 && out_lane) {
+        if (j - 1 >= y0 && out_lane && MSC_INB((size_t)((j - 1) & nmask) * n + x, NN, 2)) {
             const size_t oidx = (size_t)((j - 1) & nmask) * n + x;
 #pragma unroll
             for (int k = 0; k < 9; ++k) st_pop<T, S>(fout, k * NN + oidx, Ar[k], isig);
@@ -243,7 +298,11 @@ __device__ __forceinline__ double sweep2_unit(const S* fin, const T* dm, const T
 }
 
 // FP32 operating-point sweeps keep five blocks (20 warps, two rows of loads in flight each) per SM
-template <typename T, typename S, bool EXPLICIT, bool GRAPH, bool TRT = false>
+// HPAIR: h is the march's binary32 pair and the collision keeps its dominant term exact (graph-mode
+// march sweeps with binary32 arithmetic, or the stage call msc_sweep_hpair); the explicit LBM keeps
+// the plain binary32 collision
+template <typename T, typename S, bool EXPLICIT, bool GRAPH, bool TRT = false,
+          bool HPAIR = GRAPH && !EXPLICIT && std::is_same<T, float>::value>
 __global__ void __launch_bounds__(kSweepWarps * 32, sizeof(T) == 4 && !TRT ? 5 : 1) k_sweep2(Sweep2Args<T, S> A) {
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -286,8 +345,9 @@ __global__ void __launch_bounds__(kSweepWarps * 32, sizeof(T) == 4 && !TRT ? 5 :
     const int unit = blockIdx.x * kSweepWarps + warp;
     double ssq = 0.0;
     if (unit < A.nstrips * A.nrowblk)  // warp-uniform
-        ssq = sweep2_unit<T, S, EXPLICIT, TRT>(fin, dm, hh, fout, pr, a, inv, lift, n, A.hb, unit % A.nstrips,
-                                               unit / A.nstrips, lane, (T)fs, (T)ifs, (T)wpd, (T)wmd);
+        ssq = sweep2_unit<T, S, EXPLICIT, TRT, HPAIR>(
+            fin, dm, hh, fout, pr, a, inv, lift, n, A.hb, unit % A.nstrips, unit / A.nstrips, lane, (T)fs, (T)ifs,
+            (T)wpd, (T)wmd);
     if (EXPLICIT) return;
 
     // ---- residual norm: block partials, last block reduces in a fixed order ----
@@ -332,8 +392,8 @@ struct Sweep2Geom {
     int nstrips, hb, nrowblk, blocks;
 };
 
-inline Sweep2Geom sweep2_geometry(int n) {
-    Sweep2Geom g;
+constexpr Sweep2Geom sweep2_geometry(int n) {
+    Sweep2Geom g{};
     g.nstrips = (n + kStripOut - 1) / kStripOut;
     // largest row block (<= 64, dividing n) that still gives 12 warps per SM: fewer halo rows, and
     // one resident wave where 16 warps per SM would need 1.5 (N = 1024: 560 blocks instead of 1120,

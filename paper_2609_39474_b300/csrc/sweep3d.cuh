@@ -1,6 +1,8 @@
-// D3Q19 fused collide-stream sweep (same equations as the D2Q9 sweep: Eqs. macro-reconstruct,
-// source-moments, source-distribution, collision-operating, sweep, residual) and the explicit
-// D3Q19 LBM step.
+// D3Q19 collide-stream sweep in push form with population halos: the explicit D3Q19 LBM step (the
+// baseline, EXPLICIT) and, in its general form, the fused sweep of the corrected iteration (Eqs.
+// macro-reconstruct, source-moments, source-distribution, collision-operating, sweep, residual).
+// The march and the stage call use the halo-free sweep of sweep3p.cuh instead, so only the explicit
+// step is instantiated.
 //
 // Design: a block owns a 32 x TYB tile of (x, y) columns (30 x (TYB-2) output columns plus a
 // one-column halo on each side) and marches along z over HB output planes.  For each plane it
@@ -139,9 +141,12 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 512) k_sweep3(Sweep3Arg
     for (int j = z0 - 1; j <= z0 + A.g.hb; ++j) {
         const size_t idx = (size_t)(j & m) * n * n + col;
         T f[19];
+        const bool idx_ok = MSC_INB(idx, NNN, 3);
+        if (idx_ok) {
 #pragma unroll
-        for (int k = 0; k < 19; ++k) f[k] = fin[k * NNN + idx];
-        if (!EXPLICIT && lift) {
+            for (int k = 0; k < 19; ++k) f[k] = fin[k * NNN + idx];
+        }
+        if (!EXPLICIT && lift && idx_ok) {
             const T dp = dm[idx], dux = dm[NNN + idx], duy = dm[2 * NNN + idx], duz = dm[3 * NNN + idx];
 #pragma unroll
             for (int k = 0; k < 19; ++k)
@@ -159,7 +164,8 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 512) k_sweep3(Sweep3Arg
         if (EXPLICIT) {
             p = rho; ux = jx; uy = jy; uz = jz;
         } else {
-            const T h0 = hh[idx], h1 = hh[NNN + idx], h2 = hh[2 * NNN + idx], h3 = hh[3 * NNN + idx];
+            const size_t hi_ = idx_ok ? idx : 0;
+            const T h0 = hh[hi_], h1 = hh[NNN + hi_], h2 = hh[2 * NNN + hi_], h3 = hh[3 * NNN + hi_];
             // m = P f + (h - a P f) / (2 (1 + a/2)): the rounded 1/(1 + a/2) scales only the O(a) term
             const T hinv = T(0.5) * inv;
             p = rho + (h0 - a * rho) * hinv;
@@ -186,19 +192,20 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 512) k_sweep3(Sweep3Arg
         T* sC = sC0 + (size_t)(j & 1) * 16 * tyb * 32;
 #pragma unroll
         for (int k = 0; k < 19; ++k)
-            if (L::cx(k) != 0 || L::cy(k) != 0) sC[(shift_slot(k) * tyb + ty) * 32 + tx] = C[k];
+            if ((L::cx(k) != 0 || L::cy(k) != 0) && MSC_INB((shift_slot(k) * tyb + ty) * 32 + tx, 16 * tyb * 32, 4))
+                sC[(shift_slot(k) * tyb + ty) * 32 + tx] = C[k];
         __syncthreads();
         if (out_site) {
 #pragma unroll
             for (int k = 0; k < 19; ++k)
-                if (L::cx(k) != 0 || L::cy(k) != 0)
+                if ((L::cx(k) != 0 || L::cy(k) != 0) && MSC_INB(ty - L::cy(k), tyb, 5) && MSC_INB(tx - L::cx(k), 32, 5))
                     C[k] = sC[(shift_slot(k) * tyb + (ty - L::cy(k))) * 32 + (tx - L::cx(k))];
         }
         // plane j-1 receives the c_z = -1 directions and is complete
 #pragma unroll
         for (int k = 0; k < 19; ++k)
             if (L::cz(k) == -1) Ar[k] = C[k];
-        if (j - 1 >= z0 && out_site) {
+        if (j - 1 >= z0 && out_site && MSC_INB((size_t)((j - 1) & m) * n * n + col, NNN, 6)) {
             const size_t oidx = (size_t)((j - 1) & m) * n * n + col;
 #pragma unroll
             for (int k = 0; k < 19; ++k) fout[k * NNN + oidx] = Ar[k];
@@ -273,10 +280,7 @@ template <typename T>
 int set_sweep3_smem_limits(int n) {
     const Sweep3Geom g = sweep3_geometry(n, sizeof(T));
     const int bytes = (int)g.smem;
-    if (cudaFuncSetAttribute(k_sweep3<T, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) ||
-        cudaFuncSetAttribute(k_sweep3<T, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) ||
-        cudaFuncSetAttribute(k_sweep3<T, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))
-        return 1;
+    if (cudaFuncSetAttribute(k_sweep3<T, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) return 1;
     return 0;
 }
 

@@ -12,8 +12,6 @@
 // translation unit.
 #pragma once
 
-#include <mutex>
-
 #include "common.cuh"
 #include "sweep2d.cuh"
 
@@ -27,23 +25,24 @@ constexpr size_t kNoAllocBytes = 256 + (size_t)kNoAllocMaxBlocks * sizeof(double
 
 static __device__ __align__(256) unsigned char g_sweep_scratch[kNoAllocBytes];
 
-constexpr int kNoAllocMaxDevices = 64;
+// every D2Q9 lattice that the entry point accepts (n = 8 .. 4096, powers of two) launches at most
+// kNoAllocMaxBlocks sweep blocks: checked at compile time against the sweep's own geometry rule
+constexpr bool noalloc_covers_all_lattices() {
+    for (int n = 8; n <= 4096; n *= 2)
+        if (sweep2_geometry(n).blocks > kNoAllocMaxBlocks) return false;
+    return true;
+}
+static_assert(noalloc_covers_all_lattices(), "the static sweep scratch is too small for some lattice");
 
-// Device address of g_sweep_scratch for each device, looked up once per device with that device
-// current.  In host code the symbol itself is only a host-side stand-in; kernels must be given the
-// address returned by cudaGetSymbolAddress.
+// Device address of g_sweep_scratch on the current device.  In host code the symbol itself is only
+// a host-side stand-in; kernels must be given the address that cudaGetSymbolAddress returns for the
+// current device.  The lookup is repeated on every call (a host-side table lookup after the first
+// call on a device has loaded the module), so the address stays right after a device reset, when
+// the module may be loaded again at another address.
 inline int noalloc_scratch(void** out) {
-    static std::mutex mu;
-    static void* addr[kNoAllocMaxDevices] = {};
-    int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) return MSC_ERR_CUDA;
-    std::lock_guard<std::mutex> lock(mu);
-    if (!addr[dev]) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_sweep_scratch) != cudaSuccess || !p) return MSC_ERR_CUDA;
-        addr[dev] = p;
-    }
-    *out = addr[dev];
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_sweep_scratch) != cudaSuccess || !p) return MSC_ERR_CUDA;
+    *out = p;
     return MSC_OK;
 }
 

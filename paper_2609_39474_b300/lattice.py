@@ -340,6 +340,47 @@ def sweep(dim: int, n: int, precision: str, a: float, f_in: torch.Tensor, h: tor
     return f_out, pr, ssq
 
 
+def sweep_hpair(n: int, precision: str, a: float, f_in: torch.Tensor, h: torch.Tensor, dm: torch.Tensor = None,
+                scratch: StageScratch = None, stream=None):
+    """The D2Q9 march's sweep through msc_sweep_hpair: h of shape (2, 3, n, n) (high, low parts) for
+    binary32 storage, (3, n, n) for FP64; returns (f_out, P r, sum r^2 as a device double)."""
+    dt, ft = storage_dtype(precision), field_dtype(precision)
+    hshape = (3, n, n) if precision == "fp64" else (2, 3, n, n)
+    if tuple(h.shape) != hshape:
+        raise ValueError(f"h must have shape {hshape}")
+    for t, want in ((f_in, dt), (h, ft)) + (((dm, ft),) if dm is not None else ()):
+        if t.dtype != want or not t.is_cuda or not t.is_contiguous():
+            raise ValueError("stage inputs must be contiguous device tensors of the storage / field type")
+    scratch = scratch or StageScratch(2, n, precision, f_in.device)
+    f_out = torch.empty_like(f_in)
+    pr = torch.empty((3, n, n), dtype=ft, device=f_in.device)
+    ssq = torch.empty((), dtype=torch.float64, device=f_in.device)
+    L.check(L.lib.msc_sweep_hpair(n, precision_code(precision), float(a), _ptr(f_in),
+                                  _ptr(dm) if dm is not None else None, _ptr(h), _ptr(f_out), _ptr(pr), _ptr(ssq),
+                                  _ptr(scratch.buf), scratch.nbytes, _stream(stream)), "msc_sweep_hpair")
+    return f_out, pr, ssq
+
+
+def sweep_d3q19_pf(n: int, precision: str, a: float, f_in: torch.Tensor, pf_in: torch.Tensor, h: torch.Tensor,
+                   dm: torch.Tensor = None, scratch: StageScratch = None, stream=None):
+    """The march's halo-free D3Q19 sweep through msc_sweep_d3q19_pf (pf_in = P f_in): returns
+    (f_out, P f_out, P r, sum r^2 as a device double)."""
+    dt = storage_dtype(precision)
+    for t in (f_in, pf_in, h) + ((dm,) if dm is not None else ()):
+        if t.dtype != dt or not t.is_cuda or not t.is_contiguous():
+            raise ValueError("stage inputs must be contiguous device tensors of the storage type")
+    scratch = scratch or StageScratch(3, n, precision, f_in.device)
+    f_out = torch.empty_like(f_in)
+    pf_out = torch.empty_like(pf_in)
+    pr = torch.empty((4, n, n, n), dtype=dt, device=f_in.device)
+    ssq = torch.empty((), dtype=torch.float64, device=f_in.device)
+    L.check(L.lib.msc_sweep_d3q19_pf(n, precision_code(precision), float(a), _ptr(f_in), _ptr(pf_in),
+                                     _ptr(dm) if dm is not None else None, _ptr(h), _ptr(f_out), _ptr(pf_out), _ptr(pr),
+                                     _ptr(ssq), _ptr(scratch.buf), scratch.nbytes, _stream(stream)),
+            "msc_sweep_d3q19_pf")
+    return f_out, pf_out, pr, ssq
+
+
 def sweep_trt(n: int, precision: str, a: float, omega_p: float, omega_m: float, f_in: torch.Tensor, h: torch.Tensor,
               dm: torch.Tensor = None, scratch: StageScratch = None, stream=None):
     """One D2Q9 sweep with the general TRT collision through msc_sweep_trt: (f_out, P r, sum r^2)."""

@@ -1,3 +1,5 @@
+import ctypes
+import json
 import os
 import sys
 
@@ -16,3 +18,16 @@ def pytest_configure(config):
 @pytest.fixture(scope="session")
 def repo_root():
     return ROOT
+
+
+def pytest_sessionfinish(session, exitstatus):
+    """Under the bounds-checked library (MSC_LIB_VARIANT=check) write the library's index-check
+    report to the file MSC_BOUNDS_REPORT names (read by test_gpu_bounds_check.py)."""
+    path = os.environ.get("MSC_BOUNDS_REPORT")
+    mod = sys.modules.get("paper_2609_39474_b300._lib")
+    if not path or os.environ.get("MSC_LIB_VARIANT") != "check" or mod is None:
+        return
+    count, first = ctypes.c_ulonglong(), ctypes.c_ulonglong()
+    rc = mod.lib.msc_bounds_check_report(ctypes.byref(count), ctypes.byref(first), 0)
+    with open(path, "w") as fh:
+        json.dump({"rc": rc, "count": count.value, "first": first.value, "lib": mod.LIB_PATH}, fh)

@@ -222,3 +222,57 @@ def test_shadow_solve_at_the_largest_sizes_single_modes(dim, n, precision):
         ref = np.stack([np.real(sol[c] * z) for c in range(dim + 1)])
         del z
         assert rel_l2(dm, ref) < tol
+
+
+def _pair(h64):
+    """Binary32 pair (hi, lo) of an FP64 field: hi = RN(h), lo = RN(h - hi); hi + lo is exact in FP64."""
+    hi = h64.astype(np.float32)
+    lo = (h64 - hi.astype(np.float64)).astype(np.float32)
+    return hi, lo
+
+
+@pytest.mark.parametrize("n,lift", [(8, True), (64, False), (256, True), (1024, True)])
+def test_sweep_hpair_matches_oracle(n, lift):
+    # the FP32 march's sweep (history term as a binary32 pair) against the oracle fed h = hi + lo
+    PL = _lib()
+    lat = lattice_for_dim(2)
+    f = random_populations(9, (n, n), seed=31, scale=1e-3).astype(np.float32)
+    h64 = random_moments(2, (n, n), seed=32, scale=1e-4)
+    dm = random_moments(2, (n, n), seed=33, scale=1e-4).astype(np.float32) if lift else None
+    hi, lo = _pair(h64)
+    a = 0.05
+    f_out, pr, ss = PL.sweep_hpair(n, "fp32", a, dev(f, torch.float32), dev(np.stack([hi, lo]), torch.float32),
+                                   dev(dm, torch.float32) if lift else None)
+    trial = f.astype(np.float64) + (OK.linear_lift(lat, dm.astype(np.float64)) if lift else 0.0)
+    f_T = OSW.sweep(lat, trial, a, hi.astype(np.float64) + lo.astype(np.float64))
+    r, _ = OSW.residual(f_T, trial)
+    assert rel_l2(host(f_out), f_T) < TOL["fp32"]["f"]
+    assert rel_l2(host(pr), OK.moments(lat, r)) < TOL["fp32"]["pr"]
+    assert abs(float(ss.item()) / float(np.sum(r * r)) - 1) < TOL["fp32"]["ss"]
+
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("n,lift", [(8, True), (16, False), (32, True), (64, True)])
+def test_sweep_d3q19_halo_free_matches_oracle(n, lift, precision):
+    # the march's D3Q19 sweep (moments of the input given, outputs pulled from the neighbours' collision
+    # inputs) against the oracle's sweep, and its P f_out against the oracle's moments of f_T
+    PL = _lib()
+    lat = lattice_for_dim(3)
+    T = PL.storage_dtype(precision)
+    f = random_populations(19, (n, n, n), seed=41, scale=1e-3)
+    h = random_moments(3, (n, n, n), seed=42, scale=1e-4)
+    dm = random_moments(3, (n, n, n), seed=43, scale=1e-4) if lift else None
+    f_s, h_s = dev(f, T), dev(h, T)
+    dm_s = dev(dm, T) if lift else None
+    pf_s = dev(OK.moments(lat, host(f_s)), T)
+    a = 0.05
+    f_out, pf_out, pr, ss = PL.sweep_d3q19_pf(n, precision, a, f_s, pf_s, h_s, dm_s)
+    trial = host(f_s) + (OK.linear_lift(lat, host(dm_s)) if lift else 0.0)
+    f_T = OSW.sweep(lat, trial, a, host(h_s))
+    r, _ = OSW.residual(f_T, trial)
+    tol = TOL[precision]
+    assert rel_l2(host(f_out), f_T) < tol["f"]
+    assert rel_l2(host(pr), OK.moments(lat, r)) < tol["pr"]
+    assert rel_l2(host(pf_out), OK.moments(lat, f_T)) < tol["pr"]
+    assert abs(float(ss.item()) / float(np.sum(r * r)) - 1) < tol["ss"]

@@ -53,8 +53,11 @@ def test_noalloc_sweep_matches_allocating_sweep_twice(n, lift, precision):
         assert abs(out_ss.item() / ref_ss.item() - 1) < tol["ss"]
 
 
-def test_noalloc_rejects_lattices_beyond_its_static_scratch():
+def test_noalloc_argument_validation():
+    # sizes and storage types outside the documented limits are rejected before any launch (the
+    # bound of the static scratch itself is a compile-time check in the library)
     from paper_2609_39474_b300 import _lib as L
-    rc = L.lib.msc_sweep_d2q9_noalloc(8192, L.MSC_FP32, 0.01, ctypes.c_void_p(16), None, ctypes.c_void_p(16),
-                                      ctypes.c_void_p(32), ctypes.c_void_p(64), ctypes.c_void_p(128), None)
-    assert rc == L.MSC_ERR_ARG
+    p = [ctypes.c_void_p(16), None, ctypes.c_void_p(16), ctypes.c_void_p(32), ctypes.c_void_p(64),
+         ctypes.c_void_p(128), None]
+    for n, prec in ((8192, L.MSC_FP32), (4096, L.MSC_FP64), (100, L.MSC_FP32), (4, L.MSC_FP64), (64, L.MSC_FP16)):
+        assert L.lib.msc_sweep_d2q9_noalloc(n, prec, 0.01, *p) == L.MSC_ERR_ARG, (n, prec)

@@ -42,9 +42,9 @@ NU = 1.0 / 6.0
 S_LIST = [4, 8, 16, 32, 64, 128, 256, 512, 1024, 2048, 4096]
 EPS_LIST = [1e-6, 1e-8, 1e-10]
 KMAX = 300
-# candidate the reference arm uses: the one the GPU candidate search times at N = 1024 (at this size no
-# searched FP32-storage candidate reaches the matched gate; this is the most accurate one) and at N = 256
-DEFAULT_CANDIDATE = {1024: (512, 1e-10), 256: (256, 1e-6)}
+# candidate the reference arm (and the single-phase profiling aids) use: the fastest matched-gate candidate
+# of the GPU candidate search at N = 1024 and at N = 256
+DEFAULT_CANDIDATE = {1024: (1024, 1e-8), 256: (256, 1e-6)}
 # the march's D2Q9 sweep: f in/out, h as a binary32 pair, lifted dm, P r
 SWEEP_BYTES_PER_SITE_FP32 = 2 * 9 * 4 + 2 * 3 * 4 + 3 * 4 + 3 * 4
 SWEEP_BYTES_PER_SITE_FP16 = 2 * 9 * 2 + 2 * 3 * 4 + 3 * 4 + 3 * 4  # binary16 f in/out, FP32 h pair, dm, P r

@@ -11,8 +11,8 @@
 // and a full collision.  The streamed output at x is pulled, f_T,k(x) = C_k(x - c_k), from the K of
 // the 18 neighbours.
 //
-// Design: a block owns a 32 x 8 tile of (x, y) columns, one thread per output column, and marches
-// along z.  For every plane it computes K on the tile plus a one-site ring (34 x 10 sites, the ring
+// Design: a block owns a 32 x 4 tile of (x, y) columns, one thread per output column, and marches
+// along z.  For every plane it computes K on the tile plus a one-site ring (34 x 6 sites, the ring
 // costing moment loads only) into shared memory, in four rotating plane buffers so that one block
 // barrier per plane separates the writers of plane z+1 from the readers of planes z-1, z, z+1.  A
 // thread loads the 19 populations of its own site (coalesced, no halo), pulls its 19 outputs,
@@ -24,10 +24,14 @@
 
 namespace msc {
 
-constexpr int kP3TX = 32, kP3TY = 8;                        // output tile (x, y)
+// 32 x 4 output tiles, eight 128-thread blocks (64 registers) per SM: the occupancy that hides the
+// latency of the per-plane ring loads (A/B at N = 128 FP32: 32 x 8 tiles at three blocks per SM
+// 128 us, at four 114 us, 32 x 4 at eight 112 us; 32 x 16 tiles, longer plane runs, a next-plane
+// register prefetch and a vectorised shared-memory layout were all slower)
+constexpr int kP3TX = 32, kP3TY = 4;                        // output tile (x, y)
 constexpr int kP3RX = kP3TX + 2, kP3RY = kP3TY + 2;         // tile plus ring
-constexpr int kP3Ring = kP3RX * kP3RY;                      // 340 sites per plane
-constexpr int kP3Threads = kP3TX * kP3TY;                   // 256
+constexpr int kP3Ring = kP3RX * kP3RY;                      // 204 sites per plane
+constexpr int kP3Threads = kP3TX * kP3TY;                   // 128
 constexpr int kP3K = 7;                                     // A0, ux, uy, uz, sx, sy, sz
 constexpr int kP3Bufs = 4;
 
@@ -86,7 +90,7 @@ struct Sweep3PArgs {
     int cond;
 };
 
-// K of the ring sites of plane zz (periodic index) into buffer b: threads take ring sites t and t + 256
+// K of the ring sites of plane zz (periodic index) into buffer b: thread t takes ring sites t, t + 128, ...
 template <typename T, bool HPAIR>
 __device__ __forceinline__ void p3_ring_plane(T* __restrict__ kb, const T* __restrict__ pfin,
                                               const T* __restrict__ dm, const T* __restrict__ hh, int lift, T a,
@@ -96,7 +100,7 @@ __device__ __forceinline__ void p3_ring_plane(T* __restrict__ kb, const T* __res
     const size_t zoff = (size_t)(zz & m) * n * n;
     const T hinv = T(0.5) * inv;
 #pragma unroll
-    for (int rep = 0; rep < 2; ++rep) {
+    for (int rep = 0; rep < (kP3Ring + kP3Threads - 1) / kP3Threads; ++rep) {
         const int r = threadIdx.x + rep * kP3Threads;
         if (r >= kP3Ring) break;
         const int rx = r % kP3RX, ry = r / kP3RX;
@@ -130,7 +134,7 @@ __device__ __forceinline__ void p3_ring_plane(T* __restrict__ kb, const T* __res
 }
 
 template <typename T, bool GRAPH, bool HPAIR = GRAPH && std::is_same<T, float>::value>
-__global__ void __launch_bounds__(kP3Threads, sizeof(T) == 4 ? 3 : 2) k_sweep3p(Sweep3PArgs<T> A) {
+__global__ void __launch_bounds__(kP3Threads, sizeof(T) == 4 ? 8 : 2) k_sweep3p(Sweep3PArgs<T> A) {
     using L = D3Q19;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* K0 = reinterpret_cast<T*>(smem_raw);  // [kP3Bufs][kP3K][kP3Ring]

@@ -237,8 +237,12 @@ int msc_sweep(int dim, int n, int precision, double a, const void* f_in, const v
    from pf_in, dm and h alone and the outputs are pulled, f_out,k(x) = C_k(x - c_k).  Same results as
    msc_sweep (dim 3) up to rounding, plus pf_out = P f_out for the next sweep.  f_in / f_out:
    19*n^3 elements of the storage type (FP64 or FP32); pf_in / pf_out: 4*n^3 elements, P f_in and
-   P f_out (density, then the three momentum components); dm (NULL: no lift), h, pr_out: 4*n^3.
-   f_in != f_out and pf_in != pf_out.  Scratch as msc_sweep (msc_stage_scratch_bytes(3, n, ...)).
+   P f_out (density, then the three momentum components); dm (NULL: no lift), pr_out: 4*n^3.  h as
+   the march holds it (Eq. bdf2): 4*n^3 doubles with FP64 storage; with FP32 storage a binary32 pair
+   of 2*4*n^3 floats, the four high parts followed by the four low parts, every difference h - a m
+   formed as fma(-a, m, hi) + lo (as msc_sweep_hpair does in 2D), so that this call runs the FP32
+   march's sweep kernel itself.  f_in != f_out and pf_in != pf_out.  Scratch as msc_sweep
+   (msc_stage_scratch_bytes(3, n, ...)).
    MSC_ERR_ARG for invalid sizes, pointers, scratch or FP16 storage. */
 int msc_sweep_d3q19_pf(int n, int precision, double a, const void* f_in, const void* pf_in, const void* dm,
                        const void* h, void* f_out, void* pf_out, void* pr_out, double* sumsq_out, void* scratch,

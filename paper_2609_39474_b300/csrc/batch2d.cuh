@@ -8,13 +8,17 @@
 //               row block) units of all active instances; the last unit of an instance reduces its
 //               residual norm in a fixed order and takes the acceptance decision (Algorithm 1)
 //   k_browfft   forward / inverse row transforms and k_bcolsolve the column FFT + FP64 solve, for
-//               the instances whose sweep asked for a shadow correction; a block finds its
-//               instance in a prefix table
+//               the instances whose sweep asked for a shadow correction
 //   k_bstep_end acceptance (m^{n+1}) and the next step's h and warm start, accepted instances only
-//   k_bfinish   history rotation per instance and the loop condition (any instance still active)
+//   k_bfinish   history rotation per instance, the loop condition (any instance still active) and
+//               the next round's work list
 // Instances therefore drift apart in phase (each converges in its own number of inner
 // iterations) without waiting for one another; an instance leaves the work list when its steps
-// are done or it stops with an error.
+// are done or it stops with an error.  The work list is compacted at every round (BAct): its
+// prefix tables cover the active instances only.  The sweep and the field kernels run grids of at
+// most one resident wave that stride over the list, so the tail rounds, in which a few small
+// instances are still iterating, run no work for the finished ones; the spectral kernels keep one
+// block per row (column) block of the whole batch, and those past the list's total leave at once.
 #pragma once
 
 #include "common.cuh"
@@ -61,6 +65,38 @@ struct BMap {
     int max_steps[kBatchMax];
 };
 
+// the round's work list: the active instances in batch order and prefix tables over their sweep
+// units, row blocks, column blocks and field blocks (written on the device by k_bsetup / k_bfinish)
+struct BAct {
+    int n_act;
+    int inst[kBatchMax];
+    int unit_off[kBatchMax + 1];
+    int row_off[kBatchMax + 1];
+    int col_off[kBatchMax + 1];
+    int fld_off[kBatchMax + 1];
+};
+
+// a prefix-table view of the work: entry j is instance ids[j] (ids null: instance j) and owns the
+// items [off[j], off[j + 1])
+struct BList {
+    const int* off;
+    const int* ids;
+    int n;
+    __device__ __forceinline__ int total() const { return __ldg(off + n); }
+};
+
+// MODE 0 (the march) walks the compacted list of active instances; the tuning and explicit modes
+// walk every instance of the batch
+template <int MODE>
+__device__ __forceinline__ BList blist(const BMap* __restrict__ M, const BAct* __restrict__ A, int which) {
+    if (MODE == 0) {
+        const int* o = which == 0 ? A->unit_off : which == 1 ? A->row_off : which == 2 ? A->col_off : A->fld_off;
+        return {o, A->inst, __ldg(&A->n_act)};
+    }
+    const int* o = which == 0 ? M->unit_off : which == 1 ? M->row_off : which == 2 ? M->col_off : M->fld_off;
+    return {o, nullptr, __ldg(&M->n_inst)};
+}
+
 // per-call step counts (kernel parameter)
 struct BSteps {
     int n[kBatchMax];
@@ -76,6 +112,14 @@ __device__ __forceinline__ int find_inst(const int* __restrict__ off, int n_inst
     return lo;
 }
 
+// item x of a list -> (entry j, instance, first item of the entry)
+__device__ __forceinline__ int list_entry(const BList& L, int x, int* inst, int* first) {
+    const int j = find_inst(L.off, L.n, x);
+    *inst = L.ids ? __ldg(L.ids + j) : j;
+    *first = __ldg(L.off + j);
+    return j;
+}
+
 __device__ __forceinline__ bool inst_active(const DevState* vs) {
     return vs->params_ok && vs->status == MSC_OK && vs->steps_target > 0;
 }
@@ -84,15 +128,17 @@ __device__ __forceinline__ bool inst_active(const DevState* vs) {
 // step `ex_node` of the unrolled explicit loop body.
 template <typename T, int MODE>
 __global__ void __launch_bounds__(kSweepWarps * 32) k_bsweep2(const BInst<T>* __restrict__ I,
-                                                             const BMap* __restrict__ M, int ex_node) {
+                                                             const BMap* __restrict__ M,
+                                                             const BAct* __restrict__ W, int ex_node) {
     const int lane = threadIdx.x & 31;
     const int nw = gridDim.x * kSweepWarps;
-    const int n_inst = M->n_inst;
-    const int total = __ldg(M->unit_off + n_inst);
+    const BList L = blist<MODE>(M, W, 0);
+    const int total = L.total();
     for (int u = blockIdx.x * kSweepWarps + (threadIdx.x >> 5); u < total; u += nw) {  // warp-uniform
-        const int i = find_inst(M->unit_off, n_inst, u);
+        int i, u0;
+        list_entry(L, u, &i, &u0);
         const BInst<T>& B = I[i];
-        const int lu = u - __ldg(M->unit_off + i);
+        const int lu = u - u0;
         const Sweep2Args<T>& A = B.sw;
         const T* fin;
         T* fout;
@@ -168,66 +214,89 @@ __device__ __forceinline__ bool spec_inst(const BInst<T>& B, Spec2Args<T>* A) {
     return inst_active(vs) && vs->lift;
 }
 
+// The spectral kernels take one row (column) block of the list per thread block, over a grid of
+// the whole batch's blocks; the blocks past the list's total leave at once.  (A grid-stride loop over
+// the items would launch fewer blocks in the tail rounds, but a transform inside any loop needs
+// twice the registers, 190-255 per thread, and the column solve spills.)  Whether an instance takes
+// the correction is read from its state.
 template <typename T, bool INV, int MODE>
-__global__ void __launch_bounds__(kFftThreads) k_browfft(const BInst<T>* __restrict__ I, const BMap* __restrict__ M) {
-    const int i = find_inst(M->row_off, M->n_inst, blockIdx.x);
+__global__ void __launch_bounds__(kFftThreads) k_browfft(const BInst<T>* __restrict__ I, const BMap* __restrict__ M,
+                                                         const BAct* __restrict__ W) {
+    const BList L = blist<MODE>(M, W, 1);
+    const int x = blockIdx.x;
+    if (x >= L.total()) return;
+    int i, x0;
+    list_entry(L, x, &i, &x0);
     Spec2Args<T> A;
     if (!spec_inst<T, MODE>(I[i], &A)) return;
-    const int bid = blockIdx.x - __ldg(M->row_off + i);
-    if (INV) rowfft_inv_block<T>(A, bid);
-    else rowfft_fwd_block<T>(A, bid);
+    if (INV) rowfft_inv_block<T>(A, x - x0);
+    else rowfft_fwd_block<T>(A, x - x0);
 }
 
 template <typename T, int MODE>
 __global__ void __launch_bounds__(sizeof(T) == 8 ? 384 : 768) k_bcolsolve(const BInst<T>* __restrict__ I,
-                                                                          const BMap* __restrict__ M) {
-    const int i = find_inst(M->col_off, M->n_inst, blockIdx.x);
+                                                                          const BMap* __restrict__ M,
+                                                                          const BAct* __restrict__ W) {
+    const BList L = blist<MODE>(M, W, 2);
+    const int x = blockIdx.x;
+    if (x >= L.total()) return;
+    int i, x0;
+    list_entry(L, x, &i, &x0);
     Spec2Args<T> A;
     if (!spec_inst<T, MODE>(I[i], &A)) return;
-    colsolve_block<T>(A, blockIdx.x - __ldg(M->col_off + i), __ldg(M->col_g + i));
+    colsolve_block<T>(A, x - x0, __ldg(M->col_g + i));
 }
 
-// field kernels: instance i owns blocks [fld_off[i], fld_off[i+1]) of a grid-stride loop
-template <typename T>
-__device__ __forceinline__ void fld_range(const BMap* __restrict__ M, int* inst, size_t* i0, size_t* istride) {
-    const int i = find_inst(M->fld_off, M->n_inst, blockIdx.x);
-    const int b0 = __ldg(M->fld_off + i), nb = __ldg(M->fld_off + i + 1) - b0;
-    *inst = i;
-    *i0 = (size_t)(blockIdx.x - b0) * blockDim.x + threadIdx.x;
+// field kernels: list entry j owns the field blocks [off[j], off[j + 1]), which cover its
+// instance's sites with a grid-stride loop; item x -> instance, first site and stride
+__device__ __forceinline__ int fld_item(const BList& L, int x, size_t* i0, size_t* istride) {
+    int i, b0;
+    const int j = list_entry(L, x, &i, &b0);
+    const int nb = __ldg(L.off + j + 1) - b0;
+    *i0 = (size_t)(x - b0) * blockDim.x + threadIdx.x;
     *istride = (size_t)nb * blockDim.x;
+    return i;
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kFieldThreads) k_bstep_begin(const BInst<T>* __restrict__ I,
-                                                               const BMap* __restrict__ M) {
-    int i;
-    size_t i0, is;
-    fld_range<T>(M, &i, &i0, &is);
-    const BInst<T>& B = I[i];
-    if (!inst_active(B.st)) return;
-    step_begin_range<D2Q9, T>(B.st, B.fbase, B.fstride, B.mbuf, B.h, B.sites, i0, is);
+                                                               const BMap* __restrict__ M,
+                                                               const BAct* __restrict__ W) {
+    const BList L = blist<0>(M, W, 3);
+    const int total = L.total();
+    for (int x = blockIdx.x; x < total; x += gridDim.x) {
+        size_t i0, is;
+        const BInst<T>& B = I[fld_item(L, x, &i0, &is)];
+        if (inst_active(B.st)) step_begin_range<D2Q9, T>(B.st, B.fbase, B.fstride, B.mbuf, B.h, B.sites, i0, is);
+    }
 }
 
 template <typename T, bool FORCE>
 __global__ void __launch_bounds__(kFieldThreads) k_bstep_end(const BInst<T>* __restrict__ I,
-                                                             const BMap* __restrict__ M) {
-    int i;
-    size_t i0, is;
-    fld_range<T>(M, &i, &i0, &is);
-    const BInst<T>& B = I[i];
-    step_end_range<D2Q9, T, T, FORCE>(B.st, B.fbase, B.fstride, B.mbuf, B.h, B.sites, i0, is);  // accepted only
+                                                             const BMap* __restrict__ M,
+                                                             const BAct* __restrict__ W) {
+    const BList L = blist<0>(M, W, 3);
+    const int total = L.total();
+    for (int x = blockIdx.x; x < total; x += gridDim.x) {
+        size_t i0, is;
+        const BInst<T>& B = I[fld_item(L, x, &i0, &is)];
+        step_end_range<D2Q9, T, T, FORCE>(B.st, B.fbase, B.fstride, B.mbuf, B.h, B.sites, i0, is);  // accepted only
+    }
 }
 
 // m^n = P f^n after a batched explicit march, for the instances that took steps
 template <typename T>
 __global__ void __launch_bounds__(kFieldThreads) k_bmoments_state(const BInst<T>* __restrict__ I,
                                                                   const BMap* __restrict__ M, BSteps steps) {
-    int i;
-    size_t i0, is;
-    fld_range<T>(M, &i, &i0, &is);
-    if (steps.n[i] <= 0) return;
-    const BInst<T>& B = I[i];
-    moments_state_range<D2Q9, T>(B.st, B.fbase, B.fstride, B.mbuf, B.sites, i0, is);
+    const BList L = blist<1>(M, nullptr, 3);
+    const int total = L.total();
+    for (int x = blockIdx.x; x < total; x += gridDim.x) {
+        size_t i0, is;
+        const int i = fld_item(L, x, &i0, &is);
+        if (steps.n[i] <= 0) continue;
+        const BInst<T>& B = I[i];
+        moments_state_range<D2Q9, T>(B.st, B.fbase, B.fstride, B.mbuf, B.sites, i0, is);
+    }
 }
 
 // ---- control kernels: one thread per instance, one block ---------------------------------------
@@ -237,8 +306,60 @@ __global__ void k_btargets(const BMap* __restrict__ M, BSteps steps) {
     if (i < M->n_inst) set_target(M->st[i], steps.n[i]);
 }
 
-// first step of every instance that runs, and the loop condition
-__global__ void k_bsetup(const BMap* __restrict__ M, cudaGraphConditionalHandle h_round) {
+// Compact the instances whose thread passes on = true into the work list W, in batch order.  One
+// block of kBatchMax threads, thread i = instance i: a block-wide inclusive scan (two warps) of
+// (on, units, row blocks, column blocks, field blocks); an active instance writes its entry at its
+// exclusive prefix, the last thread the totals.  Returns whether any instance is on.
+__device__ inline bool build_work_list(const BMap* __restrict__ M, BAct* __restrict__ W, bool on) {
+    static_assert(kBatchMax == 64, "the scan below covers two warps");
+    __shared__ int s_tot[2][5];
+    const int i = threadIdx.x, lane = i & 31, w = i >> 5;
+    int v[5] = {0, 0, 0, 0, 0};
+    if (on) {
+        v[0] = 1;
+        v[1] = M->unit_off[i + 1] - M->unit_off[i];
+        v[2] = M->row_off[i + 1] - M->row_off[i];
+        v[3] = M->col_off[i + 1] - M->col_off[i];
+        v[4] = M->fld_off[i + 1] - M->fld_off[i];
+    }
+    int inc[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        int x = v[k];
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, d);
+            if (lane >= d) x += y;
+        }
+        inc[k] = x;
+        if (lane == 31) s_tot[w][k] = x;
+    }
+    __syncthreads();
+    if (w == 1) {
+#pragma unroll
+        for (int k = 0; k < 5; ++k) inc[k] += s_tot[0][k];
+    }
+    if (on) {
+        const int j = inc[0] - 1;
+        W->inst[j] = i;
+        W->unit_off[j] = inc[1] - v[1];
+        W->row_off[j] = inc[2] - v[2];
+        W->col_off[j] = inc[3] - v[3];
+        W->fld_off[j] = inc[4] - v[4];
+    }
+    if (i == kBatchMax - 1) {
+        const int n = inc[0];
+        W->n_act = n;
+        W->unit_off[n] = inc[1];
+        W->row_off[n] = inc[2];
+        W->col_off[n] = inc[3];
+        W->fld_off[n] = inc[4];
+    }
+    return s_tot[0][0] + s_tot[1][0] > 0;
+}
+
+// first step of every instance that runs, the first round's work list and the loop condition
+__global__ void k_bsetup(const BMap* __restrict__ M, BAct* __restrict__ W, cudaGraphConditionalHandle h_round) {
     const int i = threadIdx.x;
     bool go = false;
     if (i < M->n_inst) {
@@ -248,11 +369,11 @@ __global__ void k_bsetup(const BMap* __restrict__ M, cudaGraphConditionalHandle 
             go = true;
         }
     }
-    go = __syncthreads_or(go);
+    go = build_work_list(M, W, go);
     if (threadIdx.x == 0) cudaGraphSetConditional(h_round, go ? 1u : 0u);
 }
 
-__global__ void k_bfinish(const BMap* __restrict__ M, cudaGraphConditionalHandle h_round) {
+__global__ void k_bfinish(const BMap* __restrict__ M, BAct* __restrict__ W, cudaGraphConditionalHandle h_round) {
     const int i = threadIdx.x;
     bool active = false;
     if (i < M->n_inst) {
@@ -261,9 +382,9 @@ __global__ void k_bfinish(const BMap* __restrict__ M, cudaGraphConditionalHandle
             step_finish(st, M->iters[i], M->max_steps[i]);
             st->accepted = 0;  // k_bstep_end of the next round must not see this step again
         }
-        active = st->params_ok && st->status == MSC_OK && st->steps_target > 0;
+        active = inst_active(st);
     }
-    active = __syncthreads_or(active);
+    active = build_work_list(M, W, active);
     if (threadIdx.x == 0) cudaGraphSetConditional(h_round, active ? 1u : 0u);
 }
 

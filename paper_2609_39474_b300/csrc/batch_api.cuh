@@ -14,10 +14,12 @@ struct msc_batch {
     int cls[kBatchMax];       // batch index -> size class
     cudaStream_t stream;
     unsigned char* ws;
-    size_t off_inst, off_map, off_upart, off_ucount, off_tsum;
+    size_t off_inst, off_map, off_act, off_upart, off_ucount, off_tsum;
     msc_batch_tuning tun;
-    // launch geometry derived from the tiling
+    // launch geometry derived from the tiling; fld_grid: the field kernels' strided grid (at most one
+    // resident wave, and no more blocks than the whole batch has field blocks)
     int sweep_grid, row_blocks, row_threads, col_blocks, col_threads, fld_blocks;
+    int fld_grid;
     size_t row_smem, col_smem;
     BMap map;  // host copy of the uploaded prefix tables
     bool graph_force;  // the march graph's step end carries the body-force terms
@@ -56,7 +58,7 @@ bool batch_list_ok(msc_ctx* const* ctxs, int n_inst, int* n_classes) {
 }
 
 struct BatchOffsets {
-    size_t inst, map, upart, ucount, tsum, total;
+    size_t inst, map, act, upart, ucount, tsum, total;
 };
 
 BatchOffsets batch_offsets(msc_ctx* const* ctxs, int n_inst) {
@@ -71,6 +73,7 @@ BatchOffsets batch_offsets(msc_ctx* const* ctxs, int n_inst) {
     for (int i = 0; i < n_inst; ++i) units += max_units(ctxs[i]->desc.n);
     o.inst = take((size_t)n_inst * binst_bytes());
     o.map = take(sizeof(BMap));
+    o.act = take(sizeof(BAct));
     o.upart = take(units * sizeof(double));
     o.ucount = take((size_t)n_inst * 32);
     o.tsum = take((size_t)n_inst * sizeof(double));
@@ -200,6 +203,16 @@ int upload_batch(msc_batch* b, const int (*t_slots)[2] = nullptr) {
     CK(cudaFuncSetAttribute(k_browfft<T, true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rsm));
     CK(cudaFuncSetAttribute(k_bcolsolve<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm));
     CK(cudaFuncSetAttribute(k_bcolsolve<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm));
+    {  // the field kernels' strided grid: one resident wave (the march's rounds walk the compacted list)
+        int occ = 0, dev = 0, sms = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bstep_end<T, false>, kFieldThreads, 0) !=
+                cudaSuccess ||
+            cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return MSC_ERR_CUDA;
+        const int cap = (occ < 1 ? 1 : occ) * sms;
+        b->fld_grid = b->fld_blocks < cap ? b->fld_blocks : cap;
+    }
     CK(cudaMemcpyAsync(b->ws + b->off_inst, I, (size_t)b->n_inst * sizeof(BInst<T>), cudaMemcpyHostToDevice,
                        b->stream));
     CK(cudaMemcpyAsync(b->ws + b->off_map, &M, sizeof(BMap), cudaMemcpyHostToDevice, b->stream));
@@ -226,21 +239,22 @@ int build_batch_march_graph(msc_batch* b) {
     CK(cudaGraphCreate(&g, 0));
     const BInst<T>* I = reinterpret_cast<const BInst<T>*>(b->ws + b->off_inst);
     const BMap* M = reinterpret_cast<const BMap*>(b->ws + b->off_map);
+    BAct* W = reinterpret_cast<BAct*>(b->ws + b->off_act);
     int zero = 0;
     cudaGraphConditionalHandle h_round;
     CK(cudaGraphConditionalHandleCreate(&h_round, g, 0, 0));
-    void* a_setup[] = {&M, &h_round};
+    void* a_setup[] = {&M, &W, &h_round};
     cudaGraphNode_t setup = add_kernel(g, {}, (const void*)k_bsetup, dim3(1), dim3(kBatchMax), 0, a_setup, &err);
-    void* a_fld[] = {&I, &M};
-    cudaGraphNode_t begin = add_kernel(g, {setup}, (const void*)k_bstep_begin<T>, dim3(b->fld_blocks),
+    void* a_fld[] = {&I, &M, &W};
+    cudaGraphNode_t begin = add_kernel(g, {setup}, (const void*)k_bstep_begin<T>, dim3(b->fld_grid),
                                        dim3(kFieldThreads), 0, a_fld, &err);
     cudaGraph_t body;
     add_cond(g, {begin}, h_round, cudaGraphCondTypeWhile, &body, &err);
     if (err != cudaSuccess) { cudaGraphDestroy(g); return MSC_ERR_CUDA; }
-    void* a_sw[] = {&I, &M, &zero};
+    void* a_sw[] = {&I, &M, &W, &zero};
     cudaGraphNode_t sw = add_kernel(body, {}, (const void*)k_bsweep2<T, 0>, dim3(b->sweep_grid),
                                     dim3(kSweepWarps * 32), 0, a_sw, &err);
-    void* a_sp[] = {&I, &M};
+    void* a_sp[] = {&I, &M, &W};
     cudaGraphNode_t r1 = add_kernel(body, {sw}, (const void*)k_browfft<T, false, 0>, dim3(b->row_blocks),
                                     dim3(b->row_threads), b->row_smem, a_sp, &err);
     cudaGraphNode_t cs = add_kernel(body, {r1}, (const void*)k_bcolsolve<T, 0>, dim3(b->col_blocks),
@@ -248,9 +262,9 @@ int build_batch_march_graph(msc_batch* b) {
     cudaGraphNode_t r2 = add_kernel(body, {cs}, (const void*)k_browfft<T, true, 0>, dim3(b->row_blocks),
                                     dim3(b->row_threads), b->row_smem, a_sp, &err);
     const void* fn_end = b->graph_force ? (const void*)k_bstep_end<T, true> : (const void*)k_bstep_end<T, false>;
-    cudaGraphNode_t en = add_kernel(body, {r2}, fn_end, dim3(b->fld_blocks),
+    cudaGraphNode_t en = add_kernel(body, {r2}, fn_end, dim3(b->fld_grid),
                                     dim3(kFieldThreads), 0, a_fld, &err);
-    void* a_fin[] = {&M, &h_round};
+    void* a_fin[] = {&M, &W, &h_round};
     add_kernel(body, {en}, (const void*)k_bfinish, dim3(1), dim3(kBatchMax), 0, a_fin, &err);
     if (err != cudaSuccess) { cudaGraphDestroy(g); return MSC_ERR_CUDA; }
     cudaGraphExec_t x;
@@ -276,10 +290,11 @@ int build_batch_explicit_graph(msc_batch* b) {
     add_cond(g, {arm}, h_ex, cudaGraphCondTypeWhile, &body, &err);
     if (err != cudaSuccess) { cudaGraphDestroy(g); return MSC_ERR_CUDA; }
     int nodes[kBatchExUnroll];
+    const BAct* no_list = nullptr;  // the explicit march walks every instance
     cudaGraphNode_t prev = nullptr;
     for (int i = 0; i < kBatchExUnroll; ++i) {
         nodes[i] = i;
-        void* a_sw[] = {&I, &M, &nodes[i]};
+        void* a_sw[] = {&I, &M, &no_list, &nodes[i]};
         std::vector<cudaGraphNode_t> deps;
         if (prev) deps.push_back(prev);
         prev = add_kernel(body, deps, (const void*)k_bsweep2<T, 2>, dim3(b->sweep_grid), dim3(kSweepWarps * 32), 0,
@@ -320,12 +335,12 @@ float time_batch_kernel(msc_batch* b, BatchTimer& tm, int which, int reps) {
     for (int r = 0; r < reps + 1; ++r) {  // the first launch warms up
         if (cudaEventRecord(tm.e0, b->stream) != cudaSuccess) return -1.f;
         if (which == 0) {
-            k_bsweep2<T, 1><<<b->sweep_grid, kSweepWarps * 32, 0, b->stream>>>(I, M, 0);
+            k_bsweep2<T, 1><<<b->sweep_grid, kSweepWarps * 32, 0, b->stream>>>(I, M, nullptr, 0);
         } else if (which == 1) {
-            k_browfft<T, false, 1><<<b->row_blocks, b->row_threads, b->row_smem, b->stream>>>(I, M);
-            k_browfft<T, true, 1><<<b->row_blocks, b->row_threads, b->row_smem, b->stream>>>(I, M);
+            k_browfft<T, false, 1><<<b->row_blocks, b->row_threads, b->row_smem, b->stream>>>(I, M, nullptr);
+            k_browfft<T, true, 1><<<b->row_blocks, b->row_threads, b->row_smem, b->stream>>>(I, M, nullptr);
         } else {
-            k_bcolsolve<T, 1><<<b->col_blocks, b->col_threads, b->col_smem, b->stream>>>(I, M);
+            k_bcolsolve<T, 1><<<b->col_blocks, b->col_threads, b->col_smem, b->stream>>>(I, M, nullptr);
         }
         if (cudaGetLastError() != cudaSuccess) return -1.f;
         if (cudaEventRecord(tm.e1, b->stream) != cudaSuccess || cudaEventSynchronize(tm.e1) != cudaSuccess)
@@ -454,6 +469,7 @@ int msc_batch_create(msc_batch** out, msc_ctx* const* ctxs, int n_inst, void* ws
     b->ws = (unsigned char*)ws;
     b->off_inst = o.inst;
     b->off_map = o.map;
+    b->off_act = o.act;
     b->off_upart = o.upart;
     b->off_ucount = o.ucount;
     b->off_tsum = o.tsum;
@@ -555,10 +571,10 @@ int msc_batch_explicit_march(msc_batch* b, const int* n_steps) {
     k_bex_finish<<<1, kBatchMax, 0, b->stream>>>(M, s);
     CK(cudaGetLastError());
     if (b->precision == MSC_FP64)
-        k_bmoments_state<double><<<b->fld_blocks, kFieldThreads, 0, b->stream>>>(
+        k_bmoments_state<double><<<b->fld_grid, kFieldThreads, 0, b->stream>>>(
             reinterpret_cast<const BInst<double>*>(b->ws + b->off_inst), M, s);
     else
-        k_bmoments_state<float><<<b->fld_blocks, kFieldThreads, 0, b->stream>>>(
+        k_bmoments_state<float><<<b->fld_grid, kFieldThreads, 0, b->stream>>>(
             reinterpret_cast<const BInst<float>*>(b->ws + b->off_inst), M, s);
     CK(cudaGetLastError());
     return MSC_OK;

@@ -203,6 +203,7 @@ __device__ __forceinline__ void step_begin_range(const DevState* __restrict__ st
                                                  S* __restrict__ pfbase = nullptr, size_t pfstride = 0) {
     const DevState* vs = st;
     if (vs->prepared) return;  // formed by the previous step's k_step_end
+    if (!vs->params_ok || vs->steps_target <= 0 || vs->status != MSC_OK) return;  // no step runs
     const int q = vs->q;
     const double dt = vs->dt;
     const int nav = vs->n_avail < vs->warm_order ? vs->n_avail : vs->warm_order;
@@ -516,10 +517,6 @@ __device__ inline bool arm_state(DevState* st) {
     return st->steps_target > 0 && st->status == MSC_OK;
 }
 
-__global__ void k_arm(DevState* st, cudaGraphConditionalHandle h_step) {
-    cudaGraphSetConditional(h_step, arm_state(st) ? 1u : 0u);
-}
-
 __device__ inline bool slot_in_history(const DevState* st, int s) {
     for (int i = 0; i < st->n_avail; ++i)
         if (st->slot_fn[i] == s) return true;
@@ -590,10 +587,26 @@ __device__ inline unsigned int step_finish(DevState* st, int* iters_out, int max
     return go;
 }
 
+// the march graph's prologue: arm the step loop and set up its first step (k_step_begin follows)
+__global__ void k_arm_setup(DevState* st, cudaGraphConditionalHandle h_step) {
+    const bool go = arm_state(st);
+    if (go) step_setup(st);
+    cudaGraphSetConditional(h_step, go ? 1u : 0u);
+}
+
 __global__ void k_step_finish(DevState* st, int* iters_out, int max_steps,
                               cudaGraphConditionalHandle h_step, int cond) {
     const unsigned int go = step_finish(st, iters_out, max_steps);
     if (cond) cudaGraphSetConditional(h_step, go);
+}
+
+// the march graph's step end: the step loop's condition, and the inner loop of the next step
+// opened (the first step of a launch opens it through the handle's default value)
+__global__ void k_step_finish_graph(DevState* st, int* iters_out, int max_steps, cudaGraphConditionalHandle h_step,
+                                    cudaGraphConditionalHandle h_iter) {
+    const unsigned int go = step_finish(st, iters_out, max_steps);
+    cudaGraphSetConditional(h_step, go);
+    cudaGraphSetConditional(h_iter, 1u);
 }
 
 // m^n = P f^n of the accepted slot into both moment slots (after an explicit march)

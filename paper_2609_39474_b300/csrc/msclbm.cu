@@ -325,31 +325,33 @@ int build_march_graph(msc_ctx* c) {
     int max_steps = c->desc.max_steps;
     const int fgrid = grid_for(sites);
 
+    // prologue: arm the step loop, set up the first step and form its h and trial; every later
+    // step is set up by the previous step's k_step_finish_graph, its h and trial formed by k_step_end
     cudaGraphConditionalHandle h_step, h_iter, h_corr;
     CK(cudaGraphConditionalHandleCreate(&h_step, g, 0, 0));
     void* a_arm[] = {&st, &h_step};
-    cudaGraphNode_t arm = add_kernel(g, {}, (const void*)k_arm, dim3(1), dim3(1), 0, a_arm, &err);
-    cudaGraph_t body_step;
-    add_cond(g, {arm}, h_step, cudaGraphCondTypeWhile, &body_step, &err);
-    if (err != cudaSuccess) { cudaGraphDestroy(g); return MSC_ERR_CUDA; }
-
-    CK(cudaGraphConditionalHandleCreate(&h_iter, body_step, 0, 0));
-    int cond1 = 1;
-    void* a_setup[] = {&st, &h_iter, &cond1};
-    cudaGraphNode_t setup = add_kernel(body_step, {}, (const void*)k_step_setup, dim3(1), dim3(1), 0, a_setup, &err);
+    cudaGraphNode_t arm = add_kernel(g, {}, (const void*)k_arm_setup, dim3(1), dim3(1), 0, a_arm, &err);
     FS* pfbase = pf_base<FS>(c);
     size_t pfstride = c->lay.pfstride;
     void* a_begin[] = {&st, &fbase, (void*)&fstride, &mbuf, &h, &sites, &pfbase, &pfstride};
-    cudaGraphNode_t begin = add_kernel(body_step, {setup}, (const void*)k_step_begin<L, T, FS>, dim3(fgrid),
+    cudaGraphNode_t begin = add_kernel(g, {arm}, (const void*)k_step_begin<L, T, FS>, dim3(fgrid),
                                        dim3(kFieldThreads), 0, a_begin, &err);
+    cudaGraph_t body_step;
+    add_cond(g, {begin}, h_step, cudaGraphCondTypeWhile, &body_step, &err);
+    if (err != cudaSuccess) { cudaGraphDestroy(g); return MSC_ERR_CUDA; }
+
+    // one physical step: the inner loop (opened by the default value at launch, then by the
+    // previous step's k_step_finish_graph), acceptance with the next step's h and trial, then the
+    // history rotation and both loop conditions
+    CK(cudaGraphConditionalHandleCreate(&h_iter, body_step, 1u, cudaGraphCondAssignDefault));
     cudaGraph_t body_iter;
-    cudaGraphNode_t wit = add_cond(body_step, {begin}, h_iter, cudaGraphCondTypeWhile, &body_iter, &err);
+    cudaGraphNode_t wit = add_cond(body_step, {}, h_iter, cudaGraphCondTypeWhile, &body_iter, &err);
     if (err != cudaSuccess) { cudaGraphDestroy(g); return MSC_ERR_CUDA; }
     void* a_end[] = {&st, &fbase, (void*)&fstride, &mbuf, &h, &sites, &pfbase, &pfstride};
     cudaGraphNode_t end = add_kernel(body_step, {wit}, step_end_kernel<L, T, FS>(c), dim3(fgrid),
                                      dim3(kFieldThreads), 0, a_end, &err);
-    void* a_fin[] = {&st, &iters, &max_steps, &h_step, &cond1};
-    add_kernel(body_step, {end}, (const void*)k_step_finish, dim3(1), dim3(1), 0, a_fin, &err);
+    void* a_fin[] = {&st, &iters, &max_steps, &h_step, &h_iter};
+    add_kernel(body_step, {end}, (const void*)k_step_finish_graph, dim3(1), dim3(1), 0, a_fin, &err);
 
     CK(cudaGraphConditionalHandleCreate(&h_corr, body_iter, 0, 0));
     cudaGraphNode_t sw;
@@ -1145,7 +1147,8 @@ int msc_sweep_d3q19_pf(int n, int precision, double a, const void* f_in, const v
         A.partial = S.partial;
         A.counter = S.counter;
         A.n = n;
-        k_sweep3p<T, false><<<A.g.blocks, kP3Threads, A.g.smem, st>>>(A);
+        // the march's kernel: with binary32 storage h is the high / low pair the march holds
+        k_sweep3p<T, false, std::is_same<T, float>::value><<<A.g.blocks, kP3Threads, A.g.smem, st>>>(A);
         CK(cudaGetLastError());
         return MSC_OK;
     };

@@ -11,8 +11,8 @@
 // and a full collision.  The streamed output at x is pulled, f_T,k(x) = C_k(x - c_k), from the K of
 // the 18 neighbours.
 //
-// Design: a block owns a 32 x 4 tile of (x, y) columns, one thread per output column, and marches
-// along z.  For every plane it computes K on the tile plus a one-site ring (34 x 6 sites, the ring
+// Design: a block owns a 32 x 8 tile of (x, y) columns, one thread per output column, and marches
+// along z.  For every plane it computes K on the tile plus a one-site ring (34 x 10 sites, the ring
 // costing moment loads only) into shared memory, in four rotating plane buffers so that one block
 // barrier per plane separates the writers of plane z+1 from the readers of planes z-1, z, z+1.  A
 // thread loads the 19 populations of its own site (coalesced, no halo), pulls its 19 outputs,
@@ -24,14 +24,14 @@
 
 namespace msc {
 
-// 32 x 4 output tiles, eight 128-thread blocks (64 registers) per SM: the occupancy that hides the
-// latency of the per-plane ring loads (A/B at N = 128 FP32: 32 x 8 tiles at three blocks per SM
-// 128 us, at four 114 us, 32 x 4 at eight 112 us; 32 x 16 tiles, longer plane runs, a next-plane
-// register prefetch and a vectorised shared-memory layout were all slower)
-constexpr int kP3TX = 32, kP3TY = 4;                        // output tile (x, y)
+// 32 x 8 output tiles, four 256-thread blocks (64 registers) per SM.  A/B of the FP32 march's
+// kernel (binary32 history pair): 32 x 4 tiles at eight blocks per SM 0.65 / 0.68 of the measured
+// HBM bandwidth at N = 128 / 256, 32 x 8 at four 0.66 / 0.74, 32 x 16 at two 0.57 / 0.68 (the ring
+// costs moment loads per output site in the ratio 204 : 128, 340 : 256, 612 : 512).
+constexpr int kP3TX = 32, kP3TY = 8;                        // output tile (x, y)
 constexpr int kP3RX = kP3TX + 2, kP3RY = kP3TY + 2;         // tile plus ring
-constexpr int kP3Ring = kP3RX * kP3RY;                      // 204 sites per plane
-constexpr int kP3Threads = kP3TX * kP3TY;                   // 128
+constexpr int kP3Ring = kP3RX * kP3RY;                      // 340 sites per plane
+constexpr int kP3Threads = kP3TX * kP3TY;                   // 256
 constexpr int kP3K = 7;                                     // A0, ux, uy, uz, sx, sy, sz
 constexpr int kP3Bufs = 4;
 
@@ -40,12 +40,14 @@ struct Sweep3PGeom {
     size_t smem;
 };
 
+// A block marches one column (x, y tile) over hb planes, recomputing two ring planes at its start:
+// the longest run that still gives about four blocks per SM.  (Runs balanced to fill exactly one
+// resident wave, e.g. nine runs of 14-15 planes per column at N = 128, measured no faster at N = 128
+// and 11 % slower at N = 256 than this rule's 1.7 waves.)
 inline Sweep3PGeom sweep3p_geometry(int n, int elem) {
     Sweep3PGeom g;
     g.nsx = (n + kP3TX - 1) / kP3TX;
     g.nsy = (n + kP3TY - 1) / kP3TY;
-    // longest plane run (fewer ring planes recomputed at block ends) that still gives about four
-    // blocks per SM
     const int target_blocks = 4 * 148;
     int hb = 4;
     for (int c = 64; c >= 4; c >>= 1) {
@@ -90,7 +92,7 @@ struct Sweep3PArgs {
     int cond;
 };
 
-// K of the ring sites of plane zz (periodic index) into buffer b: thread t takes ring sites t, t + 128, ...
+// K of the ring sites of plane zz (periodic index) into buffer b: thread t takes ring sites t, t + 256, ...
 template <typename T, bool HPAIR>
 __device__ __forceinline__ void p3_ring_plane(T* __restrict__ kb, const T* __restrict__ pfin,
                                               const T* __restrict__ dm, const T* __restrict__ hh, int lift, T a,
@@ -134,7 +136,7 @@ __device__ __forceinline__ void p3_ring_plane(T* __restrict__ kb, const T* __res
 }
 
 template <typename T, bool GRAPH, bool HPAIR = GRAPH && std::is_same<T, float>::value>
-__global__ void __launch_bounds__(kP3Threads, sizeof(T) == 4 ? 8 : 2) k_sweep3p(Sweep3PArgs<T> A) {
+__global__ void __launch_bounds__(kP3Threads, sizeof(T) == 4 ? 4 : 1) k_sweep3p(Sweep3PArgs<T> A) {
     using L = D3Q19;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* K0 = reinterpret_cast<T*>(smem_raw);  // [kP3Bufs][kP3K][kP3Ring]
@@ -165,7 +167,7 @@ __global__ void __launch_bounds__(kP3Threads, sizeof(T) == 4 ? 8 : 2) k_sweep3p(
     const int sx = b % A.g.nsx;
     const int sy = (b / A.g.nsx) % A.g.nsy;
     const int zb = b / (A.g.nsx * A.g.nsy);
-    const int x0 = sx * kP3TX, y0 = sy * kP3TY, z0 = zb * A.g.hb;
+    const int x0 = sx * kP3TX, y0 = sy * kP3TY, z0 = zb * A.g.hb, z1 = z0 + A.g.hb;
     const int tx = threadIdx.x % kP3TX, ty = threadIdx.x / kP3TX;
     const bool out_site = (x0 + tx) < n && (y0 + ty) < n;
     const size_t col = (size_t)((y0 + ty) & m) * n + ((x0 + tx) & m);
@@ -176,7 +178,7 @@ __global__ void __launch_bounds__(kP3Threads, sizeof(T) == 4 ? 8 : 2) k_sweep3p(
     p3_ring_plane<T, HPAIR>(K0 + (size_t)(z0 & (kP3Bufs - 1)) * kP3K * kP3Ring, pfin, dm, hh, lift, a, inv, n, x0, y0,
                             z0);
     double ssq = 0.0;
-    for (int z = z0; z < z0 + A.g.hb; ++z) {
+    for (int z = z0; z < z1; ++z) {
         const size_t idx = (size_t)(z & m) * n * n + col;
         const bool idx_ok = MSC_INB(idx, NNN, 21);
         // this site's populations and lift, in flight while the next ring plane is computed
@@ -295,6 +297,8 @@ template <typename T>
 int set_sweep3p_smem_limits(int n) {
     const int bytes = (int)sweep3p_geometry(n, sizeof(T)).smem;
     if (cudaFuncSetAttribute(k_sweep3p<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) ||
+        cudaFuncSetAttribute(k_sweep3p<T, false, std::is_same<T, float>::value>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) ||
         cudaFuncSetAttribute(k_sweep3p<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes))
         return 1;
     return 0;

@@ -364,11 +364,14 @@ def sweep_hpair(n: int, precision: str, a: float, f_in: torch.Tensor, h: torch.T
 def sweep_d3q19_pf(n: int, precision: str, a: float, f_in: torch.Tensor, pf_in: torch.Tensor, h: torch.Tensor,
                    dm: torch.Tensor = None, scratch: StageScratch = None, stream=None):
     """The march's halo-free D3Q19 sweep through msc_sweep_d3q19_pf (pf_in = P f_in): returns
-    (f_out, P f_out, P r, sum r^2 as a device double)."""
+    (f_out, P f_out, P r, sum r^2 as a device double).  h: (4, n, n, n) for FP64 storage, the binary32
+    pair (2, 4, n, n, n) = (high parts, low parts) for FP32 storage."""
     dt = storage_dtype(precision)
     for t in (f_in, pf_in, h) + ((dm,) if dm is not None else ()):
         if t.dtype != dt or not t.is_cuda or not t.is_contiguous():
             raise ValueError("stage inputs must be contiguous device tensors of the storage type")
+    if h.numel() != (2 if precision == "fp32" else 1) * 4 * n ** 3:
+        raise ValueError("h: 4 n^3 values (FP64) or a binary32 pair of 2 x 4 n^3 values (FP32)")
     scratch = scratch or StageScratch(3, n, precision, f_in.device)
     f_out = torch.empty_like(f_in)
     pf_out = torch.empty_like(pf_in)

@@ -263,13 +263,20 @@ def test_sweep_d3q19_halo_free_matches_oracle(n, lift, precision):
     f = random_populations(19, (n, n, n), seed=41, scale=1e-3)
     h = random_moments(3, (n, n, n), seed=42, scale=1e-4)
     dm = random_moments(3, (n, n, n), seed=43, scale=1e-4) if lift else None
-    f_s, h_s = dev(f, T), dev(h, T)
+    f_s = dev(f, T)
+    if precision == "fp32":  # the FP32 march's history pair; the oracle sees h = hi + lo exactly
+        hi, lo = _pair(h)
+        h_s = dev(np.stack([hi, lo]), T)
+        h_o = hi.astype(np.float64) + lo.astype(np.float64)
+    else:
+        h_s = dev(h, T)
+        h_o = h
     dm_s = dev(dm, T) if lift else None
     pf_s = dev(OK.moments(lat, host(f_s)), T)
     a = 0.05
     f_out, pf_out, pr, ss = PL.sweep_d3q19_pf(n, precision, a, f_s, pf_s, h_s, dm_s)
     trial = host(f_s) + (OK.linear_lift(lat, host(dm_s)) if lift else 0.0)
-    f_T = OSW.sweep(lat, trial, a, host(h_s))
+    f_T = OSW.sweep(lat, trial, a, h_o)
     r, _ = OSW.residual(f_T, trial)
     tol = TOL[precision]
     assert rel_l2(host(f_out), f_T) < tol["f"]

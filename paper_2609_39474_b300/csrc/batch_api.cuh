@@ -104,7 +104,7 @@ void default_tuning(msc_batch* b) {
     msc_batch_tuning& t = b->tun;
     for (int c = 0; c < t.n_classes; ++c) {
         const int n = t.n[c];
-        t.sweep_rows[c] = sweep2_geometry(n).hb;
+        t.sweep_rows[c] = sweep2_geometry(n, 4).hb;  // the batch's unit tables assume >= 4 rows per unit
         t.fft_rows[c] = row_geometry(n, 3, n).P;
         t.col_lines[c] = 1;
     }

@@ -56,7 +56,10 @@ P* at(msc_ctx* c, size_t off) {
 }
 
 int sweep_blocks_for(int dim, int n, int precision) {
-    if (dim == 2) return sweep2_geometry(n).blocks;
+    if (dim == 2) {  // the march's sweep and the explicit step (no partials, sized for both)
+        const int b0 = sweep2_geometry(n).blocks, b1 = sweep2_geometry(n, kExplicitMinRows).blocks;
+        return b0 > b1 ? b0 : b1;
+    }
     return sweep3p_geometry(n, precision == MSC_FP64 ? 8 : 4).blocks;
 }
 
@@ -139,10 +142,10 @@ int grid_for(size_t sites) {
 // ---- typed helpers ------------------------------------------------------------------------------
 
 template <typename T, typename FS = T>
-Sweep2Args<T, FS> sweep2_args_graph(msc_ctx* c) {
+Sweep2Args<T, FS> sweep2_args_graph(msc_ctx* c, bool explicit_step = false) {
     Sweep2Args<T, FS> A;
     memset(&A, 0, sizeof(A));
-    const Sweep2Geom g = sweep2_geometry(c->desc.n);
+    const Sweep2Geom g = sweep2_geometry(c->desc.n, explicit_step ? kExplicitMinRows : kSweepMinRows);
     A.dm = at<T>(c, c->lay.dm);
     A.h = at<T>(c, c->lay.h);
     A.pr = at<T>(c, c->lay.pr);
@@ -406,13 +409,14 @@ int build_explicit_graph(msc_ctx* c) {
         std::vector<cudaGraphNode_t> deps;
         if (prev) deps.push_back(prev);
         if (L::D == 2) {
-            Sweep2Args<T, FS> A = sweep2_args_graph<T, FS>(c);
+            Sweep2Args<T, FS> A = sweep2_args_graph<T, FS>(c, true);
             A.ex_dir = i & 1;
             A.ex_count = i == kExplicitUnroll - 1;
             A.h_ex = h_ex;
             void* aa[] = {&A};
-            prev = add_kernel(body, deps, sweep2_kernel<T, FS, true, true>(c), dim3(sweep2_geometry(c->desc.n).blocks),
-                              dim3(kSweepWarps * 32), 0, aa, &err);
+            prev = add_kernel(body, deps, sweep2_kernel<T, FS, true, true>(c),
+                              dim3(sweep2_geometry(c->desc.n, kExplicitMinRows).blocks), dim3(kSweepWarps * 32), 0,
+                              aa, &err);
         } else {
             Sweep3Args<T> A = sweep3_args_graph<T>(c);
             A.ex_dir = i & 1;
@@ -446,11 +450,12 @@ int run_explicit(msc_ctx* c, int n_steps) {
     if (blocks > 0) CK(cudaGraphLaunch(c->x_ex, c->stream));
     for (int i = 0; i < rem; ++i) {  // the remainder alternates a->b, b->a, ... as in the loop body
         if (L::D == 2) {
-            Sweep2Args<T, FS> A = sweep2_args_graph<T, FS>(c);
+            Sweep2Args<T, FS> A = sweep2_args_graph<T, FS>(c, true);
             A.ex_dir = i & 1;
             void* aa[] = {&A};
-            CK(cudaLaunchKernel(sweep2_kernel<T, FS, true, true>(c), dim3(sweep2_geometry(c->desc.n).blocks),
-                                dim3(kSweepWarps * 32), aa, 0, c->stream));
+            CK(cudaLaunchKernel(sweep2_kernel<T, FS, true, true>(c),
+                                dim3(sweep2_geometry(c->desc.n, kExplicitMinRows).blocks), dim3(kSweepWarps * 32), aa,
+                                0, c->stream));
         } else {
             Sweep3Args<T> A = sweep3_args_graph<T>(c);
             A.ex_dir = i & 1;

@@ -392,15 +392,22 @@ struct Sweep2Geom {
     int nstrips, hb, nrowblk, blocks;
 };
 
-constexpr Sweep2Geom sweep2_geometry(int n) {
+// Rows per warp unit: the largest row block (<= 64, dividing n) that still gives 12 warps per SM:
+// fewer halo rows, and one resident wave where 16 warps per SM would need 1.5 (N = 1024: 560 blocks
+// instead of 1120, the sweep 34 -> 29 us and the march 4.5 % faster; N = 2048: 105 -> 97 us).  Small
+// lattices never reach 12 warps per SM and take min_rows: 2 for the march's sweep, 1 for the explicit
+// LBM step, whose row chain is shorter (A/B at N = 128 / 256, FP32: march 7.73 / 16.38 ms with 4
+// rows, 7.44 / 16.27 with 2, 7.48 / 17.04 with 1; explicit step 3.99 / 4.06 us with 4 rows, 3.14 /
+// 3.50 with 2, 2.78 / 3.41 with 1; N >= 512 unchanged).
+constexpr int kSweepMinRows = 2;
+constexpr int kExplicitMinRows = 1;
+
+constexpr Sweep2Geom sweep2_geometry(int n, int min_rows = kSweepMinRows) {
     Sweep2Geom g{};
     g.nstrips = (n + kStripOut - 1) / kStripOut;
-    // largest row block (<= 64, dividing n) that still gives 12 warps per SM: fewer halo rows, and
-    // one resident wave where 16 warps per SM would need 1.5 (N = 1024: 560 blocks instead of 1120,
-    // the sweep 34 -> 29 us and the march 4.5 % faster; N = 2048: 105 -> 97 us)
     const int target_units = 148 * 12;
-    int hb = 4;
-    for (int c = 64; c >= 4; c >>= 1) {
+    int hb = min_rows;
+    for (int c = 64; c >= min_rows; c >>= 1) {
         if (c <= n && g.nstrips * (n / c) >= target_units) { hb = c; break; }
     }
     if (hb > n) hb = n;

@@ -340,10 +340,21 @@ def sweep(dim: int, n: int, precision: str, a: float, f_in: torch.Tensor, h: tor
     return f_out, pr, ssq
 
 
+def _outputs(out, shapes, device):
+    """Caller-given output tensors (checked against (shape, dtype) pairs), or new ones."""
+    if out is None:
+        return [torch.empty(sh, dtype=dt, device=device) for sh, dt in shapes]
+    if len(out) != len(shapes) or any(tuple(t.shape) != tuple(sh) or t.dtype != dt or not t.is_cuda or
+                                      not t.is_contiguous() for t, (sh, dt) in zip(out, shapes)):
+        raise ValueError("out: contiguous device tensors of shapes and dtypes " + str(shapes))
+    return list(out)
+
+
 def sweep_hpair(n: int, precision: str, a: float, f_in: torch.Tensor, h: torch.Tensor, dm: torch.Tensor = None,
-                scratch: StageScratch = None, stream=None):
+                scratch: StageScratch = None, stream=None, out=None):
     """The D2Q9 march's sweep through msc_sweep_hpair: h of shape (2, 3, n, n) (high, low parts) for
-    binary32 storage, (3, n, n) for FP64; returns (f_out, P r, sum r^2 as a device double)."""
+    binary32 storage, (3, n, n) for FP64; returns (f_out, P r, sum r^2 as a device double), written
+    into `out` = (f_out, P r, sum) when given (repeated calls then allocate nothing)."""
     dt, ft = storage_dtype(precision), field_dtype(precision)
     hshape = (3, n, n) if precision == "fp64" else (2, 3, n, n)
     if tuple(h.shape) != hshape:
@@ -352,9 +363,7 @@ def sweep_hpair(n: int, precision: str, a: float, f_in: torch.Tensor, h: torch.T
         if t.dtype != want or not t.is_cuda or not t.is_contiguous():
             raise ValueError("stage inputs must be contiguous device tensors of the storage / field type")
     scratch = scratch or StageScratch(2, n, precision, f_in.device)
-    f_out = torch.empty_like(f_in)
-    pr = torch.empty((3, n, n), dtype=ft, device=f_in.device)
-    ssq = torch.empty((), dtype=torch.float64, device=f_in.device)
+    f_out, pr, ssq = _outputs(out, [(f_in.shape, dt), ((3, n, n), ft), ((), torch.float64)], f_in.device)
     L.check(L.lib.msc_sweep_hpair(n, precision_code(precision), float(a), _ptr(f_in),
                                   _ptr(dm) if dm is not None else None, _ptr(h), _ptr(f_out), _ptr(pr), _ptr(ssq),
                                   _ptr(scratch.buf), scratch.nbytes, _stream(stream)), "msc_sweep_hpair")
@@ -362,10 +371,10 @@ def sweep_hpair(n: int, precision: str, a: float, f_in: torch.Tensor, h: torch.T
 
 
 def sweep_d3q19_pf(n: int, precision: str, a: float, f_in: torch.Tensor, pf_in: torch.Tensor, h: torch.Tensor,
-                   dm: torch.Tensor = None, scratch: StageScratch = None, stream=None):
+                   dm: torch.Tensor = None, scratch: StageScratch = None, stream=None, out=None):
     """The march's halo-free D3Q19 sweep through msc_sweep_d3q19_pf (pf_in = P f_in): returns
-    (f_out, P f_out, P r, sum r^2 as a device double).  h: (4, n, n, n) for FP64 storage, the binary32
-    pair (2, 4, n, n, n) = (high parts, low parts) for FP32 storage."""
+    (f_out, P f_out, P r, sum r^2 as a device double), written into `out` when given.  h: (4, n, n, n)
+    for FP64 storage, the binary32 pair (2, 4, n, n, n) = (high parts, low parts) for FP32 storage."""
     dt = storage_dtype(precision)
     for t in (f_in, pf_in, h) + ((dm,) if dm is not None else ()):
         if t.dtype != dt or not t.is_cuda or not t.is_contiguous():
@@ -373,10 +382,8 @@ def sweep_d3q19_pf(n: int, precision: str, a: float, f_in: torch.Tensor, pf_in: 
     if h.numel() != (2 if precision == "fp32" else 1) * 4 * n ** 3:
         raise ValueError("h: 4 n^3 values (FP64) or a binary32 pair of 2 x 4 n^3 values (FP32)")
     scratch = scratch or StageScratch(3, n, precision, f_in.device)
-    f_out = torch.empty_like(f_in)
-    pf_out = torch.empty_like(pf_in)
-    pr = torch.empty((4, n, n, n), dtype=dt, device=f_in.device)
-    ssq = torch.empty((), dtype=torch.float64, device=f_in.device)
+    f_out, pf_out, pr, ssq = _outputs(out, [(f_in.shape, dt), (pf_in.shape, dt), ((4, n, n, n), dt),
+                                            ((), torch.float64)], f_in.device)
     L.check(L.lib.msc_sweep_d3q19_pf(n, precision_code(precision), float(a), _ptr(f_in), _ptr(pf_in),
                                      _ptr(dm) if dm is not None else None, _ptr(h), _ptr(f_out), _ptr(pf_out), _ptr(pr),
                                      _ptr(ssq), _ptr(scratch.buf), scratch.nbytes, _stream(stream)),

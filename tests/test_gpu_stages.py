@@ -249,7 +249,12 @@ def test_sweep_hpair_matches_oracle(n, lift):
     assert rel_l2(host(f_out), f_T) < TOL["fp32"]["f"]
     assert rel_l2(host(pr), OK.moments(lat, r)) < TOL["fp32"]["pr"]
     assert abs(float(ss.item()) / float(np.sum(r * r)) - 1) < TOL["fp32"]["ss"]
-
+    # caller-given outputs (the bench's timed loop): the same values, written in place
+    out = (torch.full_like(f_out, float("nan")), torch.full_like(pr, float("nan")), torch.zeros_like(ss))
+    res = PL.sweep_hpair(n, "fp32", a, dev(f, torch.float32), dev(np.stack([hi, lo]), torch.float32),
+                         dev(dm, torch.float32) if lift else None, out=out)
+    assert all(x is y for x, y in zip(res, out))
+    assert torch.equal(out[0], f_out) and torch.equal(out[1], pr) and torch.equal(out[2], ss)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
@@ -275,6 +280,9 @@ def test_sweep_d3q19_halo_free_matches_oracle(n, lift, precision):
     pf_s = dev(OK.moments(lat, host(f_s)), T)
     a = 0.05
     f_out, pf_out, pr, ss = PL.sweep_d3q19_pf(n, precision, a, f_s, pf_s, h_s, dm_s)
+    out = tuple(torch.empty_like(t) for t in (f_out, pf_out, pr, ss))
+    PL.sweep_d3q19_pf(n, precision, a, f_s, pf_s, h_s, dm_s, out=out)
+    assert all(torch.equal(x, y) for x, y in zip(out, (f_out, pf_out, pr, ss)))
     trial = host(f_s) + (OK.linear_lift(lat, host(dm_s)) if lift else 0.0)
     f_T = OSW.sweep(lat, trial, a, h_o)
     r, _ = OSW.residual(f_T, trial)

@@ -229,8 +229,13 @@ __global__ void __launch_bounds__(kFftThreads) k_browfft(const BInst<T>* __restr
     list_entry(L, x, &i, &x0);
     Spec2Args<T> A;
     if (!spec_inst<T, MODE>(I[i], &A)) return;
-    if (INV) rowfft_inv_block<T>(A, x - x0);
-    else rowfft_fwd_block<T>(A, x - x0);
+    if (A.n <= kSpec2Radix4Max) {  // the single march's radix-4 form at small n (block-uniform)
+        if (INV) rowfft_inv_block<T, false, true>(A, x - x0);
+        else rowfft_fwd_block<T, true>(A, x - x0);
+    } else {
+        if (INV) rowfft_inv_block<T>(A, x - x0);
+        else rowfft_fwd_block<T>(A, x - x0);
+    }
 }
 
 template <typename T, int MODE>
@@ -244,7 +249,8 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 384 : 768) k_bcolsolve(const 
     list_entry(L, x, &i, &x0);
     Spec2Args<T> A;
     if (!spec_inst<T, MODE>(I[i], &A)) return;
-    colsolve_block<T>(A, x - x0, __ldg(M->col_g + i));
+    if (A.n <= kSpec2Radix4Max) colsolve_block<T, false, true>(A, x - x0, __ldg(M->col_g + i));
+    else colsolve_block<T>(A, x - x0, __ldg(M->col_g + i));
 }
 
 // field kernels: list entry j owns the field blocks [off[j], off[j + 1]), which cover its

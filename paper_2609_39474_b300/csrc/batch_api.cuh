@@ -83,6 +83,11 @@ BatchOffsets batch_offsets(msc_ctx* const* ctxs, int n_inst) {
 
 int col_thread_cap(int precision) { return precision == MSC_FP64 ? 384 : 768; }
 
+// points per thread of a transform line: 16 in the radix-16 form, 4 in the radix-4 form that the
+// single-lattice correction uses at n <= kSpec2Radix4Max (the batch follows it, so that its results
+// stay those of the single march bit for bit)
+int fft_pts(int n) { return spec2_radix4(n) ? 4 : 16; }
+
 bool tuning_ok(const msc_batch* b, const msc_batch_tuning* t) {
     if (t->n_classes != b->tun.n_classes) return false;
     if (t->sweep_ctas_per_sm < 1 || t->sweep_ctas_per_sm > 16) return false;
@@ -93,8 +98,8 @@ bool tuning_ok(const msc_batch* b, const msc_batch_tuning* t) {
         bool hb_ok = false;
         for (int h : kHbChoices) hb_ok |= h == hb;
         if (!hb_ok || hb > n) return false;
-        if (!is_pow2(P) || P > n / 2 || P * n / 16 > kFftThreads) return false;
-        if (!is_pow2(G) || G > 64 || 3 * G * n / 16 > col_thread_cap(b->precision)) return false;
+        if (!is_pow2(P) || P > n / 2 || P * n / fft_pts(n) > kFftThreads) return false;
+        if (!is_pow2(G) || G > 64 || 3 * G * n / fft_pts(n) > col_thread_cap(b->precision)) return false;
     }
     return true;
 }
@@ -105,7 +110,7 @@ void default_tuning(msc_batch* b) {
     for (int c = 0; c < t.n_classes; ++c) {
         const int n = t.n[c];
         t.sweep_rows[c] = sweep2_geometry(n, 4).hb;  // the batch's unit tables assume >= 4 rows per unit
-        t.fft_rows[c] = row_geometry(n, 3, n).P;
+        t.fft_rows[c] = spec2_radix4(n) ? row_geometry_n4(n).P : row_geometry(n, 3, n).P;
         t.col_lines[c] = 1;
     }
     t.sweep_ctas_per_sm = 4;
@@ -181,8 +186,8 @@ int upload_batch(msc_batch* b, const int (*t_slots)[2] = nullptr) {
         M.st[i] = I[i].st;
         M.iters[i] = I[i].iters;
         M.max_steps[i] = I[i].max_steps;
-        rth = std::max(rth, (P * n / 16 + 31) / 32 * 32);
-        cth = std::max(cth, (3 * G * n / 16 + 31) / 32 * 32);
+        rth = std::max(rth, (P * n / fft_pts(n) + 31) / 32 * 32);
+        cth = std::max(cth, (3 * G * n / fft_pts(n) + 31) / 32 * 32);
         rsm = std::max(rsm, (size_t)P * padded_len(n) * sizeof(C));
         csm = std::max(csm, (size_t)3 * G * padded_len(n) * sizeof(C));
     }
@@ -419,7 +424,7 @@ int autotune_batch(msc_batch* b, int reps) {
         const int n = t.n[c];
         int best_p = t.fft_rows[c];
         float best = 1e30f;
-        for (int P = 1; P <= n / 2 && P * n / 16 <= kFftThreads; P <<= 1) {
+        for (int P = 1; P <= n / 2 && P * n / fft_pts(n) <= kFftThreads; P <<= 1) {
             t.fft_rows[c] = P;
             if ((rc = measure(1, &cur))) return rc;
             if (cur < best) { best = cur; best_p = P; }
@@ -432,7 +437,7 @@ int autotune_batch(msc_batch* b, int reps) {
         const int n = t.n[c];
         int best_g = t.col_lines[c];
         float best = 1e30f;
-        for (int G = 1; G <= 64 && 3 * G * n / 16 <= col_thread_cap(b->precision); G <<= 1) {
+        for (int G = 1; G <= 64 && 3 * G * n / fft_pts(n) <= col_thread_cap(b->precision); G <<= 1) {
             t.col_lines[c] = G;
             if ((rc = measure(2, &cur))) return rc;
             if (cur < best) { best = cur; best_g = G; }

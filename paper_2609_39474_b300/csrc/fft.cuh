@@ -131,11 +131,12 @@ __device__ __forceinline__ int pad(int i) { return i + (i >> 4); }
 // One in-place Stockham stage of radix R over nfft arrays of length n: every butterfly j reads the
 // R values j + r n/R, multiplies value r by w^(k r n/(Ns R)) with k = j mod Ns, does the R-point DFT
 // in registers and writes value r to (j - k) R + k + r Ns.  All reads of the stage complete before
-// any write (block barrier), so one buffer suffices.  Each thread handles at most 16/R butterflies.
-template <typename C, int R, bool INV>
+// any write (block barrier), so one buffer suffices.  Each thread handles at most MB butterflies
+// (the host geometry launches at least nfft n / (R MB) threads): 16/R in the radix-16 form (n/16
+// threads per array), 1 in the radix-4 form (n/4 threads per array).
+template <typename C, int R, bool INV, int MB = 16 / R>
 __device__ __forceinline__ void stockham_stage(C* x, int n, int logn, int Ns, int nfft, const C* __restrict__ tw) {
     constexpr int LR = R == 2 ? 1 : (R == 4 ? 2 : (R == 8 ? 3 : 4));
-    constexpr int MB = 16 / R;  // butterflies per thread (host geometry guarantees enough threads)
     const int lnb = logn - LR;
     const int nb = 1 << lnb;
     const int tstride = n / (Ns * R);
@@ -208,6 +209,24 @@ __device__ void fft_stockham(C* x, int n, int logn, int nfft, const C* __restric
     for (int rem = logn - first; rem > 0; rem -= 4) {
         stockham_stage<C, 16, INV>(x, n, logn, Ns, nfft, tw);
         Ns <<= 4;
+    }
+}
+
+// The same transform in radix-4 stages (a radix-2 stage first when log2(n) is odd) with n/4 threads
+// per array: for small n, where the radix-16 form gives an array only n/16 threads and each thread a
+// long serial chain of 16-point butterflies (N = 256: 16 threads per line).  Twice the stages and
+// barriers, a quarter of the work per thread per stage.  Must be called by all threads of the
+// block, with blockDim.x >= nfft * n / 4.
+template <typename C, bool INV>
+__device__ void fft_stockham_n4(C* x, int n, int logn, int nfft, const C* __restrict__ tw) {
+    int Ns = 1;
+    if (logn & 1) {
+        stockham_stage<C, 2, INV, 2>(x, n, logn, Ns, nfft, tw);
+        Ns = 2;
+    }
+    for (int rem = logn - (logn & 1); rem > 0; rem -= 2) {
+        stockham_stage<C, 4, INV, 1>(x, n, logn, Ns, nfft, tw);
+        Ns <<= 2;
     }
 }
 

@@ -266,13 +266,11 @@ void add_spectral_nodes(msc_ctx* c, cudaGraph_t g, cudaError_t* err) {
                                    at<double>(c, c->lay.coef));
     void* args[] = {&S};
     if (c->desc.dim == 2) {
-        const RowGeom rg = row_geometry(n, 3, n);
         S.nf = 3;
         S.rows = n;
-        S.P = rg.P;
         S.nscale = 1.0 / ((double)n * n);
         Spec2Launch L[3];
-        spectral2_launches<T>(n, L);
+        S.P = spectral2_launches<T>(n, L);
         cudaGraphNode_t n1 = add_kernel(g, {}, L[0].fn, L[0].grid, L[0].block, L[0].smem, args, err);
         cudaGraphNode_t n2 = add_kernel(g, {n1}, L[1].fn, L[1].grid, L[1].block, L[1].smem, args, err);
         add_kernel(g, {n2}, L[2].fn, L[2].grid, L[2].block, L[2].smem, args, err);
@@ -547,13 +545,11 @@ int run_stepwise(msc_ctx* c, int n_steps) {
     int nspec = 0;
     if (c->desc.dim == 2) {
         const int n = c->desc.n;
-        const RowGeom rg = row_geometry(n, 3, n);
         S.nf = 3;
         S.rows = n;
-        S.P = rg.P;
         S.nscale = 1.0 / ((double)n * n);
         Spec2Launch SL[3];
-        spectral2_launches<T>(n, SL);
+        S.P = spectral2_launches<T>(n, SL);
         for (int i = 0; i < 3; ++i) spec[i] = {SL[i].fn, SL[i].grid, SL[i].block, SL[i].smem};
         nspec = 3;
     } else {
@@ -1087,17 +1083,15 @@ int stage_shadow(int dim, int n, double a, double nu, const void* pr, void* dm, 
         A.tw = (const C*)S.tw;
         A.n = n;
         A.logn = ilog2(n);
-        const RowGeom rg = row_geometry(n, 3, n);
         A.nf = 3;
         A.rows = n;
-        A.P = rg.P;
         A.a = a;
         A.nu = nu;
         A.kunit = 6.283185307179586476925286766559 / (double)n;
         A.nscale = 1.0 / ((double)n * n);
         A.st = nullptr;
         Spec2Launch L[3];
-        spectral2_launches<T>(n, L);
+        A.P = spectral2_launches<T>(n, L);
         void* args[] = {&A};
         for (int i = 0; i < 3; ++i) CK(cudaLaunchKernel(L[i].fn, L[i].grid, L[i].block, args, L[i].smem, stream));
         return MSC_OK;

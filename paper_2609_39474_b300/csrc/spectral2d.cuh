@@ -72,13 +72,37 @@ inline RowGeom row_geometry(int n, int nf, int rows) {
     return {P, t, npairs / P};
 }
 
+// The 2D correction of small lattices takes the radix-4 transforms (n/4 threads per line): at
+// N <= kSpec2Radix4Max the radix-16 form leaves a column block 3 n/16 threads (N = 256: 48) and a
+// row block 16, so each pass is a few long serial chains per SM.
+constexpr int kSpec2Radix4Max = 256;
+inline bool spec2_radix4(int n) { return n <= kSpec2Radix4Max; }
+
+// row blocks of the radix-4 form: one row pair per block (n/4 threads), or two below n = 128 so a
+// block keeps at least 32 threads busy
+inline RowGeom row_geometry_n4(int n) {
+    int P = n >= 128 ? 1 : 128 / n;
+    if (P > n / 2) P = n / 2;
+    int t = (P * n / 4 + 31) / 32 * 32;
+    if (t < 32) t = 32;
+    return {P, t, 3 * (n / 2) / P};
+}
+
 template <typename T>
 inline size_t spec_row_smem(int n, int P) {
     return (size_t)P * padded_len(n) * sizeof(typename Cplx<T>::type);
 }
 
+// the row and column transforms: radix-16 stages (n/16 threads per array) or, N4, radix-4 stages
+// (n/4 threads per array; small lattices)
+template <typename C, bool INV, bool N4>
+__device__ __forceinline__ void fft_lines(C* s, int n, int logn, int nfft, const C* __restrict__ tw) {
+    if constexpr (N4) fft_stockham_n4<C, INV>(s, n, logn, nfft, tw);
+    else fft_stockham<C, INV>(s, n, logn, nfft, tw);
+}
+
 // 2P consecutive rows (c, y0 .. y0 + 2P - 1) form P complex rows
-template <typename T>
+template <typename T, bool N4 = false>
 __device__ __forceinline__ void rowfft_fwd_block(const Spec2Args<T>& A, int bid) {
     using C = typename Cplx<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -104,7 +128,7 @@ __device__ __forceinline__ void rowfft_fwd_block(const Spec2Args<T>& A, int bid)
         s[p * plen + pad(x)] = z;
     }
     __syncthreads();
-    fft_stockham<C, false>(s, n, logn, P, A.tw);
+    fft_lines<C, false, N4>(s, n, logn, P, A.tw);
     // split the two real transforms; thread t -> (j_x, row r in 0..2P-1), r fastest
     C* out = A.spec + (size_t)c * nx4 * A.rows + y0;
     const int l2p = __ffs(2 * P) - 1;  // P is a power of two
@@ -127,14 +151,14 @@ __device__ __forceinline__ void rowfft_fwd_block(const Spec2Args<T>& A, int bid)
     }
 }
 
-template <typename T>
+template <typename T, bool N4 = false>
 __global__ void __launch_bounds__(kFftThreads) k_rowfft_fwd(Spec2Args<T> A) {
-    rowfft_fwd_block<T>(A, blockIdx.x);
+    rowfft_fwd_block<T, N4>(A, blockIdx.x);
 }
 
 // ACC = false: dm = the correction.  ACC = true (the adjoint's update): dm += pr + the correction,
 // dm holding the iterate and pr the residual the forward pass transformed.
-template <typename T, bool ACC = false>
+template <typename T, bool ACC = false, bool N4 = false>
 __device__ __forceinline__ void rowfft_inv_block(const Spec2Args<T>& A, int bid) {
     using C = typename Cplx<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -171,7 +195,7 @@ __device__ __forceinline__ void rowfft_inv_block(const Spec2Args<T>& A, int bid)
         s[p * plen + pad(j)] = z;
     }
     __syncthreads();
-    fft_stockham<C, true>(s, n, logn, P, A.tw);
+    fft_lines<C, true, N4>(s, n, logn, P, A.tw);
     T* __restrict__ rows = A.dm + ((size_t)c * A.rows + y0) * n;
     if (ACC) {
         // four iterations at a time: all their iterate and residual loads are issued before the
@@ -214,9 +238,9 @@ __device__ __forceinline__ void rowfft_inv_block(const Spec2Args<T>& A, int bid)
     }
 }
 
-template <typename T>
+template <typename T, bool N4 = false>
 __global__ void __launch_bounds__(kFftThreads) k_rowfft_inv(Spec2Args<T> A) {
-    rowfft_inv_block<T>(A, blockIdx.x);
+    rowfft_inv_block<T, false, N4>(A, blockIdx.x);
 }
 
 // the inverse row pass of the adjoint shadow correction, fused with the iterate update
@@ -301,7 +325,7 @@ __device__ __forceinline__ void solve_mode(const Spec2Args<T>& A, typename Cplx<
 
 // 2D: G consecutive kept j_x columns per block (G a power of two; the last block of a lattice may
 // hold fewer), all three fields of each.  Line (c, g) of the block sits at (c G + g) plen in shared memory.
-template <typename T, bool ADJ = false>
+template <typename T, bool ADJ = false, bool N4 = false>
 __device__ __forceinline__ void colsolve_block(const Spec2Args<T>& A, int bid, int G) {
     using C = typename Cplx<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -325,7 +349,7 @@ __device__ __forceinline__ void colsolve_block(const Spec2Args<T>& A, int bid, i
             s[(c * G + (gy >> logn)) * plen + pad(gy & (n - 1))] = v;
     }
     __syncthreads();
-    fft_stockham<C, false>(s, n, logn, 3 * G, A.tw);
+    fft_lines<C, false, N4>(s, n, logn, 3 * G, A.tw);
     const double a = A.st ? A.st->a : A.a;
     const double* tab = solve_table(A.coef, A.st, 2, n);
     for (int t = threadIdx.x; t < gn; t += blockDim.x) {
@@ -335,7 +359,7 @@ __device__ __forceinline__ void colsolve_block(const Spec2Args<T>& A, int bid, i
         solve_mode<T, ADJ>(A, v, jx0 + g, jy, g < ng, a, tab);
     }
     __syncthreads();
-    fft_stockham<C, true>(s, n, logn, 3 * G, A.tw);
+    fft_lines<C, true, N4>(s, n, logn, 3 * G, A.tw);
     for (int t = threadIdx.x; t < 3 * gn; t += blockDim.x) {
         const int c = t >> lgn;
         const int gy = t & (gn - 1);
@@ -344,9 +368,9 @@ __device__ __forceinline__ void colsolve_block(const Spec2Args<T>& A, int bid, i
     }
 }
 
-template <typename T>
+template <typename T, bool N4 = false>
 __global__ void __launch_bounds__(sizeof(T) == 8 ? 384 : 768) k_colsolve(Spec2Args<T> A) {
-    colsolve_block<T>(A, blockIdx.x, 1);
+    colsolve_block<T, false, N4>(A, blockIdx.x, 1);
 }
 
 // the transposed column solve of the adjoint shadow correction
@@ -407,14 +431,24 @@ __global__ void __launch_bounds__(96) k_colsolve_1024(Spec2Args<float> A) {
 }
 
 // The three launches of the 2D shadow correction (row FFTs, column FFT + solve + inverse, inverse
-// row FFTs) for lattice size n and working type T, all taking one Spec2Args block.
+// row FFTs) for lattice size n and working type T, all taking one Spec2Args block; returns the row
+// pairs per row block (Spec2Args::P) that the launches assume.
 struct Spec2Launch {
     const void* fn;
     dim3 grid, block;
     size_t smem;
 };
 template <typename T>
-inline void spectral2_launches(int n, Spec2Launch L[3]) {
+inline int spectral2_launches(int n, Spec2Launch L[3]) {
+    if (spec2_radix4(n)) {  // small lattices: radix-4 transforms, n/4 threads per line
+        const RowGeom rg = row_geometry_n4(n);
+        const size_t rsm = spec_row_smem<T>(n, rg.P);
+        const int ct = (3 * n / 4 + 31) / 32 * 32;
+        L[0] = {(const void*)k_rowfft_fwd<T, true>, dim3(rg.blocks), dim3(rg.threads), rsm};
+        L[1] = {(const void*)k_colsolve<T, true>, dim3(n / 4 + 1), dim3(ct < 32 ? 32 : ct), spec2_col_smem<T>(n)};
+        L[2] = {(const void*)k_rowfft_inv<T, true>, dim3(rg.blocks), dim3(rg.threads), rsm};
+        return rg.P;
+    }
     const RowGeom rg = row_geometry(n, 3, n);
     const size_t rsm = spec_row_smem<T>(n, rg.P);
     L[0] = {(const void*)k_rowfft_fwd<T>, dim3(rg.blocks), dim3(rg.threads), rsm};
@@ -422,6 +456,7 @@ inline void spectral2_launches(int n, Spec2Launch L[3]) {
     if (std::is_same<T, float>::value && n == 1024)
         L[1] = {(const void*)k_colsolve_1024, dim3(n / 4 + 1), dim3(96), spec2_col_smem<T>(n)};
     L[2] = {(const void*)k_rowfft_inv<T>, dim3(rg.blocks), dim3(rg.threads), rsm};
+    return rg.P;
 }
 
 }  // namespace msc

@@ -46,6 +46,8 @@ KMAX = 300
 # candidate the reference arm (and the single-phase profiling aids) use: the fastest matched-gate candidate
 # of the GPU candidate search at N = 1024 and at N = 256
 DEFAULT_CANDIDATE = {1024: (1024, 1e-8), 256: (256, 1e-6)}
+# the D3Q19 workload's (N = 128) matched-gate candidate, for the profiling phases
+DEFAULT_CANDIDATE_3D = (32, 1e-10)
 # the march's D2Q9 sweep: f in/out, h as a binary32 pair, lifted dm, P r
 SWEEP_BYTES_PER_SITE_FP32 = 2 * 9 * 4 + 2 * 3 * 4 + 3 * 4 + 3 * 4
 SWEEP_BYTES_PER_SITE_FP16 = 2 * 9 * 2 + 2 * 3 * 4 + 3 * 4 + 3 * 4  # binary16 f in/out, FP32 h pair, dm, P r
@@ -729,14 +731,20 @@ def run_phase(args):
         return {"phase": "adjoint-stepwise", **adjoint_stepwise(torch, PL, dev)}
     if args.phase == "offdesign":
         return {"phase": "offdesign", **measure_offdesign(torch, PL, dev)}
-    n = args.n
-    S, eps = DEFAULT_CANDIDATE.get(n, (64, 1e-8))
-    p, u = random_phase(n, 2, 1.0, seed=1, kmax=8)
-    t_end = nint(0.15 * n * n)
+    n, dim = args.n, args.dim
+    if dim == 3:  # the D3Q19 workload and its timed candidate
+        w = WORKLOADS[(3, n)]
+        S, eps = DEFAULT_CANDIDATE_3D
+        p, u = random_phase(n, 3, 1.0, seed=w["seed"], kmax=w["kmax"])
+        t_end, nmin = w["t_end"], w["nmin"]
+    else:
+        S, eps = DEFAULT_CANDIDATE.get(n, (64, 1e-8))
+        p, u = random_phase(n, 2, 1.0, seed=1, kmax=8)
+        t_end, nmin = nint(0.15 * n * n), 2
     p_d = torch.as_tensor(p, device=dev)
     u_d = torch.as_tensor(u, device=dev)
-    L = PL.MscLattice(2, n, "fp32", max_steps=4096, device="cuda:0")
-    L.set_params(dt=t_end / S, eps=eps, kmax=KMAX, nmin=2)
+    L = PL.MscLattice(dim, n, "fp32", max_steps=4096, device="cuda:0")
+    L.set_params(dt=t_end / S, eps=eps, kmax=KMAX, nmin=nmin)
     times = []
     for i in range(args.warmup + args.steps):
         L.init_fields(p_d, u_d)
@@ -751,8 +759,8 @@ def run_phase(args):
         if i >= args.warmup:
             times.append(e0.elapsed_time(e1))
     st = L.stats()
-    return {"phase": "msc", "n": n, "S": S, "eps": eps, "ms": statistics.mean(times), "inner": st["inner_total"],
-            "status": st["status"]}
+    return {"phase": "msc", "dim": dim, "n": n, "S": S, "eps": eps, "ms": statistics.mean(times),
+            "inner": st["inner_total"], "status": st["status"]}
 
 
 def warm_up(torch, fn, seconds=0.25, least=3):
@@ -1021,6 +1029,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=1024)
+    ap.add_argument("--dim", type=int, default=2, choices=[2, 3], help="lattice of --phase msc / msc-stepwise "
+                    "(3: the D3Q19 workload, use with --n 128)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--details", default=None,
                     help="write the full results (candidates, secondary workloads, batch, FP16, adjoint, "

@@ -28,11 +28,27 @@ __host__ __device__ inline int ypass_lines(int n) {
     int g = 4096 / n;
     return g > n ? n : (g < 1 ? 1 : g);
 }
-// z pass: 4 fields x G masked j_y lines per block (4 G n / 16 <= 768 FP32, 384 FP64)
+// z pass: 4 fields x G masked j_y lines per block (4 G n / 16 <= 768 FP32, 384 FP64).  G = 512 / n
+// (FP32; 256 / n FP64): at N = 128, 561 blocks of 128 threads instead of 165 of 512, which left most
+// SMs with one block of long serial FFT and FP64-solve chains (D3Q19 march 36.5 -> 34.8 ms alone)
 template <typename T>
 __host__ __device__ inline int zsolve_lines(int n) {
-    int g = (sizeof(T) == 8 ? 1024 : 2048) / n;  // power of two
+    int g = (sizeof(T) == 8 ? 256 : 512) / n;  // power of two
     return g < 1 ? 1 : g;
+}
+
+// x passes of the 3D correction: the 2D row rule with at most 8 row pairs per block (N = 128: 4096
+// blocks of 64 threads instead of 1024 of 256; with the z pass above the D3Q19 march 36.5 -> 33.4 ms,
+// same inner counts; 4 pairs per block, or 2 z lines per block, gained nothing more)
+inline RowGeom row_geometry3(int n) {
+    RowGeom rg = row_geometry(n, 4, n * n);
+    if (rg.P > 8) {
+        rg.blocks = rg.blocks * rg.P / 8;
+        rg.P = 8;
+        rg.threads = (8 * n / 16 + 31) / 32 * 32;
+        if (rg.threads < 32) rg.threads = 32;
+    }
+    return rg;
 }
 
 template <typename T, bool INV>
@@ -142,8 +158,7 @@ template <typename T>
 inline void spectral3_launches(int n, LaunchDesc* L) {
     using C = typename Cplx<T>::type;
     const int nx4 = n / 4 + 1, ny = n / 2 + 1;
-    const int rows = n * n;
-    const RowGeom rg = row_geometry(n, 4, rows);
+    const RowGeom rg = row_geometry3(n);
     const size_t rsm = spec_row_smem<T>(n, rg.P);
     const int yg = ypass_lines(n), zg = zsolve_lines<T>(n);
     const int yth = ((yg * n / 16 + 31) / 32) * 32;
@@ -162,7 +177,7 @@ inline void spectral3_launches(int n, LaunchDesc* L) {
 // passes read P, the y pass and the z pass read G.  The launchers below set both.
 template <typename T>
 inline void spec3_pass_args(int n, Spec2Args<T>* A, int pass) {
-    A->P = row_geometry(n, 4, n * n).P;
+    A->P = row_geometry3(n).P;
     A->G = pass == 2 ? zsolve_lines<T>(n) : ypass_lines(n);
 }
 

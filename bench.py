@@ -248,7 +248,7 @@ def measure_workload(torch, PL, dev, dim, n, steps, warmup, dist=None, full=Fals
                          "timing the most accurate converged candidate\n")
 
     # -- timed region: K full marches of the matched winner --------------------------------------
-    clocks = ClockSampler(dev.index) if full else None
+    clocks = ClockSampler(dev.index)  # secondary workloads keep theirs in the details
     if clocks:
         clocks.start()
     for _ in range(warmup):
@@ -691,14 +691,12 @@ def run_ours(args, rank, world, dist):
         # FP16 population storage on the headline workload, against the FP32 explicit baseline
         f16 = measure_workload(torch, PL, dev, 2, args.n, max(3, min(args.steps, 10)), 3, dist, full=False,
                                precision="fp16", explicit_ref=(res["t_explicit_ms"], res["e_explicit"]))
-        f16.pop("clocks", None)
         f16["sweep_roofline_n4096"] = sweep_time(torch, PL, dev, ROOF_N, reps=20, precision="fp16")
         res["fp16"] = f16
         for dim, n in ((2, 256), (3, 128)):
             if (dim, n) != (2, args.n):
                 try:
                     sec = measure_workload(torch, PL, dev, dim, n, max(3, min(args.steps, 10)), 3, dist, full=False)
-                    sec.pop("clocks", None)
                 except RuntimeError as exc:
                     sec = {"workload": f"dim {dim} N {n}", "error": str(exc)}
                 res["secondary"].append(sec)

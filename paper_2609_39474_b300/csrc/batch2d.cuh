@@ -130,6 +130,7 @@ template <typename T, int MODE>
 __global__ void __launch_bounds__(kSweepWarps * 32) k_bsweep2(const BInst<T>* __restrict__ I,
                                                              const BMap* __restrict__ M,
                                                              const BAct* __restrict__ W, int ex_node) {
+    if constexpr (MODE == 2) wait_for_predecessor();  // the batched explicit graph chains its steps (programmatic)
     const int lane = threadIdx.x & 31;
     const int nw = gridDim.x * kSweepWarps;
     const BList L = blist<MODE>(M, W, 0);

@@ -302,8 +302,11 @@ int build_batch_explicit_graph(msc_batch* b) {
         void* a_sw[] = {&I, &M, &no_list, &nodes[i]};
         std::vector<cudaGraphNode_t> deps;
         if (prev) deps.push_back(prev);
-        prev = add_kernel(body, deps, (const void*)k_bsweep2<T, 2>, dim3(b->sweep_grid), dim3(kSweepWarps * 32), 0,
-                          a_sw, &err);
+        prev = prev && kExplicitProgrammatic
+                   ? add_kernel_after(body, prev, (const void*)k_bsweep2<T, 2>, dim3(b->sweep_grid),
+                                      dim3(kSweepWarps * 32), 0, a_sw, &err)
+                   : add_kernel(body, deps, (const void*)k_bsweep2<T, 2>, dim3(b->sweep_grid), dim3(kSweepWarps * 32),
+                                0, a_sw, &err);
     }
     void* a_cnt[] = {&M, &unroll, &h_ex};
     add_kernel(body, {prev}, (const void*)k_bex_count, dim3(1), dim3(kBatchMax), 0, a_cnt, &err);

@@ -214,6 +214,12 @@ __device__ __forceinline__ void split_f64(double x, float& hi, float& lo) {
     lo = __uint_as_float(__float_as_uint(v) ^ (up ? sgn ^ 0x80000000u : sgn));
 }
 
+// Programmatic dependent launch: a kernel that a graph starts on a programmatic edge may begin while its
+// predecessor drains; it waits here, before its first read of the predecessor's results, until that
+// grid has completed and its memory operations are visible.  Without such an edge (stream launches,
+// ordinary graph edges) the instruction returns at once.
+__device__ __forceinline__ void wait_for_predecessor() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // s + e = a + b exactly (Knuth's two-sum, six binary32 operations, no ordering assumption)
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
     s = a + b;

@@ -604,6 +604,7 @@ __global__ void k_step_finish(DevState* st, int* iters_out, int max_steps,
 // opened (the first step of a launch opens it through the handle's default value)
 __global__ void k_step_finish_graph(DevState* st, int* iters_out, int max_steps, cudaGraphConditionalHandle h_step,
                                     cudaGraphConditionalHandle h_iter) {
+    wait_for_predecessor();
     const unsigned int go = step_finish(st, iters_out, max_steps);
     cudaGraphSetConditional(h_step, go);
     cudaGraphSetConditional(h_iter, 1u);

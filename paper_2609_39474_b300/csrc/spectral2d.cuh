@@ -240,6 +240,7 @@ __device__ __forceinline__ void rowfft_inv_block(const Spec2Args<T>& A, int bid)
 
 template <typename T, bool N4 = false>
 __global__ void __launch_bounds__(kFftThreads) k_rowfft_inv(Spec2Args<T> A) {
+    wait_for_predecessor();
     rowfft_inv_block<T, false, N4>(A, blockIdx.x);
 }
 
@@ -370,6 +371,7 @@ __device__ __forceinline__ void colsolve_block(const Spec2Args<T>& A, int bid, i
 
 template <typename T, bool N4 = false>
 __global__ void __launch_bounds__(sizeof(T) == 8 ? 384 : 768) k_colsolve(Spec2Args<T> A) {
+    wait_for_predecessor();
     colsolve_block<T, false, N4>(A, blockIdx.x, 1);
 }
 
@@ -399,6 +401,7 @@ inline size_t spec2_col_smem(int n) {
 // SM, and ran slower than the block-synchronous versions.)
 // column pass at N = 1024: warp c transforms field c of kept column j_x = blockIdx.x
 __global__ void __launch_bounds__(96) k_colsolve_1024(Spec2Args<float> A) {
+    wait_for_predecessor();
     using C = float2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* s = reinterpret_cast<C*>(smem_raw);

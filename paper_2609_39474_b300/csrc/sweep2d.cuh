@@ -304,6 +304,7 @@ __device__ __forceinline__ double sweep2_unit(const S* fin, const T* dm, const T
 template <typename T, typename S, bool EXPLICIT, bool GRAPH, bool TRT = false,
           bool HPAIR = GRAPH && !EXPLICIT && std::is_same<T, float>::value>
 __global__ void __launch_bounds__(kSweepWarps * 32, sizeof(T) == 4 && !TRT ? 5 : 1) k_sweep2(Sweep2Args<T, S> A) {
+    if constexpr (EXPLICIT && GRAPH) wait_for_predecessor();  // the explicit graph chains its steps on programmatic edges
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int n = A.n;

@@ -80,6 +80,7 @@ inline Sweep3Geom sweep3_geometry(int n, int elem) {
 
 template <typename T, bool EXPLICIT, bool GRAPH>
 __global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 512) k_sweep3(Sweep3Args<T> A) {
+    if constexpr (EXPLICIT && GRAPH) wait_for_predecessor();  // the explicit graph chains its steps on programmatic edges
     using L = D3Q19;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sC0 = reinterpret_cast<T*>(smem_raw);  // [2][16][TYB][32]: plane j uses buffer j & 1

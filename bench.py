@@ -328,7 +328,7 @@ def measure_workload(torch, PL, dev, dim, n, steps, warmup, dist=None, full=Fals
 
 BATCH_NS = (128, 256, 512)
 BATCH_RES = [float(r) for r in np.logspace(-4, 2, 16)]
-BATCH_S = [8, 16, 32, 64, 128]
+BATCH_S = [8, 16, 32, 64, 128, 256, 512]
 BATCH_EPS = [1e-6, 1e-8, 1e-10, 1e-12]
 
 

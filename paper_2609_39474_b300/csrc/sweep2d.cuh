@@ -192,7 +192,10 @@ __device__ __forceinline__ double sweep2_unit(const S* fin, const T* dm, const T
             }
         }
         T C[9];
-        if constexpr (!TRT && HPAIR) {
+        // the exact dominant term serves FP32 storage (the matched-accuracy march); binary16 storage
+        // rounds every stored population to 2^-11, which swamps the binary32 collision rounding that
+        // the exact term removes, and takes the plain collision below (fewer instructions per site)
+        if constexpr (!TRT && HPAIR && std::is_same<S, float>::value) {
             // operating-point collision C = f_eq + Phi/2 (Eq. collision-operating) in binary32 with the
             // dominant term kept exact.  With u = J + Y (J = P_u f the moment sums, Y the O(a) correction)
             // C_k = (3 w_k) c_k.J + w_k (A0 + 3 c_k.Y + 1.5 c_k.s + 4.5 c_k.u (c_k.u + c_k.s)): the first

@@ -40,14 +40,17 @@ NU = 1.0 / 6.0
 # physical steps per march searched by the candidate matrix (Table protocol, with bracket extensions
 # beyond 256 and between the powers of two there): the long end is needed by the matched gate at N = 1024,
 # where the explicit LBM is accurate to 1.5e-6 relative
-S_LIST = [4, 8, 16, 32, 64, 128, 256, 384, 512, 768, 1024, 1536, 2048, 4096]
+S_LIST = [4, 8, 16, 32, 64, 128, 192, 256, 320, 384, 512, 768, 1024, 1536, 2048, 4096]
+# n_min of Algorithm 1 searched with S and eps (D2Q9): 2, and 4 (four converged sweeps per step
+# make each step more accurate, so that fewer, larger steps meet the matched gate)
+NMIN_2D = [2, 4]
 EPS_LIST = [1e-6, 1e-8, 1e-10]
 KMAX = 300
-# candidate the reference arm (and the single-phase profiling aids) use: the fastest matched-gate candidate
-# of the GPU candidate search at N = 1024 and at N = 256
-DEFAULT_CANDIDATE = {1024: (1024, 1e-8), 256: (256, 1e-6)}
+# candidate (S, eps, n_min) the reference arm (and the single-phase profiling aids) use: the fastest
+# matched-gate candidate of the GPU candidate search at N = 1024 and at N = 256
+DEFAULT_CANDIDATE = {1024: (384, 1e-8, 4), 256: (192, 1e-6, 2)}
 # the D3Q19 workload's (N = 128) matched-gate candidate, for the profiling phases
-DEFAULT_CANDIDATE_3D = (32, 1e-10)
+DEFAULT_CANDIDATE_3D = (32, 1e-10, 1)
 # the march's D2Q9 sweep: f in/out, h as a binary32 pair, lifted dm, P r
 SWEEP_BYTES_PER_SITE_FP32 = 2 * 9 * 4 + 2 * 3 * 4 + 3 * 4 + 3 * 4
 SWEEP_BYTES_PER_SITE_FP16 = 2 * 9 * 2 + 2 * 3 * 4 + 3 * 4 + 3 * 4  # binary16 f in/out, FP32 h pair, dm, P r
@@ -57,9 +60,11 @@ ROOF_N = 4096  # out-of-L2 size for the sweep roofline (16.7 M sites, 1.8 GB per
 # (dim, N): seed, band limit, T_end, n_min, candidate matrix (Table protocol; FP32 storage cannot
 # reach eps = 1e-12), NS reference resolution
 WORKLOADS = {
-    (2, 1024): dict(seed=1, kmax=8, t_end=nint(0.15 * 1024 ** 2), nmin=2, S=S_LIST, eps=EPS_LIST, M=64, steps=None),
-    (2, 256): dict(seed=1, kmax=8, t_end=nint(0.15 * 256 ** 2), nmin=2, S=S_LIST, eps=EPS_LIST, M=64, steps=None),
-    (3, 128): dict(seed=7, kmax=6, t_end=nint(0.075 * 128 ** 2), nmin=1, S=[3, 4, 5, 8, 16, 32, 64, 128, 256, 512],
+    (2, 1024): dict(seed=1, kmax=8, t_end=nint(0.15 * 1024 ** 2), nmins=NMIN_2D, S=S_LIST, eps=EPS_LIST, M=64,
+                    steps=None),
+    (2, 256): dict(seed=1, kmax=8, t_end=nint(0.15 * 256 ** 2), nmins=NMIN_2D, S=S_LIST, eps=EPS_LIST, M=64,
+                   steps=None),
+    (3, 128): dict(seed=7, kmax=6, t_end=nint(0.075 * 128 ** 2), nmins=[1], S=[3, 4, 5, 8, 16, 32, 64, 128, 256, 512],
                    eps=EPS_LIST, M=32, steps=100),
 }
 
@@ -215,8 +220,8 @@ def measure_workload(torch, PL, dev, dim, n, steps, warmup, dist=None, full=Fals
         t_ex, e_ex = explicit_ref
 
     # -- candidate matrix (Table protocol), untimed selection ------------------------------------
-    def msc_once(S, eps):
-        L.set_params(dt=t_end / S, eps=eps, kmax=KMAX, nmin=w["nmin"])
+    def msc_once(S, eps, nmin):
+        L.set_params(dt=t_end / S, eps=eps, kmax=KMAX, nmin=nmin)
         L.init_fields(p_d, u_d)
         flush.zero_()
         e0, e1 = ev(), ev()
@@ -226,17 +231,17 @@ def measure_workload(torch, PL, dev, dim, n, steps, warmup, dist=None, full=Fals
         torch.cuda.synchronize()
         return e0.elapsed_time(e1), L.stats()
 
-    msc_once(w["S"][0], w["eps"][0])  # builds the march graph outside any measurement
+    msc_once(w["S"][0], w["eps"][0], w["nmins"][0])  # builds the march graph outside any measurement
     cands = []
     u0_rms = rms_vector(u)
     for S in [S for S in w["S"] if S <= t_end]:
-        for eps in w["eps"]:
-            ms, st = msc_once(S, eps)
+        for eps, nmin in [(e, m) for m in w["nmins"] for e in w["eps"]]:
+            ms, st = msc_once(S, eps, nmin)
             ok = st["status"] == 0 and st["steps_done"] == S
             uu = L.fields()[1].cpu().numpy() if ok else None
             e = velocity_error(uu, u_ref) if ok else float("inf")
             rel = e / max(rms_vector(uu), 1e-12) if ok else float("inf")
-            c = dict(S=S, eps=eps, ms=ms, err=e, rel=rel, ok=ok, inner=st["inner_total"])
+            c = dict(S=S, eps=eps, nmin=nmin, ms=ms, err=e, rel=rel, ok=ok, inner=st["inner_total"])
             if dim == 3 and ok:  # the paper's 3D engineering error: vs the explicit endpoint / initial RMS
                 c["rel_vs_explicit"] = velocity_error(uu, u_ex) / u0_rms
             cands.append(c)
@@ -252,7 +257,7 @@ def measure_workload(torch, PL, dev, dim, n, steps, warmup, dist=None, full=Fals
     if clocks:
         clocks.start()
     for _ in range(warmup):
-        msc_once(best["S"], best["eps"])
+        msc_once(best["S"], best["eps"], best["nmin"])
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
@@ -260,12 +265,12 @@ def measure_workload(torch, PL, dev, dim, n, steps, warmup, dist=None, full=Fals
     launches = 0
     S = best["S"]
     for _ in range(steps):
-        ms, st = msc_once(S, best["eps"])
+        ms, st = msc_once(S, best["eps"], best["nmin"])
         times.append(ms)
         inner.append(st["inner_total"])
-        # set_target + arm, 4 per physical step (setup, begin, end, finish), one sweep per inner
-        # iteration and the spectral kernels of every correction (each non-accepted iteration)
-        launches += 2 + 4 * S + st["inner_total"] + nspec * (st["inner_total"] - S)
+        # set_target, arm + first set-up and warm start, 2 per physical step (end, finish), one sweep per
+        # inner iteration and the spectral kernels of every correction (each non-accepted iteration)
+        launches += 3 + 2 * S + st["inner_total"] + nspec * (st["inner_total"] - S)
     torch.cuda.synchronize()
     clk = clocks.stop() if clocks else None
     ms_step = max_over_ranks(dist, statistics.mean(times), dev)
@@ -277,7 +282,7 @@ def measure_workload(torch, PL, dev, dim, n, steps, warmup, dist=None, full=Fals
     rho = [x for x in rho if x is not None]
     diag = {"s_work": DG.work_ratio(t_end, inner[-1], S), "rho_obs_max": max(rho) if rho else None,
             "rho_obs_steps": len(rho), "final_residual": per_step[-1][-1] if per_step else None}
-    s_1pct = t_ex / min(msc_once(best1["S"], best1["eps"])[0] for _ in range(3)) if best1 else None
+    s_1pct = t_ex / min(msc_once(best1["S"], best1["eps"], best1["nmin"])[0] for _ in range(3)) if best1 else None
     res = {
         "workload": f"{'D2Q9' if dim == 2 else 'D3Q19'} periodic N={n} Re=1 random-phase seed {w['seed']} "
                     f"{precision.upper()} storage",
@@ -312,7 +317,7 @@ def measure_workload(torch, PL, dev, dim, n, steps, warmup, dist=None, full=Fals
             torch.cuda.synchronize()
             return e0.elapsed_time(e1)
 
-        L.set_params(dt=t_end / S, eps=best["eps"], kmax=KMAX, nmin=w["nmin"])
+        L.set_params(dt=t_end / S, eps=best["eps"], kmax=KMAX, nmin=best["nmin"])
         t_msc_e2e = statistics.mean(e2e(lambda: L.march(S)) for _ in range(3))
         t_ex_e2e = e2e(lambda: L.explicit_march(t_end))
         bytes_io = (dim + 1) * n ** dim * 8
@@ -330,6 +335,9 @@ BATCH_NS = (128, 256, 512)
 BATCH_RES = [float(r) for r in np.logspace(-4, 2, 16)]
 BATCH_S = [8, 16, 32, 64, 128, 256, 512]
 BATCH_EPS = [1e-6, 1e-8, 1e-10, 1e-12]
+# per-instance candidates (S, eps, n_min): every S with every eps at n_min = 2, and every S at n_min = 4
+# with the loose eps (acceptance then at exactly four sweeps)
+BATCH_CANDIDATES = [(S, eps, 2) for S in BATCH_S for eps in BATCH_EPS] + [(S, BATCH_EPS[0], 4) for S in BATCH_S]
 
 
 def batch_instances():
@@ -398,14 +406,14 @@ def measure_batch(torch, PL, dev, refs_async=None, reps=3):
     e_ex = [velocity_error(a, r) for a, r in zip(u_ex, refs)]
 
     def set_all(choice):
-        for L, d, (S, eps) in zip(lats, insts, choice):
-            L.set_params(dt=d["t_end"] / S, eps=eps, kmax=KMAX, nmin=2)
+        for L, d, (S, eps, nmin) in zip(lats, insts, choice):
+            L.set_params(dt=d["t_end"] / S, eps=eps, kmax=KMAX, nmin=nmin)
 
     def run(choice):
         set_all(choice)
         ms = timed(lambda: B.march([c[0] for c in choice]))
         out = []
-        for L, d, r, (S, eps) in zip(lats, insts, refs, choice):
+        for L, d, r, (S, eps, nmin) in zip(lats, insts, refs, choice):
             st = L.stats()
             ok = st["status"] == 0 and st["steps_done"] == S
             if ok:
@@ -414,17 +422,16 @@ def measure_batch(torch, PL, dev, refs_async=None, reps=3):
                 rel = e / max(rms_vector(uu), 1e-300)
             else:
                 e = rel = float("inf")
-            out.append(dict(S=S, eps=eps, ok=ok, err=e, rel=rel, inner=st["inner_total"]))
+            out.append(dict(S=S, eps=eps, nmin=nmin, ok=ok, err=e, rel=rel, inner=st["inner_total"]))
         return ms, out
 
     # candidate matrix over the whole batch; per instance the cheapest passing candidate (work proxy:
     # inner sweeps plus one step end per physical step, in site updates)
     table = [[] for _ in insts]
-    for S in BATCH_S:
-        for eps in BATCH_EPS:
-            _, out = run([(S, eps)] * len(insts))
-            for k, o in enumerate(out):
-                table[k].append(o)
+    for cand in BATCH_CANDIDATES:
+        _, out = run([cand] * len(insts))
+        for k, o in enumerate(out):
+            table[k].append(o)
 
     def pick(gate):
         choice, npass = [], 0
@@ -436,7 +443,7 @@ def measure_batch(torch, PL, dev, refs_async=None, reps=3):
             else:  # no candidate meets the gate: the most accurate one that converged
                 conv = [o for o in table[k] if o["ok"]] or table[k]
                 best = min(conv, key=lambda o: o["err"])
-            choice.append((best["S"], best["eps"]))
+            choice.append((best["S"], best["eps"], best["nmin"]))
         return choice, npass
 
     res = {"workload": "48 D2Q9 periodic instances, N in {128,256,512} x Re = logspace(-4,2,16), random-phase "
@@ -456,7 +463,7 @@ def measure_batch(torch, PL, dev, refs_async=None, reps=3):
         res[name] = {"s_wall": t_ex / ms, "t_msc_ms": ms, "instances_passing": npass,
                      "all_converged": all(o["ok"] for o in out),
                      "inner_mlups": inner_sites / (ms * 1e3),
-                     "per_instance": [{"n": d["n"], "Re": d["Re"], "S": o["S"], "eps": o["eps"],
+                     "per_instance": [{"n": d["n"], "Re": d["Re"], "S": o["S"], "eps": o["eps"], "nmin": o["nmin"],
                                        "inner": o["inner"], "rel": o["rel"]} for d, o in zip(insts, out)]}
     # per-Re single-instance ratio at N = 256 (the 1%-gate candidates), as in the paper's Re sweep
     sweep256 = []
@@ -466,8 +473,8 @@ def measure_batch(torch, PL, dev, refs_async=None, reps=3):
             continue
         L = lats[k]
         p_d, u_d, _ = fields[k]
-        S, eps = choice1[k]
-        L.set_params(dt=d["t_end"] / S, eps=eps, kmax=KMAX, nmin=2)
+        S, eps, nmin = choice1[k]
+        L.set_params(dt=d["t_end"] / S, eps=eps, kmax=KMAX, nmin=nmin)
 
         def one(fn):
             L.init_fields(p_d, u_d)
@@ -732,13 +739,13 @@ def run_phase(args):
     n, dim = args.n, args.dim
     if dim == 3:  # the D3Q19 workload and its timed candidate
         w = WORKLOADS[(3, n)]
-        S, eps = DEFAULT_CANDIDATE_3D
+        S, eps, nmin = DEFAULT_CANDIDATE_3D
         p, u = random_phase(n, 3, 1.0, seed=w["seed"], kmax=w["kmax"])
-        t_end, nmin = w["t_end"], w["nmin"]
+        t_end = w["t_end"]
     else:
-        S, eps = DEFAULT_CANDIDATE.get(n, (64, 1e-8))
+        S, eps, nmin = DEFAULT_CANDIDATE.get(n, (64, 1e-8, 2))
         p, u = random_phase(n, 2, 1.0, seed=1, kmax=8)
-        t_end, nmin = nint(0.15 * n * n), 2
+        t_end = nint(0.15 * n * n)
     p_d = torch.as_tensor(p, device=dev)
     u_d = torch.as_tensor(u, device=dev)
     L = PL.MscLattice(dim, n, "fp32", max_steps=4096, device="cuda:0")
@@ -859,13 +866,13 @@ def kernel_hash():
 # the FP64 CPU oracle on a bounded sample (cpu_baseline and --impl reference)
 # ---------------------------------------------------------------------------------------------------
 
-def oracle_sample(n, S, eps, msc_steps=1, explicit_steps=3):
+def oracle_sample(n, S, eps, nmin=2, msc_steps=1, explicit_steps=3):
     """Seconds per MSC physical step and per explicit step of the oracle at this workload."""
     from oracle import march as OM
     from oracle.lattice import D2Q9
     p, u = random_phase(n, 2, 1.0, seed=1, kmax=8)
     t_end = nint(0.15 * n * n)
-    prm = OM.MarchParams(dt=t_end / S, eps=eps, kmax=KMAX, nmin=2)
+    prm = OM.MarchParams(dt=t_end / S, eps=eps, kmax=KMAX, nmin=nmin, warm_order=2, count_multiple=2)
     st = OM.init_state(D2Q9, p, u)
     OM.physical_step(st, prm)  # the BDF1 starter (untimed)
     t0 = time.perf_counter()
@@ -901,10 +908,10 @@ def run_reference(args):
     from oracle.shadow import shadow_correction
     from oracle.sweep import residual, sweep
     n = args.n
-    S, eps = DEFAULT_CANDIDATE.get(n, (64, 1e-8))
+    S, eps, nmin = DEFAULT_CANDIDATE.get(n, (64, 1e-8, 2))
     p, u = random_phase(n, 2, 1.0, seed=1, kmax=8)
     t_end = nint(0.15 * n * n)
-    prm = OM.MarchParams(dt=t_end / S, eps=eps, kmax=KMAX, nmin=2)
+    prm = OM.MarchParams(dt=t_end / S, eps=eps, kmax=KMAX, nmin=nmin, warm_order=2, count_multiple=2)
     st = OM.init_state(D2Q9, p, u)
     OM.physical_step(st, prm)  # BDF1 starter
     probe = OM.DualTimeState(D2Q9, list(st.f_hist), st.m_n.copy(), st.m_nm1.copy(), st.steps_done)
@@ -940,7 +947,7 @@ def run_reference(args):
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"D2Q9 periodic N={n} Re=1 random-phase seed 1 (FP64 oracle, CPU)", "N": n,
-                   "S": S, "eps": eps, "T_end": t_end, "inner_iterations_per_step": iters,
+                   "S": S, "eps": eps, "nmin": nmin, "T_end": t_end, "inner_iterations_per_step": iters,
                    "step": "one oracle MSC inner iteration (+ one explicit step)"},
         "cpu_baseline": {"value": val, "unit": "x", "cores": cpu_cores(), "kind": "oracle", "sample": sample},
         # the oracle's time to solution, in the unit of the GPU arm's e2e (ms), so that the two e2e values
@@ -991,7 +998,7 @@ def contract_line(res, cpu, args, world, warm_order=2, count_multiple=2) -> str:
         "config": {"workload": f"D2Q9 periodic N={args.n} Re=1 nu=1/6 random-phase (k^-2, 1<=|k|<=8, seed 1), "
                                "FP32 deviation storage, FP64 BDF history and per-wavenumber solve",
                    "N": args.n, "Re": 1.0, "T_end": res["t_end"], "S": cand["S"], "eps": cand["eps"],
-                   "dt": res["t_end"] / cand["S"], "kmax": KMAX, "nmin": 2, "warm_order": warm_order,
+                   "dt": res["t_end"] / cand["S"], "kmax": KMAX, "nmin": cand["nmin"], "warm_order": warm_order,
                    "count_multiple": count_multiple, "step": "one full MSC-LBM march to T_end",
                    "l2": "working set > L2; 256 MB flush between timed steps",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -1078,12 +1085,12 @@ def main():
         return
     cpu = None
     if not args.no_cpu_baseline:
-        S, eps = res["candidate"]["S"], res["candidate"]["eps"]
-        t_msc_step, t_ex_step, it, t_end = oracle_sample(args.n, S, eps, msc_steps=1, explicit_steps=2)
+        S, eps, nmin = res["candidate"]["S"], res["candidate"]["eps"], res["candidate"]["nmin"]
+        t_msc_step, t_ex_step, it, t_end = oracle_sample(args.n, S, eps, nmin, msc_steps=1, explicit_steps=2)
         t_or_msc = t_msc_step * S
         t_or_ex = t_ex_step * t_end
         cpu = {"value": t_or_ex / t_or_msc, "unit": "x", "cores": cpu_cores(), "kind": "oracle",
-               "sample": f"1 MSC physical step (S={S}, eps={eps}, {it} inner iterations) and 2 explicit steps "
+               "sample": f"1 MSC physical step (S={S}, eps={eps}, nmin={nmin}, {it} inner iterations) and 2 explicit steps "
                          f"of the FP64 numpy oracle at N={args.n}, extrapolated to S steps and T_end={t_end}",
                "oracle_time_to_solution_s": t_or_msc, "oracle_explicit_s": t_or_ex}
     print(contract_line(res, cpu, args, world))

@@ -69,7 +69,7 @@ def test_candidate_selection_gates_and_fallback():
 
 def _stub_result(matched):
     inf = float("inf")
-    cand = dict(S=512, eps=1e-10, ms=90.0, err=1.6e-10, rel=8e-6, ok=True, inner=2048)
+    cand = dict(S=512, eps=1e-10, nmin=2, ms=90.0, err=1.6e-10, rel=8e-6, ok=True, inner=2048)
     return {
         "candidate": cand, "candidate_1pct": dict(cand, S=8), "t_end": 157286,
         "s_wall_matched": 22.0 if matched else None, "s_wall_timed": 22.0, "s_wall_1pct": 1400.0,

@@ -337,11 +337,11 @@ def test_count_multiple_free_run_fp64():
     assert rel_l2(host(L.fields()[1]), st.m_n[1:]) < 1e-8
 
 
-def _fp32_horizon_parity(N, S, steps, eps):
+def _fp32_horizon_parity(N, S, steps, eps, nmin=2):
     # Table protocol T_end = nint(0.15 N^2), dt = T_end / S, the FP32 D2Q9 defaults (linear warm start,
     # inner sweeps in pairs) on both sides; the GPU replays the oracle's accepted inner counts
     p, u = random_phase(N, 2, 1.0, seed=1)
-    prm = OM.MarchParams(dt=nint(0.15 * N * N) / S, eps=eps, nmin=2, warm_order=2, count_multiple=2)
+    prm = OM.MarchParams(dt=nint(0.15 * N * N) / S, eps=eps, nmin=nmin, warm_order=2, count_multiple=2)
     st = OM.init_state(lattice_for_dim(2), p, u)
     recs = OM.march(st, prm, steps)
     assert all(r.converged for r in recs)
@@ -349,17 +349,24 @@ def _fp32_horizon_parity(N, S, steps, eps):
     s = L.stats()
     assert s["status"] == 0 and s["steps_done"] == steps
     err = rel_l2(host(L.fields()[1]), st.m_n[1:])
-    print(f"FP32 storage vs FP64 oracle, D2Q9 N={N}, dt=T_end/{S}, {steps} steps: rel L2(u) = {err:.2e} (gate 1e-5)")
+    print(f"FP32 storage vs FP64 oracle, D2Q9 N={N}, dt=T_end/{S}, n_min={nmin}, {steps} steps: "
+          f"rel L2(u) = {err:.2e} (gate 1e-5)")
     return err
 
 
 def test_fp32_full_horizon_n256_matches_oracle():
-    # The N = 256 workload over its whole horizon: S = 256 physical steps to T_end = 9830 at the
-    # timed candidate's step (eps = 1e-6), 1e-5 relative L2 in u against the FP64 oracle
-    assert _fp32_horizon_parity(256, 256, 256, 1e-6) < 1e-5
+    # The N = 256 workload over its whole horizon at the timed candidate: S = 192 physical steps to
+    # T_end = 9830 (eps = 1e-6, n_min = 2), 1e-5 relative L2 in u against the FP64 oracle
+    assert _fp32_horizon_parity(256, 192, 192, 1e-6) < 1e-5
 
 
 def test_fp32_n1024_many_steps_match_oracle():
-    # The N = 1024 benchmark workload at the timed step dt = T_end / 512 over the BDF1 starter and
-    # 17 BDF2 steps (eps = 1e-10), 1e-5 relative L2 in u against the FP64 oracle
+    # The N = 1024 benchmark workload at the timed candidate, dt = T_end / 384 with n_min = 4 (four
+    # sweeps per step, eps = 1e-8), over the BDF1 starter and 17 BDF2 steps: 1e-5 relative L2 in u
+    # against the FP64 oracle
+    assert _fp32_horizon_parity(1024, 384, 18, 1e-8, nmin=4) < 1e-5
+
+
+def test_fp32_n1024_two_sweep_candidate_matches_oracle():
+    # the two-sweep candidate of the same workload (dt = T_end / 512, eps = 1e-10, n_min = 2)
     assert _fp32_horizon_parity(1024, 512, 18, 1e-10) < 1e-5

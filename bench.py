@@ -50,7 +50,7 @@ KMAX = 300
 # matched-gate candidate of the GPU candidate search at N = 1024 and at N = 256
 DEFAULT_CANDIDATE = {1024: (384, 1e-8, 4), 256: (192, 1e-6, 2)}
 # the D3Q19 workload's (N = 128) matched-gate candidate, for the profiling phases
-DEFAULT_CANDIDATE_3D = (32, 1e-10, 1)
+DEFAULT_CANDIDATE_3D = (32, 1e-6, 4)
 # the march's D2Q9 sweep: f in/out, h as a binary32 pair, lifted dm, P r
 SWEEP_BYTES_PER_SITE_FP32 = 2 * 9 * 4 + 2 * 3 * 4 + 3 * 4 + 3 * 4
 SWEEP_BYTES_PER_SITE_FP16 = 2 * 9 * 2 + 2 * 3 * 4 + 3 * 4 + 3 * 4  # binary16 f in/out, FP32 h pair, dm, P r
@@ -64,7 +64,8 @@ WORKLOADS = {
                     steps=None),
     (2, 256): dict(seed=1, kmax=8, t_end=nint(0.15 * 256 ** 2), nmins=NMIN_2D, S=S_LIST, eps=EPS_LIST, M=64,
                    steps=None),
-    (3, 128): dict(seed=7, kmax=6, t_end=nint(0.075 * 128 ** 2), nmins=[1], S=[3, 4, 5, 8, 16, 32, 64, 128, 256, 512],
+    (3, 128): dict(seed=7, kmax=6, t_end=nint(0.075 * 128 ** 2), nmins=[1, 4],
+                   S=[3, 4, 5, 8, 16, 24, 32, 48, 64, 128, 256, 512],
                    eps=EPS_LIST, M=32, steps=100),
 }
 

@@ -40,7 +40,7 @@ NU = 1.0 / 6.0
 # physical steps per march searched by the candidate matrix (Table protocol, with bracket extensions
 # beyond 256 and between the powers of two there): the long end is needed by the matched gate at N = 1024,
 # where the explicit LBM is accurate to 1.5e-6 relative
-S_LIST = [4, 8, 16, 32, 64, 128, 192, 256, 320, 384, 512, 768, 1024, 1536, 2048, 4096]
+S_LIST = [4, 8, 16, 32, 64, 128, 192, 256, 320, 352, 384, 448, 512, 768, 1024, 1536, 2048, 4096]
 # n_min of Algorithm 1 searched with S and eps (D2Q9): 2, and 4 (four converged sweeps per step
 # make each step more accurate, so that fewer, larger steps meet the matched gate)
 NMIN_2D = [2, 4]
@@ -48,7 +48,7 @@ EPS_LIST = [1e-6, 1e-8, 1e-10]
 KMAX = 300
 # candidate (S, eps, n_min) the reference arm (and the single-phase profiling aids) use: the fastest
 # matched-gate candidate of the GPU candidate search at N = 1024 and at N = 256
-DEFAULT_CANDIDATE = {1024: (384, 1e-8, 4), 256: (192, 1e-6, 2)}
+DEFAULT_CANDIDATE = {1024: (352, 1e-8, 4), 256: (192, 1e-6, 2)}
 # the D3Q19 workload's (N = 128) matched-gate candidate, for the profiling phases
 DEFAULT_CANDIDATE_3D = (32, 1e-6, 4)
 # the march's D2Q9 sweep: f in/out, h as a binary32 pair, lifted dm, P r

@@ -361,10 +361,10 @@ def test_fp32_full_horizon_n256_matches_oracle():
 
 
 def test_fp32_n1024_many_steps_match_oracle():
-    # The N = 1024 benchmark workload at the timed candidate, dt = T_end / 384 with n_min = 4 (four
+    # The N = 1024 benchmark workload at the timed candidate, dt = T_end / 352 with n_min = 4 (four
     # sweeps per step, eps = 1e-8), over the BDF1 starter and 17 BDF2 steps: 1e-5 relative L2 in u
     # against the FP64 oracle
-    assert _fp32_horizon_parity(1024, 384, 18, 1e-8, nmin=4) < 1e-5
+    assert _fp32_horizon_parity(1024, 352, 18, 1e-8, nmin=4) < 1e-5
 
 
 def test_fp32_n1024_two_sweep_candidate_matches_oracle():

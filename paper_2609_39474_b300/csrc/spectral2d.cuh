@@ -251,24 +251,29 @@ __global__ void __launch_bounds__(kFftThreads) k_rowfft_inv_acc(Spec2Args<T> A) 
 }
 
 // Schur solve at one masked wavevector in FP64: dp = A rp - i B (k.rm), du = Dv rm - i Cc k dp
-template <typename C, int D>
+// ICVT: the binary32 <-> binary64 conversions on the integer pipe (widen_f32 / narrow_f64, the same
+// values): where the solve holds the FP64 pipe (the warp-per-line column pass at N = 1024, the 3D z
+// pass) that takes 12 of its ~30 FP64-pipe instructions per mode off it
+template <typename C, int D, bool ICVT = false>
 __device__ __forceinline__ void schur_apply(C* v[D + 1], const double* kv, const double* cf) {
     using T = decltype(v[0]->x);
+    auto wide = [](T x) { return ICVT ? to_f64<T>(x) : (double)x; };
+    auto narrow = [](double x) { return ICVT ? from_f64<T>(x) : (T)x; };
     double rx[D + 1], ry[D + 1];
 #pragma unroll
-    for (int i = 0; i <= D; ++i) { rx[i] = (double)v[i]->x; ry[i] = (double)v[i]->y; }
+    for (int i = 0; i <= D; ++i) { rx[i] = wide(v[i]->x); ry[i] = wide(v[i]->y); }
     double krx = 0.0, kry = 0.0;
 #pragma unroll
     for (int al = 0; al < D; ++al) { krx += kv[al] * rx[al + 1]; kry += kv[al] * ry[al + 1]; }
     const double dpx = cf[0] * rx[0] + cf[1] * kry;
     const double dpy = cf[0] * ry[0] - cf[1] * krx;
-    v[0]->x = (T)dpx;
-    v[0]->y = (T)dpy;
+    v[0]->x = narrow(dpx);
+    v[0]->y = narrow(dpy);
 #pragma unroll
     for (int al = 0; al < D; ++al) {
         const double ck = cf[2] * kv[al];
-        v[al + 1]->x = (T)(cf[3] * rx[al + 1] + ck * dpy);
-        v[al + 1]->y = (T)(cf[3] * ry[al + 1] - ck * dpx);
+        v[al + 1]->x = narrow(cf[3] * rx[al + 1] + ck * dpy);
+        v[al + 1]->y = narrow(cf[3] * ry[al + 1] - ck * dpx);
     }
 }
 
@@ -299,7 +304,7 @@ __device__ __forceinline__ void schur_apply_adjoint(C* v[D + 1], const double* k
 
 // The Schur solve of one (j_x, j_y) mode of the column pass in place on its three field values v
 // (zero outside the mask |j_y| <= n/4 or for a column past the last kept one)
-template <typename T, bool ADJ>
+template <typename T, bool ADJ, bool ICVT = false>
 __device__ __forceinline__ void solve_mode(const Spec2Args<T>& A, typename Cplx<T>::type* v[3], int jx, int jy,
                                            bool live, double a, const double* tab) {
     using C = typename Cplx<T>::type;
@@ -321,7 +326,7 @@ __device__ __forceinline__ void solve_mode(const Spec2Args<T>& A, typename Cplx<
         solve_coefficients(a, A.nu, kv[0] * kv[0] + kv[1] * kv[1], A.nscale, cf);
     }
     if (ADJ) schur_apply_adjoint<C, 2>(v, kv, cf);
-    else schur_apply<C, 2>(v, kv, cf);
+    else schur_apply<C, 2, ICVT>(v, kv, cf);
 }
 
 // 2D: G consecutive kept j_x columns per block (G a power of two; the last block of a lattice may
@@ -423,7 +428,7 @@ __global__ void __launch_bounds__(96) k_colsolve_1024(Spec2Args<float> A) {
     const double* tab = solve_table(A.coef, A.st, 2, n);
     for (int jy = threadIdx.x; jy < n; jy += blockDim.x) {
         C* w[3] = {s + pad(jy), s + plen + pad(jy), s + 2 * plen + pad(jy)};
-        solve_mode<float, false>(A, w, jx, jy, true, a, tab);
+        solve_mode<float, false, true>(A, w, jx, jy, true, a, tab);
     }
     __syncthreads();
 #pragma unroll

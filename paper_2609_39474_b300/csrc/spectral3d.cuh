@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 384 : 768) k_zsolve(Spec2Args
         } else {
             solve_coefficients(a, A.nu, kv[0] * kv[0] + kv[1] * kv[1] + kv[2] * kv[2], scale, cf);
         }
-        schur_apply<C, 3>(v, kv, cf);
+        schur_apply<C, 3, true>(v, kv, cf);
     }
     __syncthreads();
     fft_stockham<C, true>(s, n, logn, 4 * G, A.tw);

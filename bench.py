@@ -250,8 +250,8 @@ def measure_workload(torch, PL, dev, dim, n, steps, warmup, dist=None, full=Fals
     if not converged:
         raise RuntimeError(f"no MSC candidate converged (dim {dim}, N {n})")
     if not matched_ok:  # reported, not hidden: the matched value is then null
-        sys.stderr.write(f"no MSC candidate passes the matched-accuracy gate (dim {dim}, N {n}); "
-                         "timing the most accurate converged candidate\n")
+        sys.stderr.write(f"no MSC candidate passes the matched-accuracy gate (dim {dim}, N {n}, "
+                         f"{precision.upper()} storage); timing the most accurate converged candidate\n")
 
     # -- timed region: K full marches of the matched winner --------------------------------------
     clocks = ClockSampler(dev.index)  # secondary workloads keep theirs in the details
@@ -724,7 +724,8 @@ def run_phase(args):
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     if args.phase == "sweep3":
-        return {"phase": "sweep3", **sweep3_time(torch, PL, dev, reps=args.steps)}
+        n3 = args.n if 8 <= args.n <= 256 else 128  # --n when it is a D3Q19 FP32 size, else the C4 lattice
+        return {"phase": "sweep3", **sweep3_time(torch, PL, dev, n=n3, reps=args.steps)}
     if args.phase == "sweep":
         return {"phase": "sweep", **sweep_time(torch, PL, dev, ROOF_N, reps=args.steps, precision=args.precision)}
     if args.phase == "batch-stage":
@@ -1056,7 +1057,7 @@ def main():
                          "48-instance batched parameter sweep, 'batch-stage' the batch's kernels timed one "
                          "family at a time (stateless, visible to ncu), 'adjoint' the config-5 gradient, "
                          "'adjoint-stepwise' 16 steps of it driven from the host (visible to ncu), 'sweep3' the "
-                         "D3Q19 FP32 sweep at N = 128")
+                         "D3Q19 FP32 sweep at N = 128 (at --n when that is at most 256)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
 

@@ -46,6 +46,7 @@ struct msc_ctx {
     cudaGraphExec_t x_ex;
     cudaGraphExec_t x_adj[2];  // transposed solve of one adjoint step, BDF1 and BDF2
     int sweep_blocks;
+    int march_prefix;  // straight-line inner iterations per step in the march graph
 };
 
 namespace {
@@ -287,14 +288,17 @@ cudaGraphNode_t add_cond(cudaGraph_t g, const std::vector<cudaGraphNode_t>& deps
 }
 
 // spectral correction nodes: 2D forward row FFT, column FFT + solve + inverse, inverse row FFT;
-// 3D the five passes of spectral3d.cuh.  All take the same argument block.
+// 3D the five passes of spectral3d.cuh.  All take the same argument block.  The first pass follows
+// prev (if any) on a programmatic edge; gate: the passes check that the sweep before them asked for
+// the correction (graph nodes outside a conditional node).  Returns the last pass.
 template <typename T>
-void add_spectral_nodes(msc_ctx* c, cudaGraph_t g, cudaError_t* err) {
+cudaGraphNode_t add_spectral_nodes(msc_ctx* c, cudaGraph_t g, cudaGraphNode_t prev, int gate, cudaError_t* err) {
     using C = typename Cplx<T>::type;
     const int n = c->desc.n;
     Spec2Args<T> S = spec3_args<T>(n, c->logn, 0.0, c->params.nu, at<T>(c, c->lay.pr), at<C>(c, c->lay.spec),
                                    at<T>(c, c->lay.dm), at<C>(c, c->lay.tw), at<DevState>(c, c->lay.state),
                                    at<double>(c, c->lay.coef));
+    S.gate = gate;
     void* args[] = {&S};
     if (c->desc.dim == 2) {
         S.nf = 3;
@@ -302,19 +306,55 @@ void add_spectral_nodes(msc_ctx* c, cudaGraph_t g, cudaError_t* err) {
         S.nscale = 1.0 / ((double)n * n);
         Spec2Launch L[3];
         S.P = spectral2_launches<T>(n, L);
-        cudaGraphNode_t n1 = add_kernel(g, {}, L[0].fn, L[0].grid, L[0].block, L[0].smem, args, err);
-        cudaGraphNode_t n2 = add_kernel_after(g, n1, L[1].fn, L[1].grid, L[1].block, L[1].smem, args, err);
-        add_kernel_after(g, n2, L[2].fn, L[2].grid, L[2].block, L[2].smem, args, err);
+        for (int i = 0; i < 3; ++i)
+            prev = prev ? add_kernel_after(g, prev, L[i].fn, L[i].grid, L[i].block, L[i].smem, args, err)
+                        : add_kernel(g, {}, L[i].fn, L[i].grid, L[i].block, L[i].smem, args, err);
     } else {
         LaunchDesc L[5];
         spectral3_launches<T>(n, L);
-        cudaGraphNode_t prev = nullptr;
         for (int i = 0; i < 5; ++i) {
             spec3_pass_args<T>(n, &S, i);  // node parameters are copied when the node is added
             prev = prev ? add_kernel_after(g, prev, L[i].fn, L[i].grid, L[i].block, L[i].smem, args, err)
                         : add_kernel(g, {}, L[i].fn, L[i].grid, L[i].block, L[i].smem, args, err);
         }
     }
+    return prev;
+}
+
+// The first n_min - 1 inner iterations of a step can never be accepted (Algorithm 1: l >= n_min), so
+// the march graph runs them as straight-line nodes ahead of the conditional inner loop: no loop or
+// branch node per iteration, and programmatic edges from each sweep into its correction and on into
+// the next sweep.  Replay mode (the counts are given) keeps every iteration inside the loop.
+constexpr int kMaxMarchPrefix = 7;
+inline int march_prefix_count(const msc_params& p) {
+    if (p.replay) return 0;
+    return p.nmin - 1 < 0 ? 0 : (p.nmin - 1 > kMaxMarchPrefix ? kMaxMarchPrefix : p.nmin - 1);
+}
+
+// the march's sweep as a graph node in g (after prev on a programmatic edge, if given); cond as in
+// Sweep2Args (1: inside the inner loop, 2: before it)
+template <class L, typename T, typename FS>
+cudaGraphNode_t add_sweep_node(msc_ctx* c, cudaGraph_t g, cudaGraphNode_t prev, cudaGraphConditionalHandle h_iter,
+                               cudaGraphConditionalHandle h_corr, int cond, cudaError_t* err) {
+    if (L::D == 2) {
+        Sweep2Args<T, FS> A = sweep2_args_graph<T, FS>(c);
+        A.h_iter = h_iter;
+        A.h_corr = h_corr;
+        A.cond = cond;
+        void* a_sw[] = {&A};
+        const void* fn = sweep2_kernel<T, FS, false, true>(c);
+        const dim3 grid(sweep2_geometry(c->desc.n).blocks), block(kSweepWarps * 32);
+        return prev ? add_kernel_after(g, prev, fn, grid, block, 0, a_sw, err)
+                    : add_kernel(g, {}, fn, grid, block, 0, a_sw, err);
+    }
+    Sweep3PArgs<T> A = sweep3p_args_graph<T>(c);
+    A.h_iter = h_iter;
+    A.h_corr = h_corr;
+    A.cond = cond;
+    void* a_sw[] = {&A};
+    const void* fn = (const void*)k_sweep3p<T, true>;
+    return prev ? add_kernel_after(g, prev, fn, dim3(A.g.blocks), dim3(kP3Threads), A.g.smem, a_sw, err)
+                : add_kernel(g, {}, fn, dim3(A.g.blocks), dim3(kP3Threads), A.g.smem, a_sw, err);
 }
 
 template <typename T>
@@ -375,8 +415,18 @@ int build_march_graph(msc_ctx* c) {
     // previous step's k_step_finish_graph), acceptance with the next step's h and trial, then the
     // history rotation and both loop conditions
     CK(cudaGraphConditionalHandleCreate(&h_iter, body_step, 1u, cudaGraphCondAssignDefault));
+    const int npre = march_prefix_count(c->params);
+    cudaGraphNode_t pre = nullptr;
+    for (int i = 0; i < npre; ++i) {
+        pre = add_sweep_node<L, T, FS>(c, body_step, pre, h_iter, 0, 2, &err);
+        pre = add_spectral_nodes<T>(c, body_step, pre, 1, &err);
+    }
+    if (err != cudaSuccess) { cudaGraphDestroy(g); return MSC_ERR_CUDA; }
+    c->march_prefix = npre;
     cudaGraph_t body_iter;
-    cudaGraphNode_t wit = add_cond(body_step, {}, h_iter, cudaGraphCondTypeWhile, &body_iter, &err);
+    std::vector<cudaGraphNode_t> wdeps;
+    if (pre) wdeps.push_back(pre);
+    cudaGraphNode_t wit = add_cond(body_step, wdeps, h_iter, cudaGraphCondTypeWhile, &body_iter, &err);
     if (err != cudaSuccess) { cudaGraphDestroy(g); return MSC_ERR_CUDA; }
     void* a_end[] = {&st, &fbase, (void*)&fstride, &mbuf, &h, &sites, &pfbase, &pfstride};
     cudaGraphNode_t end = add_kernel(body_step, {wit}, step_end_kernel<L, T, FS>(c), dim3(fgrid),
@@ -385,28 +435,11 @@ int build_march_graph(msc_ctx* c) {
     add_kernel_after(body_step, end, (const void*)k_step_finish_graph, dim3(1), dim3(1), 0, a_fin, &err);
 
     CK(cudaGraphConditionalHandleCreate(&h_corr, body_iter, 0, 0));
-    cudaGraphNode_t sw;
-    if (L::D == 2) {
-        Sweep2Args<T, FS> A = sweep2_args_graph<T, FS>(c);
-        A.h_iter = h_iter;
-        A.h_corr = h_corr;
-        A.cond = 1;
-        void* a_sw[] = {&A};
-        sw = add_kernel(body_iter, {}, sweep2_kernel<T, FS, false, true>(c), dim3(sweep2_geometry(c->desc.n).blocks),
-                        dim3(kSweepWarps * 32), 0, a_sw, &err);
-    } else {
-        Sweep3PArgs<T> A = sweep3p_args_graph<T>(c);
-        A.h_iter = h_iter;
-        A.h_corr = h_corr;
-        A.cond = 1;
-        void* a_sw[] = {&A};
-        sw = add_kernel(body_iter, {}, (const void*)k_sweep3p<T, true>, dim3(A.g.blocks), dim3(kP3Threads), A.g.smem,
-                        a_sw, &err);
-    }
+    cudaGraphNode_t sw = add_sweep_node<L, T, FS>(c, body_iter, nullptr, h_iter, h_corr, 1, &err);
     cudaGraph_t body_corr;
     add_cond(body_iter, {sw}, h_corr, cudaGraphCondTypeIf, &body_corr, &err);
     if (err != cudaSuccess) { cudaGraphDestroy(g); return MSC_ERR_CUDA; }
-    add_spectral_nodes<T>(c, body_corr, &err);
+    add_spectral_nodes<T>(c, body_corr, nullptr, 0, &err);
     if (err != cudaSuccess) { cudaGraphDestroy(g); return MSC_ERR_CUDA; }
 
     cudaGraphExec_t x;
@@ -727,7 +760,9 @@ int msc_set_params(msc_ctx* c, const msc_params* p) {
     // the shadow solve bakes nu into the graph, the collision kind picks the sweep kernel: rebuild
     const bool kind_changes = c->params_set && (params_trt(*p) != params_trt(c->params) ||
                                                 params_force(*p) != params_force(c->params));
-    if (c->params_set && (p->nu != c->params.nu || kind_changes) && c->x_march) {
+    // so do n_min and replay, which set the straight-line iterations of each step
+    const bool prefix_changes = c->x_march && march_prefix_count(*p) != c->march_prefix;
+    if (c->params_set && (p->nu != c->params.nu || kind_changes || prefix_changes) && c->x_march) {
         cudaGraphExecDestroy(c->x_march);
         cudaGraphDestroy(c->g_march);
         c->x_march = nullptr;

@@ -39,7 +39,16 @@ struct Spec2Args {
     double nscale;       // 1 / N_Omega (formed on the host)
     const DevState* st;  // graph mode: a and q from the state
     const double* coef;  // per-mode solve coefficients (k_solve_tables): for q = 1, 2 with st, else one table
+    int gate;            // graph mode outside a conditional node: run only if the sweep asked for it
 };
+
+// A correction that the march graph runs unconditionally (after a sweep that the acceptance rule
+// cannot accept: fewer than n_min inner iterations) returns at once when that sweep asked for none
+// (corrector off) or the march stopped with an error.
+template <typename T>
+__device__ __forceinline__ bool spec_gated_off(const Spec2Args<T>& A) {
+    return A.gate && !(A.st->lift && A.st->status == MSC_OK);
+}
 
 // pick the coefficient table of the current BDF order (graph mode), the table the caller chose
 // (no state), or none (stage calls)
@@ -153,6 +162,8 @@ __device__ __forceinline__ void rowfft_fwd_block(const Spec2Args<T>& A, int bid)
 
 template <typename T, bool N4 = false>
 __global__ void __launch_bounds__(kFftThreads) k_rowfft_fwd(Spec2Args<T> A) {
+    wait_for_predecessor();
+    if (spec_gated_off(A)) return;
     rowfft_fwd_block<T, N4>(A, blockIdx.x);
 }
 
@@ -241,6 +252,7 @@ __device__ __forceinline__ void rowfft_inv_block(const Spec2Args<T>& A, int bid)
 template <typename T, bool N4 = false>
 __global__ void __launch_bounds__(kFftThreads) k_rowfft_inv(Spec2Args<T> A) {
     wait_for_predecessor();
+    if (spec_gated_off(A)) return;
     rowfft_inv_block<T, false, N4>(A, blockIdx.x);
 }
 
@@ -377,6 +389,7 @@ __device__ __forceinline__ void colsolve_block(const Spec2Args<T>& A, int bid, i
 template <typename T, bool N4 = false>
 __global__ void __launch_bounds__(sizeof(T) == 8 ? 384 : 768) k_colsolve(Spec2Args<T> A) {
     wait_for_predecessor();
+    if (spec_gated_off(A)) return;
     colsolve_block<T, false, N4>(A, blockIdx.x, 1);
 }
 
@@ -407,6 +420,7 @@ inline size_t spec2_col_smem(int n) {
 // column pass at N = 1024: warp c transforms field c of kept column j_x = blockIdx.x
 __global__ void __launch_bounds__(96) k_colsolve_1024(Spec2Args<float> A) {
     wait_for_predecessor();
+    if (spec_gated_off(A)) return;
     using C = float2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* s = reinterpret_cast<C*>(smem_raw);

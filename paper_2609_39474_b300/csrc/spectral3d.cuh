@@ -54,6 +54,7 @@ inline RowGeom row_geometry3(int n) {
 template <typename T, bool INV>
 __global__ void __launch_bounds__(kFftThreads) k_ypass(Spec2Args<T> A) {
     wait_for_predecessor();
+    if (spec_gated_off(A)) return;
     using C = typename Cplx<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* s = reinterpret_cast<C*>(smem_raw);
@@ -86,6 +87,7 @@ __global__ void __launch_bounds__(kFftThreads) k_ypass(Spec2Args<T> A) {
 template <typename T>
 __global__ void __launch_bounds__(sizeof(T) == 8 ? 384 : 768) k_zsolve(Spec2Args<T> A) {
     wait_for_predecessor();
+    if (spec_gated_off(A)) return;
     using C = typename Cplx<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* s = reinterpret_cast<C*>(smem_raw);  // line (c, g) at (c G + g) plen

@@ -48,7 +48,7 @@ struct Sweep2Args {
     const int* replay_counts;
     int max_steps;
     cudaGraphConditionalHandle h_iter, h_corr;
-    int cond;  // set the graph conditionals (0 when the march is driven from the host)
+    int cond;  // graph conditionals: 1 both, 2 the loop handle only, 0 when driven from the host
     // explicit graph mode: 0 = a->b, 1 = b->a; ex_count: decrement the pair counter
     int ex_dir, ex_count;
     cudaGraphConditionalHandle h_ex;
@@ -89,9 +89,9 @@ __device__ inline void march_after_sweep(DevState* st, double total, double qsit
         corr = st->corrector;
     }
     st->lift = corr;
-    if (cond) {
+    if (cond) {  // 1: both handles (inside the inner loop); 2: the loop handle only (before it)
         cudaGraphSetConditional(h_iter, cont);
-        cudaGraphSetConditional(h_corr, corr);
+        if (cond == 1) cudaGraphSetConditional(h_corr, corr);
     }
 }
 
@@ -307,7 +307,12 @@ __device__ __forceinline__ double sweep2_unit(const S* fin, const T* dm, const T
 template <typename T, typename S, bool EXPLICIT, bool GRAPH, bool TRT = false,
           bool HPAIR = GRAPH && !EXPLICIT && std::is_same<T, float>::value>
 __global__ void __launch_bounds__(kSweepWarps * 32, sizeof(T) == 4 && !TRT ? 5 : 1) k_sweep2(Sweep2Args<T, S> A) {
-    if constexpr (EXPLICIT && GRAPH) wait_for_predecessor();  // the explicit graph chains its steps on programmatic edges
+    // the graphs chain the explicit steps, and the march's corrections and the sweeps that follow
+    // them, on programmatic edges
+    if constexpr (GRAPH) wait_for_predecessor();
+    if constexpr (GRAPH && !EXPLICIT) {
+        if (A.st->status != MSC_OK) return;  // the march stopped (a sweep outside the conditional loop)
+    }
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int n = A.n;

@@ -150,7 +150,9 @@ __global__ void __launch_bounds__(kP3Threads, sizeof(T) == 4 ? 4 : 1) k_sweep3p(
     T a = (T)A.a, inv = (T)A.inv;
     int lift = A.lift;
     if (GRAPH) {
+        wait_for_predecessor();  // a sweep that follows a correction on a programmatic edge
         const DevState* vs = A.st;
+        if (vs->status != MSC_OK) return;  // the march stopped (a sweep outside the conditional loop)
         fin = A.fbase + (size_t)vs->slot_cur * A.fstride;
         fout = A.fbase + (size_t)vs->slot_nxt * A.fstride;
         pfin = A.pfbase + (size_t)vs->slot_cur * A.pfstride;

@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(kSweepWarps * 32) k_bsweep2(const BInst<T>* __
                 *B.ucount = 0u;
                 if (MODE == 0)
                     march_after_sweep(B.st, s, 9.0 * (double)B.sites, A.hist, A.hist_cap, A.replay_counts, A.max_steps,
-                                      0, 0, 0);
+                                      0, 0);
                 else
                     *B.t_sumsq = s;
             }

@@ -600,14 +600,11 @@ __global__ void k_step_finish(DevState* st, int* iters_out, int max_steps,
     if (cond) cudaGraphSetConditional(h_step, go);
 }
 
-// the march graph's step end: the step loop's condition, and the inner loop of the next step
-// opened (the first step of a launch opens it through the handle's default value)
-__global__ void k_step_finish_graph(DevState* st, int* iters_out, int max_steps, cudaGraphConditionalHandle h_step,
-                                    cudaGraphConditionalHandle h_iter) {
+// the march graph's step end: the step loop's condition
+__global__ void k_step_finish_graph(DevState* st, int* iters_out, int max_steps, cudaGraphConditionalHandle h_step) {
     wait_for_predecessor();
     const unsigned int go = step_finish(st, iters_out, max_steps);
     cudaGraphSetConditional(h_step, go);
-    cudaGraphSetConditional(h_iter, 1u);
 }
 
 // m^n = P f^n of the accepted slot into both moment slots (after an explicit march)

@@ -290,7 +290,7 @@ cudaGraphNode_t add_cond(cudaGraph_t g, const std::vector<cudaGraphNode_t>& deps
 // spectral correction nodes: 2D forward row FFT, column FFT + solve + inverse, inverse row FFT;
 // 3D the five passes of spectral3d.cuh.  All take the same argument block.  The first pass follows
 // prev (if any) on a programmatic edge; gate: the passes check that the sweep before them asked for
-// the correction (graph nodes outside a conditional node).  Returns the last pass.
+// the correction (the march graph has no branch node for it).  Returns the last pass.
 template <typename T>
 cudaGraphNode_t add_spectral_nodes(msc_ctx* c, cudaGraph_t g, cudaGraphNode_t prev, int gate, cudaError_t* err) {
     using C = typename Cplx<T>::type;
@@ -322,25 +322,24 @@ cudaGraphNode_t add_spectral_nodes(msc_ctx* c, cudaGraph_t g, cudaGraphNode_t pr
 }
 
 // The first n_min - 1 inner iterations of a step can never be accepted (Algorithm 1: l >= n_min), so
-// the march graph runs them as straight-line nodes ahead of the conditional inner loop: no loop or
-// branch node per iteration, and programmatic edges from each sweep into its correction and on into
-// the next sweep.  Replay mode (the counts are given) keeps every iteration inside the loop.
+// the march graph runs them as straight-line nodes ahead of the conditional inner loop: no loop node
+// per iteration, and programmatic edges from each sweep into its correction and on into the next
+// sweep.  Replay mode (the counts are given) runs only the first sweep ahead of the loop.
 constexpr int kMaxMarchPrefix = 7;
 inline int march_prefix_count(const msc_params& p) {
     if (p.replay) return 0;
     return p.nmin - 1 < 0 ? 0 : (p.nmin - 1 > kMaxMarchPrefix ? kMaxMarchPrefix : p.nmin - 1);
 }
 
-// the march's sweep as a graph node in g (after prev on a programmatic edge, if given); cond as in
-// Sweep2Args (1: inside the inner loop, 2: before it)
+// the march's sweep as a graph node in g (after prev on a programmatic edge, if given); it sets the
+// inner loop's condition h_iter to "not accepted"
 template <class L, typename T, typename FS>
 cudaGraphNode_t add_sweep_node(msc_ctx* c, cudaGraph_t g, cudaGraphNode_t prev, cudaGraphConditionalHandle h_iter,
-                               cudaGraphConditionalHandle h_corr, int cond, cudaError_t* err) {
+                               cudaError_t* err) {
     if (L::D == 2) {
         Sweep2Args<T, FS> A = sweep2_args_graph<T, FS>(c);
         A.h_iter = h_iter;
-        A.h_corr = h_corr;
-        A.cond = cond;
+        A.cond = 1;
         void* a_sw[] = {&A};
         const void* fn = sweep2_kernel<T, FS, false, true>(c);
         const dim3 grid(sweep2_geometry(c->desc.n).blocks), block(kSweepWarps * 32);
@@ -349,8 +348,7 @@ cudaGraphNode_t add_sweep_node(msc_ctx* c, cudaGraph_t g, cudaGraphNode_t prev, 
     }
     Sweep3PArgs<T> A = sweep3p_args_graph<T>(c);
     A.h_iter = h_iter;
-    A.h_corr = h_corr;
-    A.cond = cond;
+    A.cond = 1;
     void* a_sw[] = {&A};
     const void* fn = (const void*)k_sweep3p<T, true>;
     return prev ? add_kernel_after(g, prev, fn, dim3(A.g.blocks), dim3(kP3Threads), A.g.smem, a_sw, err)
@@ -398,7 +396,7 @@ int build_march_graph(msc_ctx* c) {
 
     // prologue: arm the step loop, set up the first step and form its h and trial; every later
     // step is set up by the previous step's k_step_finish_graph, its h and trial formed by k_step_end
-    cudaGraphConditionalHandle h_step, h_iter, h_corr;
+    cudaGraphConditionalHandle h_step, h_iter;
     CK(cudaGraphConditionalHandleCreate(&h_step, g, 0, 0));
     void* a_arm[] = {&st, &h_step};
     cudaGraphNode_t arm = add_kernel(g, {}, (const void*)k_arm_setup, dim3(1), dim3(1), 0, a_arm, &err);
@@ -411,35 +409,31 @@ int build_march_graph(msc_ctx* c) {
     add_cond(g, {begin}, h_step, cudaGraphCondTypeWhile, &body_step, &err);
     if (err != cudaSuccess) { cudaGraphDestroy(g); return MSC_ERR_CUDA; }
 
-    // one physical step: the inner loop (opened by the default value at launch, then by the
-    // previous step's k_step_finish_graph), acceptance with the next step's h and trial, then the
-    // history rotation and both loop conditions
-    CK(cudaGraphConditionalHandleCreate(&h_iter, body_step, 1u, cudaGraphCondAssignDefault));
+    // one physical step: the inner iterations that cannot be accepted, straight-line; the next sweep;
+    // then, while the last sweep was not accepted, its correction and another sweep (every sweep sets
+    // h_iter); acceptance with the next step's h and trial; the history rotation and the step loop's
+    // condition
+    CK(cudaGraphConditionalHandleCreate(&h_iter, body_step, 0u, cudaGraphCondAssignDefault));
     const int npre = march_prefix_count(c->params);
     cudaGraphNode_t pre = nullptr;
     for (int i = 0; i < npre; ++i) {
-        pre = add_sweep_node<L, T, FS>(c, body_step, pre, h_iter, 0, 2, &err);
+        pre = add_sweep_node<L, T, FS>(c, body_step, pre, h_iter, &err);
         pre = add_spectral_nodes<T>(c, body_step, pre, 1, &err);
     }
+    pre = add_sweep_node<L, T, FS>(c, body_step, pre, h_iter, &err);
     if (err != cudaSuccess) { cudaGraphDestroy(g); return MSC_ERR_CUDA; }
     c->march_prefix = npre;
     cudaGraph_t body_iter;
-    std::vector<cudaGraphNode_t> wdeps;
-    if (pre) wdeps.push_back(pre);
-    cudaGraphNode_t wit = add_cond(body_step, wdeps, h_iter, cudaGraphCondTypeWhile, &body_iter, &err);
+    cudaGraphNode_t wit = add_cond(body_step, {pre}, h_iter, cudaGraphCondTypeWhile, &body_iter, &err);
     if (err != cudaSuccess) { cudaGraphDestroy(g); return MSC_ERR_CUDA; }
     void* a_end[] = {&st, &fbase, (void*)&fstride, &mbuf, &h, &sites, &pfbase, &pfstride};
     cudaGraphNode_t end = add_kernel(body_step, {wit}, step_end_kernel<L, T, FS>(c), dim3(fgrid),
                                      dim3(kFieldThreads), 0, a_end, &err);
-    void* a_fin[] = {&st, &iters, &max_steps, &h_step, &h_iter};
+    void* a_fin[] = {&st, &iters, &max_steps, &h_step};
     add_kernel_after(body_step, end, (const void*)k_step_finish_graph, dim3(1), dim3(1), 0, a_fin, &err);
 
-    CK(cudaGraphConditionalHandleCreate(&h_corr, body_iter, 0, 0));
-    cudaGraphNode_t sw = add_sweep_node<L, T, FS>(c, body_iter, nullptr, h_iter, h_corr, 1, &err);
-    cudaGraph_t body_corr;
-    add_cond(body_iter, {sw}, h_corr, cudaGraphCondTypeIf, &body_corr, &err);
-    if (err != cudaSuccess) { cudaGraphDestroy(g); return MSC_ERR_CUDA; }
-    add_spectral_nodes<T>(c, body_corr, nullptr, 0, &err);
+    cudaGraphNode_t cor = add_spectral_nodes<T>(c, body_iter, nullptr, 1, &err);
+    add_sweep_node<L, T, FS>(c, body_iter, cor, h_iter, &err);
     if (err != cudaSuccess) { cudaGraphDestroy(g); return MSC_ERR_CUDA; }
 
     cudaGraphExec_t x;

@@ -47,8 +47,8 @@ struct Sweep2Args {
     int hist_cap;
     const int* replay_counts;
     int max_steps;
-    cudaGraphConditionalHandle h_iter, h_corr;
-    int cond;  // graph conditionals: 1 both, 2 the loop handle only, 0 when driven from the host
+    cudaGraphConditionalHandle h_iter;
+    int cond;  // set the inner loop's graph conditional (0 when the march is driven from the host)
     // explicit graph mode: 0 = a->b, 1 = b->a; ex_count: decrement the pair counter
     int ex_dir, ex_count;
     cudaGraphConditionalHandle h_ex;
@@ -57,8 +57,7 @@ struct Sweep2Args {
 // Decide acceptance after the residual norm of inner iteration l is known (Algorithm 1).
 __device__ inline void march_after_sweep(DevState* st, double total, double qsites, double* hist,
                                          int hist_cap, const int* replay_counts, int max_steps,
-                                         cudaGraphConditionalHandle h_iter,
-                                         cudaGraphConditionalHandle h_corr, int cond) {
+                                         cudaGraphConditionalHandle h_iter, int cond) {
     const double R = sqrt(total / qsites);
     const int ell = st->iter + 1;
     st->iter = ell;
@@ -89,10 +88,7 @@ __device__ inline void march_after_sweep(DevState* st, double total, double qsit
         corr = st->corrector;
     }
     st->lift = corr;
-    if (cond) {  // 1: both handles (inside the inner loop); 2: the loop handle only (before it)
-        cudaGraphSetConditional(h_iter, cont);
-        if (cond == 1) cudaGraphSetConditional(h_corr, corr);
-    }
+    if (cond) cudaGraphSetConditional(h_iter, cont);  // another inner iteration (correction, sweep)
 }
 
 // One warp unit of the sweep: output columns [strip*30, strip*30 + 30) of rows [rb*hb, rb*hb + hb).
@@ -311,7 +307,7 @@ __global__ void __launch_bounds__(kSweepWarps * 32, sizeof(T) == 4 && !TRT ? 5 :
     // them, on programmatic edges
     if constexpr (GRAPH) wait_for_predecessor();
     if constexpr (GRAPH && !EXPLICIT) {
-        if (A.st->status != MSC_OK) return;  // the march stopped (a sweep outside the conditional loop)
+        if (A.st->status != MSC_OK) return;  // the march stopped (sweeps outside the conditional loop)
     }
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -390,7 +386,7 @@ __global__ void __launch_bounds__(kSweepWarps * 32, sizeof(T) == 4 && !TRT ? 5 :
         *A.counter = 0u;
         if (GRAPH) {
             march_after_sweep(A.st, total, 9.0 * (double)NN, A.hist, A.hist_cap, A.replay_counts,
-                              A.max_steps, A.h_iter, A.h_corr, A.cond);
+                              A.max_steps, A.h_iter, A.cond);
         } else {
             *A.sumsq_out = total;
         }

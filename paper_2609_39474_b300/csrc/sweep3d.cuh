@@ -45,7 +45,7 @@ struct Sweep3Args {
     int hist_cap;
     const int* replay_counts;
     int max_steps;
-    cudaGraphConditionalHandle h_iter, h_corr;
+    cudaGraphConditionalHandle h_iter;
     int cond;
     int ex_dir, ex_count;
     cudaGraphConditionalHandle h_ex;
@@ -270,7 +270,7 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 256 : 512) k_sweep3(Sweep3Arg
         *A.counter = 0u;
         if (GRAPH) {
             march_after_sweep(A.st, total, 19.0 * (double)NNN, A.hist, A.hist_cap, A.replay_counts,
-                              A.max_steps, A.h_iter, A.h_corr, A.cond);
+                              A.max_steps, A.h_iter, A.cond);
         } else {
             *A.sumsq_out = total;
         }

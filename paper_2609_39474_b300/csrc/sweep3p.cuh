@@ -88,7 +88,7 @@ struct Sweep3PArgs {
     int hist_cap;
     const int* replay_counts;
     int max_steps;
-    cudaGraphConditionalHandle h_iter, h_corr;
+    cudaGraphConditionalHandle h_iter;
     int cond;
 };
 
@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(kP3Threads, sizeof(T) == 4 ? 4 : 1) k_sweep3p(
     if (GRAPH) {
         wait_for_predecessor();  // a sweep that follows a correction on a programmatic edge
         const DevState* vs = A.st;
-        if (vs->status != MSC_OK) return;  // the march stopped (a sweep outside the conditional loop)
+        if (vs->status != MSC_OK) return;  // the march stopped (sweeps outside the conditional loop)
         fin = A.fbase + (size_t)vs->slot_cur * A.fstride;
         fout = A.fbase + (size_t)vs->slot_nxt * A.fstride;
         pfin = A.pfbase + (size_t)vs->slot_cur * A.pfstride;
@@ -267,7 +267,7 @@ __global__ void __launch_bounds__(kP3Threads, sizeof(T) == 4 ? 4 : 1) k_sweep3p(
         *A.counter = 0u;
         if (GRAPH) {
             march_after_sweep(A.st, total, 19.0 * (double)NNN, A.hist, A.hist_cap, A.replay_counts, A.max_steps,
-                              A.h_iter, A.h_corr, A.cond);
+                              A.h_iter, A.cond);
         } else {
             *A.sumsq_out = total;
         }

@@ -37,7 +37,8 @@ CASES = [
     "tests/test_gpu_march.py::test_fp32_storage_against_fp64_oracle[3-16-4]",
     "tests/test_gpu_march.py::test_explicit_march_matches_oracle[fp32]",
     "tests/test_gpu_march.py::test_explicit_march_3d",
-    "tests/test_gpu_march.py::test_stepwise_march_equals_graph_march[2-64-fp64]",
+    "tests/test_gpu_march.py::test_stepwise_march_equals_graph_march[2-64-fp64-None-True-1e-09]",
+    "tests/test_gpu_march.py::test_stepwise_march_equals_graph_march[3-16-fp32-4-True-1e-09]",
     "tests/test_gpu_batch.py::test_batch_fp64_replay_matches_oracle",
 ]
 

@@ -278,19 +278,26 @@ def test_benchmark_configuration_matches_oracle(precision):
     assert rel_l2(host(uu), st.m_n[1:]) < (1e-5 if fp32 else 1e-12)
 
 
-@pytest.mark.parametrize("dim,N,precision", [(2, 64, "fp64"), (2, 128, "fp32"), (3, 16, "fp64")])
-def test_stepwise_march_equals_graph_march(dim, N, precision):
+@pytest.mark.parametrize("dim,N,precision,nmin,corrector,eps", [
+    (2, 64, "fp64", None, True, 1e-9), (2, 128, "fp32", None, True, 1e-9), (3, 16, "fp64", None, True, 1e-9),
+    # the graph runs the first n_min - 1 iterations of a step as straight-line nodes: three of them,
+    # in 2D and 3D, and with the corrector off (their correction passes then return at once)
+    (2, 64, "fp64", 4, True, 1e-9), (3, 16, "fp32", 4, True, 1e-9), (2, 32, "fp64", 3, False, 1e-6)])
+def test_stepwise_march_equals_graph_march(dim, N, precision, nmin, corrector, eps):
     # the host-driven march launches the same kernels: identical bits to the graph march
     p, u = random_phase(N, dim, 1.0, seed=21, kmax=4)
     out = []
     for stepwise in (False, True):
         L = _lattice(dim, N, precision)
-        L.set_params(dt=24.0, eps=1e-9)
+        L.set_params(dt=24.0 if corrector else 4.0, eps=eps, nmin=nmin, corrector=corrector, kmax=2000)
         L.init_fields(p, u)
         (L.march_stepwise if stepwise else L.march)(5)
         out.append((L.populations(), L.step_iters().tolist(), L.stats()))
+    assert out[0][2]["status"] == out[1][2]["status"] == 0
     assert np.array_equal(out[0][0], out[1][0])
     assert out[0][1] == out[1][1] and out[0][2]["steps_done"] == out[1][2]["steps_done"] == 5
+    if nmin:
+        assert min(out[0][1]) >= nmin
 
 
 def test_fp32_long_run_stays_at_a_few_iterations():

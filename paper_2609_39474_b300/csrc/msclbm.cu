@@ -1,6 +1,6 @@
 // C ABI of the MSC-LBM library: contexts, the device-resident march (CUDA graph with nested
-// conditional WHILE/IF nodes, so that the acceptance test of Algorithm 1 never leaves the
-// device), the explicit LBM baseline and the stage entry points.  See include/msclbm.h.
+// conditional WHILE nodes, so that the acceptance test of Algorithm 1 never leaves the device),
+// the explicit LBM baseline and the stage entry points.  See include/msclbm.h.
 #include <cmath>
 #include <cstddef>
 #include <cstdio>

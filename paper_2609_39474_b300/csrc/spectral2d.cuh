@@ -110,6 +110,24 @@ __device__ __forceinline__ void fft_lines(C* s, int n, int logn, int nfft, const
     else fft_stockham<C, INV>(s, n, logn, nfft, tw);
 }
 
+// 16-byte vectors of a row (4 binary32 or 2 binary64 values): the row passes move their rows with
+// one load or store per vector when the rows are 16-byte aligned (always in the march; a stage
+// call's arrays may not be, and then take the element loop)
+template <typename T> struct RowVec;
+template <> struct RowVec<float> { using type = float4; static constexpr int V = 4; };
+template <> struct RowVec<double> { using type = double2; static constexpr int V = 2; };
+template <typename VT> __device__ __forceinline__ auto vlane(const VT& v, int i) {
+    if constexpr (sizeof(v.x) == 4) return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
+    else return i == 0 ? v.x : v.y;
+}
+template <typename VT, typename S> __device__ __forceinline__ void vset(VT& v, int i, S x) {
+    if constexpr (sizeof(v.x) == 4) {
+        if (i == 0) v.x = x; else if (i == 1) v.y = x; else if (i == 2) v.z = x; else v.w = x;
+    } else {
+        if (i == 0) v.x = x; else v.y = x;
+    }
+}
+
 // 2P consecutive rows (c, y0 .. y0 + 2P - 1) form P complex rows
 template <typename T, bool N4 = false>
 __device__ __forceinline__ void rowfft_fwd_block(const Spec2Args<T>& A, int bid) {
@@ -123,18 +141,44 @@ __device__ __forceinline__ void rowfft_fwd_block(const Spec2Args<T>& A, int bid)
     const int c = pair0 / hr;
     const int y0 = 2 * (pair0 - c * hr);
     const T* rows = A.pr + ((size_t)c * A.rows + y0) * n;
-    // unrolled so that the global loads of several iterations are in flight together
+    using VT = typename RowVec<T>::type;
+    constexpr int V = RowVec<T>::V;
+    if ((reinterpret_cast<uintptr_t>(A.pr) & 15u) == 0) {
+        // one 16-byte load per row and vector; V consecutive x share one padded 16-block
+        const int lnv = logn - (V == 4 ? 2 : 1);
+        const int nv = 1 << lnv;
+#pragma unroll 4
+        for (int t = threadIdx.x; t < P * nv; t += blockDim.x) {
+            const int p = t >> lnv;
+            const int x = (t & (nv - 1)) * V;
+            if (!MSC_INB(((size_t)c * A.rows + y0 + 2 * p + 1) * n + x + V - 1, (size_t)A.nf * A.rows * n, 11) ||
+                !MSC_INB(p * plen + pad(x) + V - 1, P * plen, 12))
+                continue;
+            const VT ra = *reinterpret_cast<const VT*>(rows + (size_t)(2 * p) * n + x);
+            const VT rb = *reinterpret_cast<const VT*>(rows + (size_t)(2 * p + 1) * n + x);
+            C* d = s + p * plen + pad(x);
+#pragma unroll
+            for (int i = 0; i < V; ++i) {
+                C z;
+                z.x = vlane(ra, i);
+                z.y = vlane(rb, i);
+                d[i] = z;
+            }
+        }
+    } else {
+        // unrolled so that the global loads of several iterations are in flight together
 #pragma unroll 8
-    for (int t = threadIdx.x; t < P * n; t += blockDim.x) {
-        const int p = t >> logn;
-        const int x = t & (n - 1);
-        if (!MSC_INB(((size_t)c * A.rows + y0 + 2 * p + 1) * n + x, (size_t)A.nf * A.rows * n, 11) ||
-            !MSC_INB(p * plen + pad(x), P * plen, 12))
-            continue;
-        C z;
-        z.x = rows[(size_t)(2 * p) * n + x];
-        z.y = rows[(size_t)(2 * p + 1) * n + x];
-        s[p * plen + pad(x)] = z;
+        for (int t = threadIdx.x; t < P * n; t += blockDim.x) {
+            const int p = t >> logn;
+            const int x = t & (n - 1);
+            if (!MSC_INB(((size_t)c * A.rows + y0 + 2 * p + 1) * n + x, (size_t)A.nf * A.rows * n, 11) ||
+                !MSC_INB(p * plen + pad(x), P * plen, 12))
+                continue;
+            C z;
+            z.x = rows[(size_t)(2 * p) * n + x];
+            z.y = rows[(size_t)(2 * p + 1) * n + x];
+            s[p * plen + pad(x)] = z;
+        }
     }
     __syncthreads();
     fft_lines<C, false, N4>(s, n, logn, P, A.tw);
@@ -236,6 +280,29 @@ __device__ __forceinline__ void rowfft_inv_block(const Spec2Args<T>& A, int bid)
                     rows[o0 + n] = v1[u] + z.y;
                 }
             }
+        }
+        return;
+    }
+    using VT = typename RowVec<T>::type;
+    constexpr int V = RowVec<T>::V;
+    if ((reinterpret_cast<uintptr_t>(A.dm) & 15u) == 0) {
+        const int lnv = logn - (V == 4 ? 2 : 1);
+        const int nv = 1 << lnv;
+        for (int t = threadIdx.x; t < P * nv; t += blockDim.x) {
+            const int p = t >> lnv;
+            const int x = (t & (nv - 1)) * V;
+            if (!MSC_INB(((size_t)c * A.rows + y0 + 2 * p + 1) * n + x + V - 1, (size_t)A.nf * A.rows * n, 15))
+                continue;
+            const C* sp = s + p * plen + pad(x);
+            VT ra, rb;
+#pragma unroll
+            for (int i = 0; i < V; ++i) {
+                const C z = sp[i];
+                vset(ra, i, z.x);
+                vset(rb, i, z.y);
+            }
+            *reinterpret_cast<VT*>(rows + (size_t)(2 * p) * n + x) = ra;
+            *reinterpret_cast<VT*>(rows + (size_t)(2 * p + 1) * n + x) = rb;
         }
         return;
     }

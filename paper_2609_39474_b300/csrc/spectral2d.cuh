@@ -182,25 +182,31 @@ __device__ __forceinline__ void rowfft_fwd_block(const Spec2Args<T>& A, int bid)
     }
     __syncthreads();
     fft_lines<C, false, N4>(s, n, logn, P, A.tw);
-    // split the two real transforms; thread t -> (j_x, row r in 0..2P-1), r fastest
+    // split the two real transforms; thread t -> (j_x, pair p), p fastest: the pair's two rows
+    // 2p, 2p + 1 are adjacent in the transposed spectrum, one 16-byte store when aligned
     C* out = A.spec + (size_t)c * nx4 * A.rows + y0;
-    const int l2p = __ffs(2 * P) - 1;  // P is a power of two
-    for (int t = threadIdx.x; t < 2 * P * nx4; t += blockDim.x) {
-        const int r = t & (2 * P - 1);
-        const int jx = t >> l2p;
-        const int p = r >> 1;
+    const int lp = __ffs(P) - 1;  // P is a power of two
+    const bool vec = sizeof(C) == 8 && (reinterpret_cast<uintptr_t>(A.spec) & 15u) == 0;
+    for (int t = threadIdx.x; t < P * nx4; t += blockDim.x) {
+        const int p = t & (P - 1);
+        const int jx = t >> lp;
         const C zj = s[p * plen + pad(jx)];
         const C zm = s[p * plen + pad((n - jx) & (n - 1))];
-        C v;
-        if ((r & 1) == 0) {  // (zj + conj(zm)) / 2
-            v.x = T(0.5) * (zj.x + zm.x);
-            v.y = T(0.5) * (zj.y - zm.y);
-        } else {             // (zj - conj(zm)) / (2i)
-            v.x = T(0.5) * (zj.y + zm.y);
-            v.y = T(-0.5) * (zj.x - zm.x);
+        C va, vb;
+        va.x = T(0.5) * (zj.x + zm.x);   // (zj + conj(zm)) / 2
+        va.y = T(0.5) * (zj.y - zm.y);
+        vb.x = T(0.5) * (zj.y + zm.y);   // (zj - conj(zm)) / (2i)
+        vb.y = T(-0.5) * (zj.x - zm.x);
+        const size_t o = (size_t)jx * A.rows + 2 * p;
+        if (!MSC_INB((size_t)c * nx4 * A.rows + y0 + o + 1, (size_t)A.nf * nx4 * A.rows, 13)) continue;
+        if (vec) {
+            float4 w;
+            w.x = (float)va.x; w.y = (float)va.y; w.z = (float)vb.x; w.w = (float)vb.y;
+            *reinterpret_cast<float4*>(out + o) = w;
+        } else {
+            out[o] = va;
+            out[o + 1] = vb;
         }
-        if (MSC_INB((size_t)c * nx4 * A.rows + y0 + (size_t)jx * A.rows + r, (size_t)A.nf * nx4 * A.rows, 13))
-            out[(size_t)jx * A.rows + r] = v;
     }
 }
 
@@ -226,7 +232,9 @@ __device__ __forceinline__ void rowfft_inv_block(const Spec2Args<T>& A, int bid)
     const int y0 = 2 * (pair0 - c * hr);
     const C* in = A.spec + (size_t)c * nx4 * A.rows + y0;
     // Z[p][j] = Xa + i Xb (j <= n/4), conj(Xa[n-j]) + i conj(Xb[n-j]) (n-j <= n/4), else 0;
-    // thread t -> (j, p), p fastest, so the spectrum reads are contiguous in the row index
+    // thread t -> (j, p), p fastest, so the spectrum reads are contiguous in the row index (Xa, Xb
+    // adjacent: one 16-byte load when aligned)
+    const bool vec = sizeof(C) == 8 && (reinterpret_cast<uintptr_t>(A.spec) & 15u) == 0;
     const int lp = __ffs(P) - 1;
 #pragma unroll 8
     for (int t = threadIdx.x; t < P * n; t += blockDim.x) {
@@ -238,14 +246,23 @@ __device__ __forceinline__ void rowfft_inv_block(const Spec2Args<T>& A, int bid)
         if (!MSC_INB((size_t)c * nx4 * A.rows + y0 + (size_t)(jr <= n / 4 ? jr : 0) * A.rows + 2 * p + 1,
                      (size_t)A.nf * nx4 * A.rows, 14))
             continue;
-        if (j <= n / 4) {
-            const C xa = in[(size_t)j * A.rows + 2 * p], xb = in[(size_t)j * A.rows + 2 * p + 1];
-            z.x = xa.x - xb.y;
-            z.y = xa.y + xb.x;
-        } else if (n - j <= n / 4) {
-            const C xa = in[(size_t)(n - j) * A.rows + 2 * p], xb = in[(size_t)(n - j) * A.rows + 2 * p + 1];
-            z.x = xa.x + xb.y;
-            z.y = xb.x - xa.y;
+        if (jr <= n / 4) {
+            const size_t o = (size_t)jr * A.rows + 2 * p;
+            C xa, xb;
+            if (vec) {
+                const float4 w = *reinterpret_cast<const float4*>(in + o);
+                xa.x = w.x; xa.y = w.y; xb.x = w.z; xb.y = w.w;
+            } else {
+                xa = in[o];
+                xb = in[o + 1];
+            }
+            if (j <= n / 4) {
+                z.x = xa.x - xb.y;
+                z.y = xa.y + xb.x;
+            } else {
+                z.x = xa.x + xb.y;
+                z.y = xb.x - xa.y;
+            }
         }
         s[p * plen + pad(j)] = z;
     }

@@ -91,6 +91,36 @@ def test_shadow_solve_full_size_fp32():
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("dim,n", [(2, 256), (2, 1024), (3, 32)])
+def test_shadow_solve_unaligned_arrays_match_aligned(dim, n, precision):
+    # the row passes move 16-byte vectors of P r and dm when both arrays are 16-byte aligned and
+    # single elements otherwise: arrays one element off alignment give the same bits (and both
+    # match the oracle)
+    import ctypes
+    from paper_2609_39474_b300 import _lib as LB
+    PL = _lib()
+    shape = (n,) * dim
+    pr = random_moments(dim, shape, seed=9, scale=1e-6)
+    a, nu = 3.0 / (2 * 48.0), 1.0 / 6.0
+    T = PL.storage_dtype(precision)
+    pr_s = dev(pr, T)
+    dm0 = PL.shadow_solve(dim, n, precision, a, nu, pr_s)
+    k = pr_s.numel()
+    pb = torch.zeros(k + 1, dtype=T, device=pr_s.device)
+    pb[1:] = pr_s.reshape(-1)
+    db = torch.zeros(k + 1, dtype=T, device=pr_s.device)
+    assert pb[1:].data_ptr() % 16 != 0 and db[1:].data_ptr() % 16 != 0
+    sc = PL.StageScratch(dim, n, precision, pr_s.device)
+    rc = LB.lib.msc_shadow_solve(dim, n, PL.precision_code(precision), a, nu, ctypes.c_void_p(pb[1:].data_ptr()),
+                                 ctypes.c_void_p(db[1:].data_ptr()), ctypes.c_void_p(sc.buf.data_ptr()), sc.nbytes,
+                                 None)
+    assert rc == 0
+    torch.cuda.synchronize()
+    assert torch.equal(db[1:].reshape(dm0.shape), dm0)
+    assert rel_l2(host(dm0), OS.shadow_dm(host(pr_s), a, nu)) < (1e-13 if precision == "fp64" else 2e-6)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
 @pytest.mark.parametrize("dim,n", [(2, 16), (3, 8)])
 def test_equilibrium_matches_oracle(dim, n, precision):
     PL = _lib()

@@ -283,7 +283,7 @@ __device__ __forceinline__ void step_end_range(const DevState* __restrict__ st, 
                                                size_t sites, size_t i0, size_t istride, S* __restrict__ pfbase = nullptr,
                                                size_t pfstride = 0) {
     const DevState* vs = st;
-    if (!vs->accepted) return;
+    if (!vs->accepted || vs->steps_target <= 0) return;  // no accepted step of this march to finish
     const double inv = vs->inv_a;
     const size_t mstride = (size_t)(L::D + 1) * sites;
     const bool next = vs->status == MSC_OK && vs->steps_target > 1;
@@ -600,9 +600,12 @@ __global__ void k_step_finish(DevState* st, int* iters_out, int max_steps,
     if (cond) cudaGraphSetConditional(h_step, go);
 }
 
-// the march graph's step end: the step loop's condition
+// the march graph's step end: the step loop's condition.  The second step of the graph's unrolled
+// pair finds no live step when the first was the march's last, and leaves the condition as that
+// step set it.
 __global__ void k_step_finish_graph(DevState* st, int* iters_out, int max_steps, cudaGraphConditionalHandle h_step) {
     wait_for_predecessor();
+    if (st->steps_target <= 0) return;
     const unsigned int go = step_finish(st, iters_out, max_steps);
     cudaGraphSetConditional(h_step, go);
 }

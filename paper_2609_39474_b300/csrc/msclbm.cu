@@ -326,6 +326,9 @@ cudaGraphNode_t add_spectral_nodes(msc_ctx* c, cudaGraph_t g, cudaGraphNode_t pr
 // per iteration, and programmatic edges from each sweep into its correction and on into the next
 // sweep.  Replay mode (the counts are given) runs only the first sweep ahead of the loop.
 constexpr int kMaxMarchPrefix = 7;
+// physical steps per iteration of the march graph's step loop (one loop node and one ordinary edge
+// into the next step's first sweep per pair instead of per step)
+constexpr int kMarchStepsPerLoop = 2;
 inline int march_prefix_count(const msc_params& p) {
     if (p.replay) return 0;
     return p.nmin - 1 < 0 ? 0 : (p.nmin - 1 > kMaxMarchPrefix ? kMaxMarchPrefix : p.nmin - 1);
@@ -409,32 +412,36 @@ int build_march_graph(msc_ctx* c) {
     add_cond(g, {begin}, h_step, cudaGraphCondTypeWhile, &body_step, &err);
     if (err != cudaSuccess) { cudaGraphDestroy(g); return MSC_ERR_CUDA; }
 
-    // one physical step: the inner iterations that cannot be accepted, straight-line; the next sweep;
-    // then, while the last sweep was not accepted, its correction and another sweep (every sweep sets
-    // h_iter); acceptance with the next step's h and trial; the history rotation and the step loop's
-    // condition
-    CK(cudaGraphConditionalHandleCreate(&h_iter, body_step, 0u, cudaGraphCondAssignDefault));
+    // kMarchStepsPerLoop physical steps per iteration of the step loop (a step after the march's last
+    // one finds no live step: its kernels return at once).  One physical step: the inner iterations
+    // that cannot be accepted, straight-line; the next sweep; then, while the last sweep was not
+    // accepted, its correction and another sweep (every sweep sets the step's inner-loop handle);
+    // acceptance with the next step's h and trial; the history rotation and the step loop's condition
     const int npre = march_prefix_count(c->params);
-    cudaGraphNode_t pre = nullptr;
-    for (int i = 0; i < npre; ++i) {
-        pre = add_sweep_node<L, T, FS>(c, body_step, pre, h_iter, &err);
-        pre = add_spectral_nodes<T>(c, body_step, pre, 1, &err);
-    }
-    pre = add_sweep_node<L, T, FS>(c, body_step, pre, h_iter, &err);
-    if (err != cudaSuccess) { cudaGraphDestroy(g); return MSC_ERR_CUDA; }
     c->march_prefix = npre;
-    cudaGraph_t body_iter;
-    cudaGraphNode_t wit = add_cond(body_step, {pre}, h_iter, cudaGraphCondTypeWhile, &body_iter, &err);
-    if (err != cudaSuccess) { cudaGraphDestroy(g); return MSC_ERR_CUDA; }
-    void* a_end[] = {&st, &fbase, (void*)&fstride, &mbuf, &h, &sites, &pfbase, &pfstride};
-    cudaGraphNode_t end = add_kernel(body_step, {wit}, step_end_kernel<L, T, FS>(c), dim3(fgrid),
-                                     dim3(kFieldThreads), 0, a_end, &err);
-    void* a_fin[] = {&st, &iters, &max_steps, &h_step};
-    add_kernel_after(body_step, end, (const void*)k_step_finish_graph, dim3(1), dim3(1), 0, a_fin, &err);
+    cudaGraphNode_t prev = nullptr;
+    for (int k = 0; k < kMarchStepsPerLoop; ++k) {
+        CK(cudaGraphConditionalHandleCreate(&h_iter, body_step, 0u, cudaGraphCondAssignDefault));
+        cudaGraphNode_t pre = prev;
+        for (int i = 0; i < npre; ++i) {
+            pre = add_sweep_node<L, T, FS>(c, body_step, pre, h_iter, &err);
+            pre = add_spectral_nodes<T>(c, body_step, pre, 1, &err);
+        }
+        pre = add_sweep_node<L, T, FS>(c, body_step, pre, h_iter, &err);
+        if (err != cudaSuccess) { cudaGraphDestroy(g); return MSC_ERR_CUDA; }
+        cudaGraph_t body_iter;
+        cudaGraphNode_t wit = add_cond(body_step, {pre}, h_iter, cudaGraphCondTypeWhile, &body_iter, &err);
+        if (err != cudaSuccess) { cudaGraphDestroy(g); return MSC_ERR_CUDA; }
+        void* a_end[] = {&st, &fbase, (void*)&fstride, &mbuf, &h, &sites, &pfbase, &pfstride};
+        cudaGraphNode_t end = add_kernel(body_step, {wit}, step_end_kernel<L, T, FS>(c), dim3(fgrid),
+                                         dim3(kFieldThreads), 0, a_end, &err);
+        void* a_fin[] = {&st, &iters, &max_steps, &h_step};
+        prev = add_kernel_after(body_step, end, (const void*)k_step_finish_graph, dim3(1), dim3(1), 0, a_fin, &err);
 
-    cudaGraphNode_t cor = add_spectral_nodes<T>(c, body_iter, nullptr, 1, &err);
-    add_sweep_node<L, T, FS>(c, body_iter, cor, h_iter, &err);
-    if (err != cudaSuccess) { cudaGraphDestroy(g); return MSC_ERR_CUDA; }
+        cudaGraphNode_t cor = add_spectral_nodes<T>(c, body_iter, nullptr, 1, &err);
+        add_sweep_node<L, T, FS>(c, body_iter, cor, h_iter, &err);
+        if (err != cudaSuccess) { cudaGraphDestroy(g); return MSC_ERR_CUDA; }
+    }
 
     cudaGraphExec_t x;
     if (cudaGraphInstantiate(&x, g, 0) != cudaSuccess) { cudaGraphDestroy(g); return MSC_ERR_CUDA; }

@@ -44,10 +44,10 @@ struct Spec2Args {
 
 // A correction that the march graph runs unconditionally (after a sweep that the acceptance rule
 // cannot accept: fewer than n_min inner iterations) returns at once when that sweep asked for none
-// (corrector off) or the march stopped with an error.
+// (corrector off), the march stopped with an error, or no step is live.
 template <typename T>
 __device__ __forceinline__ bool spec_gated_off(const Spec2Args<T>& A) {
-    return A.gate && !(A.st->lift && A.st->status == MSC_OK);
+    return A.gate && !(A.st->lift && A.st->status == MSC_OK && A.st->steps_target > 0);
 }
 
 // pick the coefficient table of the current BDF order (graph mode), the table the caller chose

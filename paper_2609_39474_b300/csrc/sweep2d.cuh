@@ -307,7 +307,13 @@ __global__ void __launch_bounds__(kSweepWarps * 32, sizeof(T) == 4 && !TRT ? 5 :
     // them, on programmatic edges
     if constexpr (GRAPH) wait_for_predecessor();
     if constexpr (GRAPH && !EXPLICIT) {
-        if (A.st->status != MSC_OK) return;  // the march stopped (sweeps outside the conditional loop)
+        // no live step: the march stopped with an error (sweeps outside the conditional loop), or
+        // its last step is done (the second step of the graph's unrolled pair); the step's inner
+        // loop stays closed
+        if (A.st->status != MSC_OK || A.st->steps_target <= 0) {
+            if (A.cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(A.h_iter, 0u);
+            return;
+        }
     }
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;

@@ -152,7 +152,10 @@ __global__ void __launch_bounds__(kP3Threads, sizeof(T) == 4 ? 4 : 1) k_sweep3p(
     if (GRAPH) {
         wait_for_predecessor();  // a sweep that follows a correction on a programmatic edge
         const DevState* vs = A.st;
-        if (vs->status != MSC_OK) return;  // the march stopped (sweeps outside the conditional loop)
+        if (vs->status != MSC_OK || vs->steps_target <= 0) {  // no live step (as the D2Q9 sweep)
+            if (A.cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(A.h_iter, 0u);
+            return;
+        }
         fin = A.fbase + (size_t)vs->slot_cur * A.fstride;
         fout = A.fbase + (size_t)vs->slot_nxt * A.fstride;
         pfin = A.pfbase + (size_t)vs->slot_cur * A.pfstride;

@@ -64,22 +64,47 @@ __global__ void __launch_bounds__(kFftThreads) k_ypass(Spec2Args<T> A) {
     const int line0 = blockIdx.x * G;         // (c * nx4 + jx) * n + z0, G divides n
     C* base = A.spec + (size_t)line0 * n;     // G contiguous lines of length n
     (void)zch;
-#pragma unroll 8
-    for (int t = threadIdx.x; t < G * n; t += blockDim.x) {
-        const int g = t >> logn;
-        const int y = t & (n - 1);
-        C z;
-        z.x = T(0); z.y = T(0);
+    // binary32: two consecutive y per thread, one 16-byte access (the lines are contiguous and the
+    // spectrum 16-byte aligned; y even keeps both in one padded 16-block of s)
+    constexpr bool VEC = sizeof(C) == 8;
+    const int lv = VEC ? 1 : 0;
+    auto kept = [&](int y) {
         const int ys = y <= n / 2 ? y : y - n;
-        if (!INV || (ys <= n / 4 && ys >= -(n / 4))) z = base[t];
-        s[g * plen + pad(y)] = z;
+        return !INV || (ys <= n / 4 && ys >= -(n / 4));
+    };
+#pragma unroll 8
+    for (int t = threadIdx.x; t < (G * n >> lv); t += blockDim.x) {
+        const int e = t << lv;  // first element
+        const int g = e >> logn;
+        const int y = e & (n - 1);
+        if constexpr (VEC) {
+            const bool k0 = kept(y), k1 = kept(y + 1);
+            float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (k0 || k1) w = *reinterpret_cast<const float4*>(base + e);
+            C z0, z1;
+            z0.x = k0 ? w.x : T(0); z0.y = k0 ? w.y : T(0);
+            z1.x = k1 ? w.z : T(0); z1.y = k1 ? w.w : T(0);
+            s[g * plen + pad(y)] = z0;
+            s[g * plen + pad(y) + 1] = z1;
+        } else {
+            C z;
+            z.x = T(0); z.y = T(0);
+            if (kept(y)) z = base[e];
+            s[g * plen + pad(y)] = z;
+        }
     }
     __syncthreads();
     fft_stockham<C, INV>(s, n, logn, G, A.tw);
-    for (int t = threadIdx.x; t < G * n; t += blockDim.x) {
-        const int g = t >> logn;
-        const int y = t & (n - 1);
-        base[t] = s[g * plen + pad(y)];
+    for (int t = threadIdx.x; t < (G * n >> lv); t += blockDim.x) {
+        const int e = t << lv;
+        const int g = e >> logn;
+        const int y = e & (n - 1);
+        if constexpr (VEC) {
+            const C z0 = s[g * plen + pad(y)], z1 = s[g * plen + pad(y) + 1];
+            *reinterpret_cast<float4*>(base + e) = make_float4(z0.x, z0.y, z1.x, z1.y);
+        } else {
+            base[e] = s[g * plen + pad(y)];
+        }
     }
 }
 

@@ -440,15 +440,27 @@ __device__ __forceinline__ void colsolve_block(const Spec2Args<T>& A, int bid, i
     const int gn = 1 << lgn;
     C* col = A.spec + (size_t)jx0 * n;  // spec[c][jx0 + g][y] at col + c * nx4 * n + g * n + y
     const size_t fs = (size_t)nx4 * n;
+    // binary32: two consecutive y per thread, one 16-byte access (y even: one padded 16-block of s)
+    constexpr int lv = sizeof(C) == 8 ? 1 : 0;
 #pragma unroll 4
-    for (int t = threadIdx.x; t < 3 * gn; t += blockDim.x) {
-        const int c = t >> lgn;
-        const int gy = t & (gn - 1);  // g * n + y
-        C v;
-        v.x = T(0); v.y = T(0);
-        if ((gy >> logn) < ng && MSC_INB((size_t)jx0 * n + c * fs + gy, (size_t)A.nf * fs, 16)) v = col[c * fs + gy];
-        if (MSC_INB((c * G + (gy >> logn)) * plen + pad(gy & (n - 1)), 3 * G * plen, 17))
-            s[(c * G + (gy >> logn)) * plen + pad(gy & (n - 1))] = v;
+    for (int t = threadIdx.x; t < (3 * gn >> lv); t += blockDim.x) {
+        const int e = t << lv;
+        const int c = e >> lgn;
+        const int gy = e & (gn - 1);  // g * n + y
+        const bool in = (gy >> logn) < ng && MSC_INB((size_t)jx0 * n + c * fs + gy + lv, (size_t)A.nf * fs, 16);
+        const int si = (c * G + (gy >> logn)) * plen + pad(gy & (n - 1));
+        if (!MSC_INB(si + lv, 3 * G * plen, 17)) continue;
+        if constexpr (lv == 1) {
+            float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (in) w = *reinterpret_cast<const float4*>(col + c * fs + gy);
+            s[si] = make_float2(w.x, w.y);
+            s[si + 1] = make_float2(w.z, w.w);
+        } else {
+            C v;
+            v.x = T(0); v.y = T(0);
+            if (in) v = col[c * fs + gy];
+            s[si] = v;
+        }
     }
     __syncthreads();
     fft_lines<C, false, N4>(s, n, logn, 3 * G, A.tw);
@@ -462,11 +474,18 @@ __device__ __forceinline__ void colsolve_block(const Spec2Args<T>& A, int bid, i
     }
     __syncthreads();
     fft_lines<C, true, N4>(s, n, logn, 3 * G, A.tw);
-    for (int t = threadIdx.x; t < 3 * gn; t += blockDim.x) {
-        const int c = t >> lgn;
-        const int gy = t & (gn - 1);
-        if ((gy >> logn) < ng && MSC_INB((size_t)jx0 * n + c * fs + gy, (size_t)A.nf * fs, 16))
-            col[c * fs + gy] = s[(c * G + (gy >> logn)) * plen + pad(gy & (n - 1))];
+    for (int t = threadIdx.x; t < (3 * gn >> lv); t += blockDim.x) {
+        const int e = t << lv;
+        const int c = e >> lgn;
+        const int gy = e & (gn - 1);
+        if ((gy >> logn) >= ng || !MSC_INB((size_t)jx0 * n + c * fs + gy + lv, (size_t)A.nf * fs, 16)) continue;
+        const int si = (c * G + (gy >> logn)) * plen + pad(gy & (n - 1));
+        if constexpr (lv == 1) {
+            const C z0 = s[si], z1 = s[si + 1];
+            *reinterpret_cast<float4*>(col + c * fs + gy) = make_float4(z0.x, z0.y, z1.x, z1.y);
+        } else {
+            col[c * fs + gy] = s[si];
+        }
     }
 }
 

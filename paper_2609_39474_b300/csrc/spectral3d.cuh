@@ -127,19 +127,27 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 384 : 768) k_zsolve(Spec2Args
     const size_t n2 = (size_t)n * n;
     const size_t fstride = (size_t)nx4 * n2;
     C* sp = A.spec + (size_t)jx * n2;  // + c * fstride + z * n + jy
+    // binary32 (G >= 2): lines g, g + 1 (g even) hold adjacent j_y values, one 16-byte access
+    constexpr int lv = sizeof(C) == 8 ? 1 : 0;
 #pragma unroll 4
-    for (int t = threadIdx.x; t < 4 * G * n; t += blockDim.x) {
-        const int g = t & (G - 1);
-        const int cz = t >> lg;
+    for (int t = threadIdx.x; t < (4 * G * n >> lv); t += blockDim.x) {
+        const int e = t << lv;
+        const int g = e & (G - 1);
+        const int cz = e >> lg;
         const int z = cz & (n - 1);
         const int c = cz >> logn;
-        C v;
-        v.x = T(0); v.y = T(0);
-        if (g < ng) {
-            const int jy = (jyk0 + g - n / 4) & (n - 1);
-            v = sp[c * fstride + (size_t)z * n + jy];
+        const int jy = (jyk0 + g - n / 4) & (n - 1);
+        if constexpr (lv == 1) {
+            float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (g < ng) w = *reinterpret_cast<const float4*>(sp + c * fstride + (size_t)z * n + jy);
+            s[(c * G + g) * plen + pad(z)] = make_float2(w.x, w.y);
+            s[(c * G + g + 1) * plen + pad(z)] = g + 1 < ng ? make_float2(w.z, w.w) : make_float2(0.f, 0.f);
+        } else {
+            C v;
+            v.x = T(0); v.y = T(0);
+            if (g < ng) v = sp[c * fstride + (size_t)z * n + jy];
+            s[(c * G + g) * plen + pad(z)] = v;
         }
-        s[(c * G + g) * plen + pad(z)] = v;
     }
     __syncthreads();
     fft_stockham<C, false>(s, n, logn, 4 * G, A.tw);
@@ -172,14 +180,26 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 384 : 768) k_zsolve(Spec2Args
     }
     __syncthreads();
     fft_stockham<C, true>(s, n, logn, 4 * G, A.tw);
-    for (int t = threadIdx.x; t < 4 * G * n; t += blockDim.x) {
-        const int g = t & (G - 1);
-        const int cz = t >> lg;
+    for (int t = threadIdx.x; t < (4 * G * n >> lv); t += blockDim.x) {
+        const int e = t << lv;
+        const int g = e & (G - 1);
+        const int cz = e >> lg;
         const int z = cz & (n - 1);
         const int c = cz >> logn;
         if (g >= ng) continue;
         const int jy = (jyk0 + g - n / 4) & (n - 1);
-        sp[c * fstride + (size_t)z * n + jy] = s[(c * G + g) * plen + pad(z)];
+        C* d = sp + c * fstride + (size_t)z * n + jy;
+        const C z0 = s[(c * G + g) * plen + pad(z)];
+        if constexpr (lv == 1) {
+            if (g + 1 < ng) {
+                const C z1 = s[(c * G + g + 1) * plen + pad(z)];
+                *reinterpret_cast<float4*>(d) = make_float4(z0.x, z0.y, z1.x, z1.y);
+            } else {
+                *d = z0;
+            }
+        } else {
+            *d = z0;
+        }
     }
 }
 

@@ -271,9 +271,9 @@ def measure_workload(torch, PL, dev, dim, n, steps, warmup, dist=None, full=Fals
         inner.append(st["inner_total"])
         # set_target, arm + first set-up and warm start, 2 per physical step (end, finish), one sweep per
         # inner iteration and the spectral kernels of every correction (each non-accepted iteration);
-        # the graph runs steps in pairs, so an odd S adds one step's kernels that return at once
-        # (its straight-line iterations, its first sweep, end and finish)
-        odd_step = (best["nmin"] - 1) * (1 + nspec) + 3 if S % 2 else 0
+        # the graph runs steps in groups of four, so S not a multiple of four adds the kernels of up to
+        # three steps that return at once (straight-line iterations, first sweep, end and finish)
+        odd_step = (-S % 4) * ((best["nmin"] - 1) * (1 + nspec) + 3)
         launches += 3 + 2 * S + st["inner_total"] + nspec * (st["inner_total"] - S) + odd_step
     torch.cuda.synchronize()
     clk = clocks.stop() if clocks else None

@@ -327,8 +327,8 @@ cudaGraphNode_t add_spectral_nodes(msc_ctx* c, cudaGraph_t g, cudaGraphNode_t pr
 // sweep.  Replay mode (the counts are given) runs only the first sweep ahead of the loop.
 constexpr int kMaxMarchPrefix = 7;
 // physical steps per iteration of the march graph's step loop (one loop node and one ordinary edge
-// into the next step's first sweep per pair instead of per step)
-constexpr int kMarchStepsPerLoop = 2;
+// into a step's first sweep per group instead of per step)
+constexpr int kMarchStepsPerLoop = 4;
 inline int march_prefix_count(const msc_params& p) {
     if (p.replay) return 0;
     return p.nmin - 1 < 0 ? 0 : (p.nmin - 1 > kMaxMarchPrefix ? kMaxMarchPrefix : p.nmin - 1);
